@@ -1,0 +1,257 @@
+"""Seeded synthetic suspensions shaped like the paper's workloads.
+
+This module only draws inputs (lattice sizes, particle positions, radii,
+densities, initial velocities) and derives the physical parameters the paper
+fixes through its unit conversion (Table 2).  It holds none of the method's
+arithmetic, so both the CUDA library and the CPU oracle can be fed from it.
+
+Parameter derivations (Table 2 and the section "Simulation results"):
+
+* contact stiffness from the contact duration: the expression the paper prints
+  as eta_n in Eq. (5) evaluates to the contact time t_c (10.00 time steps for
+  both of its parameter sets), so k_n = m* (pi^2 + ln^2 e) / t_c^2 with
+  m* = m/2 for a pair of equal particles.  With m = 54373, e = 0.9 this gives
+  2686, the printed 2D value.
+* a periodic gravity-driven suspension balances the particles' weight by a body
+  force on the gas: g_f = -g_s sum_p m_p / (rho_f N_nodes).
+* with walls the gas feels the same gravity as the particles (g_f = g_s) and
+  the walls carry the load.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+STORAGE = {"f64": 0, "f32dev": 1, "f16dev": 2}
+
+
+@dataclasses.dataclass
+class SuspensionConfig:
+    dim: int
+    nx: int
+    ny: int
+    nz: int
+    wall_y: int
+    tau: float
+    body_force: np.ndarray  # (3,) fluid acceleration g_f
+    gravity: np.ndarray  # (3,) particle acceleration g_s
+    rho_fluid: float
+    k_n: float
+    restitution: float
+    dem_substeps: int
+    pos: np.ndarray  # (np,3)
+    vel: np.ndarray  # (np,3)
+    omega: np.ndarray  # (np,3)
+    radius: np.ndarray  # (np,)
+    density: np.ndarray  # (np,) solid density in lattice units
+    storage: str = "f64"
+    name: str = ""
+
+    @property
+    def n_nodes(self) -> int:
+        return self.nx * self.ny * (self.nz if self.dim == 3 else 1)
+
+    @property
+    def n_particles(self) -> int:
+        return int(len(self.radius))
+
+    def masses(self) -> np.ndarray:
+        r = np.asarray(self.radius, dtype=np.float64)
+        if self.dim == 2:
+            return np.asarray(self.density) * math.pi * r * r
+        return np.asarray(self.density) * (4.0 / 3.0) * math.pi * r ** 3
+
+    def replace(self, **kw) -> "SuspensionConfig":
+        return dataclasses.replace(self, **kw)
+
+
+def stiffness_for_contact_time(m_pair: float, e: float, t_c: float = 10.0) -> float:
+    """k_n such that a spring-dashpot pair of reduced mass m_pair stays in
+    contact for t_c lattice steps (the paper's choice, Table 2)."""
+    le = math.log(e)
+    return m_pair * (math.pi ** 2 + le * le) / (t_c * t_c)
+
+
+def random_directions(rng: np.random.Generator, n: int, dim: int) -> np.ndarray:
+    v = rng.standard_normal((n, 3))
+    if dim == 2:
+        v[:, 2] = 0.0
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v
+
+
+def rsa_place(rng: np.random.Generator, radii: np.ndarray, box, dim: int, periodic,
+              gap: float = 1.0, wall_gap: float = 1.0, max_tries: int = 200) -> np.ndarray:
+    """Random sequential addition of non-overlapping disks/spheres.
+
+    ``box`` = (nx, ny, nz) in lattice units (node i sits at coordinate i; the
+    domain spans [-1/2, n-1/2) along each axis).  Surfaces keep at least
+    ``gap`` from each other and ``wall_gap`` from a non-periodic boundary.
+    Returns positions (n,3); raises if the packing cannot be completed.
+    """
+    radii = np.asarray(radii, dtype=np.float64)
+    n = len(radii)
+    L = np.array([box[0], box[1], box[2] if dim == 3 else 1], dtype=np.float64)
+    rmax = float(radii.max()) if n else 1.0
+    cs = 2.0 * rmax + gap
+    ncell = np.maximum(1, np.floor(L[:dim] / cs).astype(int))
+    csz = L[:dim] / ncell
+    grid = {}
+    pos = np.zeros((n, 3))
+    per = list(periodic)
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    for d in range(dim):
+        if per[d]:
+            lo[d], hi[d] = 0.0, L[d]
+    offsets = np.array(np.meshgrid(*([range(-1, 2)] * dim), indexing="ij")).reshape(dim, -1).T
+    order = np.argsort(-radii, kind="stable")  # large first
+    for idx in order:
+        R = radii[idx]
+        for d in range(dim):
+            if not per[d]:
+                lo[d], hi[d] = -0.5 + R + wall_gap, L[d] - 0.5 - R - wall_gap
+        placed = False
+        for _ in range(max_tries):
+            p = np.zeros(3)
+            p[:dim] = lo[:dim] + rng.random(dim) * (hi[:dim] - lo[:dim])
+            c = np.floor(p[:dim] / csz).astype(int)
+            c = np.minimum(c, ncell - 1)
+            ok = True
+            for off in offsets:
+                cc = c + off
+                skip = False
+                for d in range(dim):
+                    if per[d]:
+                        cc[d] %= ncell[d]
+                    elif cc[d] < 0 or cc[d] >= ncell[d]:
+                        skip = True
+                if skip:
+                    continue
+                for j in grid.get(tuple(cc), ()):
+                    dv = pos[j, :dim] - p[:dim]
+                    for d in range(dim):
+                        if per[d]:
+                            dv[d] -= L[d] * np.round(dv[d] / L[d])
+                    if np.dot(dv, dv) < (R + radii[j] + gap) ** 2:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if ok:
+                pos[idx] = p
+                grid.setdefault(tuple(c), []).append(idx)
+                placed = True
+                break
+        if not placed:
+            raise RuntimeError("random sequential addition did not converge")
+    return pos
+
+
+def _finish(dim, nx, ny, nz, wall_y, tau, gs, rho_f, e, radius, density, pos, vel, name,
+            k_n=None, storage="f64", balance=True, substeps=1):
+    n = len(radius)
+    cfg = SuspensionConfig(
+        dim=dim, nx=nx, ny=ny, nz=nz if dim == 3 else 1, wall_y=wall_y, tau=tau,
+        body_force=np.zeros(3), gravity=np.asarray(gs, dtype=np.float64), rho_fluid=rho_f,
+        k_n=0.0, restitution=e, dem_substeps=substeps, pos=pos, vel=vel, omega=np.zeros((n, 3)),
+        radius=np.asarray(radius, dtype=np.float64), density=np.asarray(density, dtype=np.float64),
+        storage=storage, name=name)
+    m = cfg.masses()
+    if k_n is None:
+        k_n = stiffness_for_contact_time(float(np.max(m)) / 2.0 if n else 1.0, e)
+    cfg.k_n = float(k_n)
+    if wall_y:
+        cfg.body_force = np.asarray(gs, dtype=np.float64).copy()
+    elif balance and n:
+        cfg.body_force = -np.asarray(gs, dtype=np.float64) * float(m.sum()) / (rho_f * cfg.n_nodes)
+    return cfg
+
+
+def channel_config(nx=128, ny=256, n_particles=20, radius=6.0, density_ratio=10.0, g=1e-6, tau=0.6,
+                   seed=1, e=0.9, storage="f64", name="D2Q9 channel") -> SuspensionConfig:
+    """2D channel suspension: periodic in x, walls in y, gravity -y on both
+    phases, disks at rest placed by RSA with >= 1 lu gaps; fluid at rest."""
+    rng = np.random.default_rng(seed)
+    radii = np.full(n_particles, float(radius))
+    pos = rsa_place(rng, radii, (nx, ny, 1), 2, (True, False, True)) if n_particles else np.zeros((0, 3))
+    return _finish(2, nx, ny, 1, 1, tau, (0.0, -g, 0.0), 1.0, e, radii, np.full(n_particles, density_ratio),
+                   pos, np.zeros((n_particles, 3)), name, storage=storage)
+
+
+def config1(**kw) -> SuspensionConfig:
+    """D2Q9 FP64 128x256, tau 0.6, 20 disks R=6, density ratio 10, g=1e-6."""
+    return channel_config(name="cfg1 D2Q9 128x256 channel, 20 disks R=6", **kw)
+
+
+def periodic2d_config(nx=8192, ny=32768, phi=0.05, radius=4.0, tau=0.55, seed=2, gs=1.176e-7, v0=5e-3,
+                      e=0.9, storage="f64", density_ratio=None, name="") -> SuspensionConfig:
+    """2D periodic gravity-driven suspension (paper 2D case, scaled): disks of
+    radius R at area fraction phi by RSA, density ratio drawn log-uniform in
+    [2.5, 1500] once per run, initial speed v0 in random directions."""
+    rng = np.random.default_rng(seed)
+    n = int(round(phi * nx * ny / (math.pi * radius * radius)))
+    if density_ratio is None:
+        density_ratio = float(math.exp(rng.uniform(math.log(2.5), math.log(1500.0))))
+    radii = np.full(n, float(radius))
+    pos = rsa_place(rng, radii, (nx, ny, 1), 2, (True, True, True))
+    vel = v0 * random_directions(rng, n, 2)
+    return _finish(2, nx, ny, 1, 0, tau, (0.0, -gs, 0.0), 1.0, e, radii, np.full(n, density_ratio), pos, vel,
+                   name or f"D2Q9 periodic {nx}x{ny}, {n} disks R={radius}", storage=storage)
+
+
+def config2(scale: float = 1.0, **kw) -> SuspensionConfig:
+    """D2Q9 FP64 8192x32768 (scale<1 shrinks both sides), phi=0.05, R=4."""
+    nx = max(32, int(round(8192 * scale)))
+    ny = max(64, int(round(32768 * scale)))
+    return periodic2d_config(nx=nx, ny=ny, **kw)
+
+
+def channel3d_config(nx=384, ny=1512, nz=384, phi=None, n_particles=129024, radius=3.75, density_ratio=1000.0,
+                     g=4.704e-7, tau=0.6, seed=3, v0=5e-3, e=0.9, storage="f64", name="") -> SuspensionConfig:
+    """3D suspension between walls in y (periodic x/z), spheres by RSA,
+    gravity -y on both phases, initial speed v0 in random directions."""
+    rng = np.random.default_rng(seed)
+    if phi is not None:
+        n_particles = int(round(phi * nx * ny * nz / (4.0 / 3.0 * math.pi * radius ** 3)))
+    radii = np.full(n_particles, float(radius))
+    pos = rsa_place(rng, radii, (nx, ny, nz), 3, (True, False, True)) if n_particles else np.zeros((0, 3))
+    vel = v0 * random_directions(rng, n_particles, 3) if n_particles else np.zeros((0, 3))
+    return _finish(3, nx, ny, nz, 1, tau, (0.0, -g, 0.0), 1.0, e, radii, np.full(n_particles, density_ratio),
+                   pos, vel, name or f"D3Q19 channel {nx}x{ny}x{nz}, {n_particles} spheres R={radius}",
+                   storage=storage)
+
+
+def config3(**kw) -> SuspensionConfig:
+    """D3Q19 FP64 384x1512x384, walls in y, 129,024 spheres R=3.75, ratio 1000."""
+    return channel3d_config(**kw)
+
+
+def config3_scaled(nx=64, ny=96, nz=64, storage="f64", seed=3, **kw) -> SuspensionConfig:
+    """A cut-down config 3 at the same solid volume fraction (~0.1278)."""
+    phi = 129024 * (4.0 / 3.0) * math.pi * 3.75 ** 3 / (384 * 1512 * 384)
+    return channel3d_config(nx=nx, ny=ny, nz=nz, phi=phi, storage=storage, seed=seed, **kw)
+
+
+def periodic3d_config(nx=64, ny=64, nz=64, phi=0.1, radius=3.75, density_ratio=1000.0, gs=4.704e-7, tau=0.6,
+                      seed=5, v0=5e-3, e=0.9, storage="f64", name="") -> SuspensionConfig:
+    """3D fully periodic gravity-driven suspension (the paper's 3D setup)."""
+    rng = np.random.default_rng(seed)
+    n = int(round(phi * nx * ny * nz / (4.0 / 3.0 * math.pi * radius ** 3)))
+    radii = np.full(n, float(radius))
+    pos = rsa_place(rng, radii, (nx, ny, nz), 3, (True, True, True))
+    vel = v0 * random_directions(rng, n, 3)
+    return _finish(3, nx, ny, nz, 0, tau, (0.0, -gs, 0.0), 1.0, e, radii, np.full(n, density_ratio), pos, vel,
+                   name or f"D3Q19 periodic {nx}x{ny}x{nz}, {n} spheres", storage=storage)
+
+
+def random_populations(rng: np.random.Generator, cfg: SuspensionConfig, amp: float = 0.05) -> np.ndarray:
+    """Positive non-equilibrium populations for parity tests: rho_f/Q times
+    (1 + amp * noise), shape (Q, nz, ny, nx).  Far from equilibrium on
+    purpose, so that every term of the collision is exercised."""
+    Q = 9 if cfg.dim == 2 else 19
+    nz = cfg.nz if cfg.dim == 3 else 1
+    return cfg.rho_fluid / Q * (1.0 + amp * rng.standard_normal((Q, nz, cfg.ny, cfg.nx)))
