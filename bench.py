@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of the LB-IMB-DEM time step on GB300 (MLUPS and roofline).
+
+Default workload: the 3D suspension shaped like the paper's 3D case, scaled
+to d = 7.5: D3Q19 384x1512x384 lattice (222.95M nodes), walls in y, periodic
+x/z, 129,024 spheres R = 3.75 (solid fraction 0.128), density ratio 1000,
+gravity 4.704e-7 in -y, FP64 storage and arithmetic.  One "step" = one full
+time step of the method (eps rasterisation, pull-stream + Eq. 1 collision +
+Eq. 3 force/torque sums, DEM), inputs resident in HBM.
+
+The JSON line carries: value (MLUPS over the timed region, CUDA events on
+the simulation's stream, graph replay), roofline of the dominant kernel
+(collide, from a second pass with events between kernel families), e2e (the
+same metric through the C ABI with pinned host buffers: particle state
+uploaded and read back every step), cpu_baseline (the FP64 CPU oracle on a
+bounded sample), clocks sampled during the timed region, and the FP32/FP16
+deviation-storage variants with their error against FP64.
+
+--impl reference times the CPU oracle (the reference arm) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1011_2613_gb300 import inputs as I  # noqa: E402
+
+METRIC = "MLUPS and % HBM roofline, D3Q19 IMB; FP32/FP16-store vs FP64 at stated error"
+UNIT = "MLUPS"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    "cfg3": dict(make=lambda seed: I.config3(seed=seed),
+                 name="D3Q19 384x1512x384 channel (walls y), 129024 spheres R=3.75, density ratio 1000, "
+                      "g=4.704e-7, tau=0.6"),
+    "cfg2": dict(make=lambda seed: I.config2(seed=seed),
+                 name="D2Q9 8192x32768 periodic, ~267k disks R=4 phi=0.05, density ratio log-uniform "
+                      "[2.5,1500], tau=0.55"),
+    "cfg1": dict(make=lambda seed: I.config1(seed=seed),
+                 name="D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6, tau=0.6"),
+}
+
+
+def algorithmic_bytes_per_lup(cfg, owned_fraction):
+    """Read and write each population once (2 Q s), read the owner word of
+    every node (4 B), read the covered fraction at owned nodes."""
+    Q = 9 if cfg.dim == 2 else 19
+    s = {"f64": 8, "f32dev": 4, "f16dev": 2}[cfg.storage]
+    se = 8 if cfg.storage == "f64" else 4
+    return 2 * Q * s + 4 + se * owned_fraction
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(steps=4, nx=96, ny=128, nz=96, seed=3):
+    """The FP64 CPU oracle on a bounded sample of the 3D workload: a
+    nx x ny x nz sub-channel at the same solid fraction and parameters."""
+    from oracle import oracle as O
+    cfg = I.config3_scaled(nx=nx, ny=ny, nz=nz, seed=seed)
+    sim = O.OracleSim(cfg)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sim.close()
+    return {"value": cfg.n_nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"D3Q19 {nx}x{ny}x{nz} channel, {cfg.n_particles} spheres R=3.75 (config-3 solid fraction "
+                      f"and parameters), {steps} steps, single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands on the host cores."""
+    import torch.distributed as dist  # noqa: F401
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    cfg = I.config3_scaled(nx=64, ny=96, nz=64, seed=3)
+    sim = O.OracleSim(cfg)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = cfg.n_nodes * args.steps / dt / 1e6
+    sample = (f"D3Q19 64x96x64 channel, {cfg.n_particles} spheres R=3.75 at config-3 solid fraction and parameters; "
+              f"each step is this bounded sample of the workload")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["name"] + " (bounded CPU sample)", "storage": "f64"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+def time_graph_steps(sim, torch, steps):
+    s = sim.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    sim.step(steps)
+    e1.record(s)
+    e1.synchronize()
+    sim.sync()
+    return e0.elapsed_time(e1)
+
+
+def owned_fraction(sim, torch):
+    eps = torch.empty(sim.N, dtype=torch.float64, device=sim.device)
+    sim.fields_device(None, None, eps)
+    torch.cuda.synchronize()
+    frac = float((eps > 0).double().mean().item())
+    del eps
+    return frac
+
+
+def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=None):
+    from paper_1011_2613_gb300 import lbm as L
+    sim = L.Simulation(cfg)
+    sim.step(args.warmup)
+    sim.sync()
+    ms = time_graph_steps(sim, torch, args.steps)
+    kms, tot = sim.step_profiled(args.steps)
+    fo = owned_fraction(sim, torch)
+    bpl = algorithmic_bytes_per_lup(cfg, fo)
+    t_coll = kms["collide"] / args.steps
+    achieved = bpl * cfg.n_nodes / (t_coll * 1e-3) / 1e9
+    res = {"mlups": cfg.n_nodes * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+           "collide_ms": t_coll, "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+           "bytes_per_lup": bpl, "collide_gbs": achieved, "hbm_frac": achieved / peaks["hbm_gbs"]}
+    if ref_sim is not None:
+        done = args.warmup + 2 * args.steps
+        if steps_target > done:
+            sim.step(steps_target - done)
+        sim.sync()
+        res.update(compare_to(ref_sim, sim, torch))
+        res["error_after_steps"] = steps_target
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return res
+
+
+def compare_to(ref, sim, torch):
+    """Velocity-field L2, particle trajectory and mass drift vs FP64."""
+    u64 = torch.empty(ref.dim * ref.N, dtype=torch.float64, device=ref.device)
+    ulo = torch.empty_like(u64)
+    ref.fields_device(None, u64, None)
+    sim.fields_device(None, ulo, None)
+    torch.cuda.synchronize()
+    l2 = float((torch.linalg.vector_norm(ulo - u64) / torch.linalg.vector_norm(u64)).item())
+    del u64, ulo
+    p64, plo = ref.particles(), sim.particles()
+    d = plo["pos"] - p64["pos"]
+    for ax, n in enumerate(ref.shape):
+        if not (ax == 1 and ref.cfg.wall_y):
+            d[:, ax] -= n * np.round(d[:, ax] / n)
+    m64, _, _ = ref.totals()
+    mlo, _, _ = sim.totals()
+    fscale = float(np.max(np.abs(p64["force"])))
+    return {"velocity_l2_rel": l2, "particle_pos_rms": float(np.sqrt((d ** 2).sum(axis=1).mean())),
+            "particle_pos_max": float(np.sqrt((d ** 2).sum(axis=1)).max()),
+            "force_max_rel": float(np.max(np.abs(plo["force"] - p64["force"]))) / fscale,
+            "mass_drift_rel": abs(mlo - m64) / m64}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1011_2613_gb300 import lbm as L
+    peaks = load_peaks()
+    wl = WORKLOADS[args.workload]
+    # weak scaling: every rank steps its own independent suspension
+    cfg = wl["make"](3 + rank)
+    cfg.storage = "f64"
+
+    sim = L.Simulation(cfg)
+    sim.step(args.warmup)
+    sim.sync()
+    launches = sim.launches_per_step() * args.steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = time_graph_steps(sim, torch, args.steps)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * cfg.n_nodes * args.steps / (ms * 1e-3) / 1e6
+
+    # per-kernel device times (events between kernel families)
+    kms, tot = sim.step_profiled(args.steps)
+    fo = owned_fraction(sim, torch)
+    bpl = algorithmic_bytes_per_lup(cfg, fo)
+    t_coll = kms["collide"] / args.steps
+    achieved = bpl * cfg.n_nodes / (t_coll * 1e-3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        n3 = 3 * cfg.n_particles
+        hin = {k: torch.from_numpy(np.ascontiguousarray(getattr(cfg, a).reshape(-1))).pin_memory()
+               for k, a in (("pos", "pos"), ("vel", "vel"), ("omega", "omega"))}
+        hout = {k: torch.empty(n3, dtype=torch.float64).pin_memory() for k in ("pos", "vel", "omega", "force",
+                                                                              "torque")}
+        pin_np = {k: v.numpy() for k, v in hout.items()}
+        p0 = sim.particles()
+        for k in ("pos", "vel", "omega"):
+            hin[k].numpy()[:] = p0[k].reshape(-1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.set_particles(hin["pos"].numpy(), hin["vel"].numpy(), hin["omega"].numpy())
+            sim.step(1)
+            sim.particles(out=pin_np)
+            for k in ("pos", "vel", "omega"):
+                hin[k].numpy()[:] = pin_np[k]
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * cfg.n_nodes * args.steps / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * n3, "d2h_bytes_per_step": 5 * 8 * n3,
+               "path": "lbm_imb_set_particles -> lbm_imb_step(1) -> lbm_imb_particles, pinned host buffers"}
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        steps_done = args.warmup + 2 * args.steps + (args.steps if e2e else 0)
+        for st in ("f32dev", "f16dev"):
+            try:
+                variants[st] = measure_variant(cfg.replace(storage=st), args, torch, peaks, st, sim, steps_done)
+            except Exception as ex:  # report, keep the headline line
+                variants[st] = {"error": str(ex)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample()
+
+    sim.close()
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "storage": "f64", "nodes": cfg.n_nodes,
+                       "particles": cfg.n_particles, "l2": "inputs larger than L2 (two FP64 lattices, "
+                       f"{2 * 19 * 8 * cfg.n_nodes / 1e9:.1f} GB)", "graph": "CUDA graph per step"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "collide_kernel<D3Q19,F64>", "bytes_per_lup": bpl,
+                         "owned_fraction": fo, "peak_src": peaks["src"]},
+            "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+            "profiled_ms_per_step": tot / args.steps,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "variants": variants,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

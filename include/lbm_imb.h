@@ -1,0 +1,208 @@
+/*
+ * lbm_imb.h -- C ABI of the GB300 LB-IMB-DEM library (liblbm_imb.so).
+ *
+ * The library advances a gas-solid suspension with the method of Xiong et al.,
+ * "Large-Scale DNS of Gas-Solid Flow on Mole-8.5" (arXiv:1011.2613):
+ *   - LBGK on D2Q9 or D3Q19 (section "Numerical scheme"),
+ *   - the Noble-Torczynski immersed moving boundary term, Eq. (1), with the
+ *     weighting beta(eps, tau) of Eq. (2) and the solid collision term
+ *     Omega^S printed after Eq. (2),
+ *   - the solid fraction eps of each lattice cell = covered area/volume (text
+ *     after the Omega^S equation), computed exactly for disks and spheres,
+ *   - the hydrodynamic force and torque on each particle, Eq. (3),
+ *   - frictionless linear spring-dashpot DEM contacts, Eqs. (4)-(5), and a
+ *     symplectic Euler particle update.
+ * Every step runs in hand-written sm_103a CUDA kernels on the caller's stream.
+ *
+ * Conventions (all calls):
+ *   - Every call returns an int status (LBM_IMB_OK = 0 or a negative code);
+ *     output parameters are written only on success.
+ *   - Lattice units: spacing h = 1, time step 1.  Node (i,j,k) sits at
+ *     (i,j,k); the domain spans [-1/2, n-1/2) along each axis.
+ *   - Population direction order (the interface order, used by
+ *     lbm_imb_get/set_populations):
+ *       D2Q9 : (0,0) (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1)
+ *       D3Q19: (0,0,0) (+-1,0,0) (0,+-1,0) (0,0,+-1) (1,1,0) (-1,-1,0)
+ *              (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+ *              (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *     i.e. the rest direction, then opposite pairs.
+ *   - Field and population arrays are dense, x fastest:
+ *       f[q][z][y][x], rho[z][y][x], u[d][z][y][x] (d < dim), eps[z][y][x].
+ *     Particle arrays are [n][3] (z and the x/y spin components are zero
+ *     in 2D).
+ *   - Pointers documented as "host" must be host memory; "device" pointers
+ *     must be device memory of the device current at lbm_imb_init.
+ *   - A handle is not thread-safe; calls on one handle must be serialised.
+ *
+ * Readings of the paper used where it is silent or garbled:
+ *   - state between steps = post-collision populations; one step =
+ *     rasterise eps -> pull-stream -> collide (Eq. 1) -> force/torque (Eq. 3)
+ *     -> DEM.
+ *   - several particles covering one cell: eps = min(1, sum_p e_p), solid
+ *     velocity = e-weighted mean of the particles' velocities, node force
+ *     split in proportion e_p.  At most LBM_IMB_MAX_OWNERS particles may
+ *     cover one cell (else LBM_IMB_EOWNERS).
+ *   - solid velocity includes rotation, V = v_p + omega_p x (x_n - x_p).
+ *   - body force F_i = 3 w_i rho (c_i . g_f) at every node.
+ *   - force on a particle = - sum_n beta_n sum_i Omega_i^S c_i (momentum the
+ *     solid term gives the fluid is taken from the particle); torque likewise
+ *     with (x_n - x_p) x.
+ *   - walls (wall_y = 1): halfway bounce-back at y = -1/2 and ny - 1/2.
+ *   - DEM: overlap xi = R_i + R_j - |r_i - r_j|; force on i =
+ *     k_n xi n_ij - eta v_n,ij, n_ij = (r_i - r_j)/|r_i - r_j|,
+ *     eta = -2 ln(e) sqrt(m* k_n / (pi^2 + ln^2 e)), m* = m_i m_j/(m_i+m_j)
+ *     (m* = m_i against a wall).  v += (F_f + F_c + m g_s)/m dt, x += v dt,
+ *     omega += T_f / I dt over dem_substeps sub-steps of dt = 1/dem_substeps.
+ *   - masses: 2D m = rho_s pi R^2 (per unit depth), I = m R^2/2;
+ *             3D m = rho_s 4/3 pi R^3, I = 2/5 m R^2.
+ */
+#ifndef LBM_IMB_H
+#define LBM_IMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_IMB_MAX_OWNERS 4
+
+/* status codes */
+enum {
+  LBM_IMB_OK = 0,
+  LBM_IMB_EINVAL = -1,      /* invalid argument or configuration */
+  LBM_IMB_ENOMEM = -2,      /* caller buffer smaller than lbm_imb_required_bytes */
+  LBM_IMB_ECUDA = -3,       /* a CUDA runtime call failed */
+  LBM_IMB_ETIMEOUT = -4,    /* a bounded device wait gave up */
+  LBM_IMB_ENONFINITE = -5,  /* NaN/Inf found by a health check */
+  LBM_IMB_EUNSUPPORTED = -6,/* configuration outside the implemented limits */
+  LBM_IMB_EOWNERS = -7,     /* a lattice cell was covered by too many particles */
+  LBM_IMB_EBIN = -8         /* a DEM cell-list bin overflowed */
+};
+
+/* population storage (the arithmetic follows the storage) */
+enum {
+  LBM_IMB_STORE_F64 = 0,    /* FP64 populations, FP64 arithmetic */
+  LBM_IMB_STORE_F32DEV = 1, /* FP32 storage of f_i - w_i rho0, FP32 arithmetic */
+  LBM_IMB_STORE_F16DEV = 2  /* FP16 storage of (f_i - w_i rho0)/w_i, FP32 arithmetic */
+};
+
+/* Problem statement: lattice, relaxation time, body force, particles with
+ * radii and densities (the quantities of the paper's Table 2). */
+typedef struct lbm_imb_config {
+  uint32_t struct_size;    /* = sizeof(lbm_imb_config) */
+  int32_t dim;             /* 2 (D2Q9) or 3 (D3Q19) */
+  int32_t nx, ny, nz;      /* lattice nodes; nz = 1 for dim = 2 */
+  int32_t wall_y;          /* 0: periodic in y; 1: bounce-back walls in y */
+  int32_t storage;         /* LBM_IMB_STORE_* */
+  double tau;              /* BGK relaxation time, > 0.5 */
+  double body_force[3];    /* gas acceleration g_f (F_i built from it) */
+  double gravity[3];       /* particle acceleration g_s */
+  double rho_fluid;        /* initial gas density rho0 (fluid starts at rest) */
+  double k_n;              /* DEM normal stiffness, >= 0 */
+  double restitution;      /* DEM restitution coefficient e in (0, 1] */
+  int32_t dem_substeps;    /* DEM sub-steps per lattice step, >= 1 */
+  int32_t reserved0;
+  int64_t n_particles;     /* >= 0 */
+  const double* pos;       /* host, [n][3], copied at init */
+  const double* vel;       /* host, [n][3], copied at init */
+  const double* omega;     /* host, [n][3], copied at init */
+  const double* radius;    /* host, [n], copied at init; > 0 */
+  const double* density;   /* host, [n], solid density in lattice units */
+} lbm_imb_config;
+
+typedef struct lbm_imb lbm_imb_t; /* opaque, library-owned host state */
+
+/* Device bytes the caller must provide to lbm_imb_init for this config
+ * (populations, solid-fraction slots, particle state, DEM bins), or 0 if the
+ * config is invalid. */
+size_t lbm_imb_required_bytes(const lbm_imb_config* cfg);
+
+/* Lay out the caller's device block (dev_buf, >= required bytes, 256-byte
+ * aligned, owned by the caller and never freed by the library), upload the
+ * particles, set the populations to the rest equilibrium w_i rho0 and
+ * rasterise eps.  cuda_stream (a cudaStream_t, may be NULL for the legacy
+ * stream) is the stream every later call of this handle uses.  On success
+ * *out receives the handle.  The device current at this call is used. */
+int lbm_imb_init(const lbm_imb_config* cfg, void* dev_buf, size_t bytes,
+                 void* cuda_stream, lbm_imb_t** out);
+
+/* Queue n >= 0 time steps on the handle's stream (asynchronous; replays a
+ * captured CUDA graph).  Device-side errors (EOWNERS, EBIN) are reported by
+ * the next synchronising call. */
+int lbm_imb_step(lbm_imb_t* h, int64_t n);
+
+/* Kernel families of one time step, in launch order (indices into the
+ * timing array of lbm_imb_step_profiled). */
+enum {
+  LBM_IMB_K_EPS_CLEAR = 0, /* clear the previous eps footprint, zero Eq. 3 sums */
+  LBM_IMB_K_EPS_RASTER = 1,/* exact eps of every covered cell */
+  LBM_IMB_K_COLLIDE = 2,   /* pull-stream + Eq. 1 collision + Eq. 3 sums */
+  LBM_IMB_K_DEM = 3,       /* cell list, Eqs. 4-5 contacts, integration */
+  LBM_IMB_NUM_KERNELS = 4
+};
+
+/* Run n (1..4096) time steps like lbm_imb_step but launched directly (no
+ * graph) with CUDA events between the kernel families, then synchronise.
+ * kernel_ms[LBM_IMB_NUM_KERNELS] receives the summed device time of each
+ * family over the n steps, *total_ms the device time from the first launch
+ * to the end of the last step.  Same results as lbm_imb_step. */
+int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* total_ms);
+
+/* Number of kernel launches one time step issues (for launch accounting). */
+int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
+
+/* Wait for the handle's stream and report device-side errors. */
+int lbm_imb_sync(lbm_imb_t* h);
+
+/* Copy particle state into caller-owned host arrays ([n][3] each, any may be
+ * NULL): positions, velocities, spins, and the hydrodynamic force and torque
+ * of the last step (Eq. 3).  cap = capacity in particles (>= n).
+ * Synchronises the stream. */
+int lbm_imb_particles(lbm_imb_t* h, double* pos, double* vel, double* omega,
+                      double* force, double* torque, int64_t cap);
+
+/* Replace particle positions/velocities/spins (host, [n][3], any may be
+ * NULL to keep the current value); n must equal the configured count.
+ * Enqueued on the stream (the host arrays are read before returning). */
+int lbm_imb_set_particles(lbm_imb_t* h, const double* pos, const double* vel,
+                          const double* omega, int64_t n);
+
+/* Macroscopic fields of the populations the next collision sees: rho,
+ * u = sum_i f_i c_i / rho + g_f/2 (dim components) and eps = min(1, sum of
+ * covered fractions) at the current particle positions.  cap = capacity in
+ * nodes (>= nx*ny*nz).  on_device = 1: the pointers are device memory, the
+ * call is enqueued on the stream; 0: host memory, the call synchronises.
+ * Any pointer may be NULL. */
+int lbm_imb_fields(lbm_imb_t* h, double* rho, double* u, double* eps,
+                   int64_t cap, int on_device);
+
+/* Read / overwrite the stored post-collision populations as FP64
+ * f[q][z][y][x] (reduced storages convert).  cap = capacity in values
+ * (>= Q*nx*ny*nz).  on_device as for lbm_imb_fields. */
+int lbm_imb_get_populations(lbm_imb_t* h, double* f, int64_t cap, int on_device);
+int lbm_imb_set_populations(lbm_imb_t* h, const double* f, int64_t cap, int on_device);
+
+/* Global sums (synchronises): total fluid mass sum f, fluid momentum
+ * sum f c [3], particle momentum sum m v [3].  Any pointer may be NULL. */
+int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum,
+                   double* particle_momentum);
+
+/* Steps taken since init. */
+int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps);
+
+/* Release the handle (its CUDA graphs and host state).  The caller's device
+ * block is not touched. */
+int lbm_imb_destroy(lbm_imb_t* h);
+
+/* Static description of a status code. */
+const char* lbm_imb_strerror(int status);
+
+/* Library version string. */
+const char* lbm_imb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_IMB_H */

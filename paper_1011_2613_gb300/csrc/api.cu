@@ -1,0 +1,625 @@
+// C ABI of liblbm_imb (declared in include/lbm_imb.h): configuration checks,
+// layout of the caller's device block, the per-step schedule (captured once
+// per ping-pong parity into a CUDA graph), and the synchronising accessors.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm_internal.cuh"
+
+using lbm::View;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStageMax = 64ull << 20;  // staging for host-side field copies
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+  int pitch;
+  long long plane;
+  int Q;
+  size_t esz_f, esz_eps;
+  int nb[3];
+  double bsz[3];
+  double rmax;
+  int smem;
+  size_t off_f[2], off_own[lbm::kMaxOwners], off_eps[lbm::kMaxOwners];
+  size_t off_pos, off_vel, off_omg, off_rad, off_mass, off_inertia, off_ff, off_tf, off_fc;
+  size_t off_lo, off_binof, off_bincount, off_binslot, off_err, off_red, off_stage;
+  size_t stage_bytes;
+  size_t total;
+};
+
+int validate(const lbm_imb_config* c) {
+  if (!c || c->struct_size < sizeof(lbm_imb_config)) return LBM_IMB_EINVAL;
+  if (c->dim != 2 && c->dim != 3) return LBM_IMB_EINVAL;
+  if (c->nx < 2 || c->ny < 2 || c->nz < 1) return LBM_IMB_EINVAL;
+  if (c->dim == 2 && c->nz != 1) return LBM_IMB_EINVAL;
+  if (c->ny > 65535 || c->nz > 65535) return LBM_IMB_EUNSUPPORTED;
+  if (!(c->tau > 0.5) || !isfinite(c->tau)) return LBM_IMB_EINVAL;
+  if (c->storage < 0 || c->storage > 2) return LBM_IMB_EINVAL;
+  if (c->wall_y != 0 && c->wall_y != 1) return LBM_IMB_EINVAL;
+  if (!(c->rho_fluid > 0.0)) return LBM_IMB_EINVAL;
+  if (c->n_particles < 0 || c->n_particles > (1ll << 30)) return LBM_IMB_EINVAL;
+  if (c->dem_substeps < 1) return LBM_IMB_EINVAL;
+  if (c->n_particles > 0) {
+    if (!c->pos || !c->radius || !c->density) return LBM_IMB_EINVAL;
+    if (!(c->k_n >= 0.0) || !(c->restitution > 0.0 && c->restitution <= 1.0)) return LBM_IMB_EINVAL;
+    for (int64_t p = 0; p < c->n_particles; p++) {
+      if (!(c->radius[p] > 0.0) || !(c->density[p] > 0.0)) return LBM_IMB_EINVAL;
+      for (int d = 0; d < 3; d++)
+        if (!isfinite(c->pos[3 * p + d])) return LBM_IMB_EINVAL;
+    }
+  }
+  return LBM_IMB_OK;
+}
+
+int make_layout(const lbm_imb_config* c, Layout* L) {
+  int st = validate(c);
+  if (st) return st;
+  const int nz = c->dim == 3 ? c->nz : 1;
+  L->Q = c->dim == 2 ? 9 : 19;
+  L->pitch = (c->nx + 31) / 32 * 32;
+  L->plane = (long long)L->pitch * c->ny * nz;
+  L->esz_f = c->storage == LBM_IMB_STORE_F64 ? 8 : (c->storage == LBM_IMB_STORE_F32DEV ? 4 : 2);
+  L->esz_eps = c->storage == LBM_IMB_STORE_F64 ? 8 : 4;
+  double rmax = 0.0;
+  for (int64_t p = 0; p < c->n_particles; p++) rmax = c->radius[p] > rmax ? c->radius[p] : rmax;
+  L->rmax = rmax;
+  const int ext[3] = {c->nx, c->ny, nz};
+  for (int d = 0; d < 3; d++) {
+    L->nb[d] = 1;
+    L->bsz[d] = (double)ext[d];
+    if (d < c->dim && rmax > 0.0) {
+      // a periodic axis must be wide enough that a particle cannot meet its
+      // own image
+      const bool periodic = !(d == 1 && c->wall_y);
+      if (periodic && ext[d] < 2.0 * rmax + 2.0) return LBM_IMB_EUNSUPPORTED;
+      int nb = (int)floor(ext[d] / (2.0 * rmax));
+      if (nb < 1) nb = 1;
+      L->nb[d] = nb;
+      L->bsz[d] = (double)ext[d] / nb;
+    }
+  }
+  L->smem = 0;
+  if (c->n_particles > 0) {
+    if ((c->dim == 3 && rmax > 12.0) || (c->dim == 2 && rmax > 29.0)) return LBM_IMB_EUNSUPPORTED;
+    L->smem = lbm::eps_raster_smem_bytes(c->dim, c->storage, rmax);
+    if (L->smem < 0) return LBM_IMB_EUNSUPPORTED;
+  }
+  const long long nbins = (long long)L->nb[0] * L->nb[1] * L->nb[2];
+  const size_t np = (size_t)(c->n_particles > 0 ? c->n_particles : 1);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  for (int k = 0; k < 2; k++) L->off_f[k] = take((size_t)L->Q * L->plane * L->esz_f);
+  for (int s = 0; s < lbm::kMaxOwners; s++) L->off_own[s] = take((size_t)L->plane * 4);
+  for (int s = 0; s < lbm::kMaxOwners; s++) L->off_eps[s] = take((size_t)L->plane * L->esz_eps);
+  L->off_pos = take(np * 24);
+  L->off_vel = take(np * 24);
+  L->off_omg = take(np * 24);
+  L->off_rad = take(np * 8);
+  L->off_mass = take(np * 8);
+  L->off_inertia = take(np * 8);
+  L->off_ff = take(np * 24);
+  L->off_tf = take(np * 24);
+  L->off_fc = take(np * 24);
+  L->off_lo = take(np * 24);
+  L->off_binof = take(np * 4);
+  L->off_bincount = take((size_t)nbins * 4);
+  L->off_binslot = take((size_t)nbins * lbm::kBinCap * 4);
+  L->off_err = take(16);
+  L->off_red = take(8 * 8);
+  const size_t dense_row = (size_t)c->nx * 8 * (L->Q > 5 ? L->Q : 5);
+  const size_t full = dense_row * (size_t)c->ny * nz;
+  L->stage_bytes = full < kStageMax ? full : kStageMax;
+  if (L->stage_bytes < dense_row) L->stage_bytes = dense_row;
+  L->off_stage = take(L->stage_bytes);
+  L->total = o;
+  return LBM_IMB_OK;
+}
+
+int map_err(int bits) {
+  if (bits & lbm::ERR_TIMEOUT) return LBM_IMB_ETIMEOUT;
+  if (bits & lbm::ERR_OWNERS) return LBM_IMB_EOWNERS;
+  if (bits & lbm::ERR_BIN) return LBM_IMB_EBIN;
+  if (bits & lbm::ERR_NONFINITE) return LBM_IMB_ENONFINITE;
+  return LBM_IMB_OK;
+}
+
+}  // namespace
+
+struct lbm_imb {
+  View v;  // fsrc/fdst filled per use
+  void* f[2];
+  int cur;
+  cudaStream_t stream;
+  int smem;
+  cudaGraphExec_t graph[2];
+  bool graphs_tried;
+  bool graphs_ok;
+  int64_t steps;
+  int dim, Q, np;
+  long long N;
+  double* stage;
+  size_t stage_bytes;
+};
+
+namespace {
+
+View view_of(const lbm_imb* h, int src) {
+  View v = h->v;
+  v.fsrc = h->f[src];
+  v.fdst = h->f[src ^ 1];
+  return v;
+}
+
+void enqueue_step(lbm_imb* h, int src) {
+  View v = view_of(h, src);
+  lbm::launch_eps_clear(v, true, h->stream);
+  lbm::launch_eps_raster(v, h->smem, h->stream);
+  lbm::launch_collide(v, h->stream);
+  lbm::launch_dem(v, h->stream);
+}
+
+void try_capture(lbm_imb* h) {
+  h->graphs_tried = true;
+  h->graphs_ok = false;
+  if (h->stream == nullptr) return;  // the legacy stream cannot be captured
+  for (int k = 0; k < 2; k++) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    enqueue_step(h, k);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess || g == nullptr) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      if (k == 1) cudaGraphExecDestroy(h->graph[0]);
+      return;
+    }
+    e = cudaGraphInstantiate(&h->graph[k], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (k == 1) cudaGraphExecDestroy(h->graph[0]);
+      return;
+    }
+  }
+  h->graphs_ok = true;
+}
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? LBM_IMB_OK : LBM_IMB_ECUDA; }
+
+int read_err(lbm_imb* h) {
+  int bits = 0;
+  if (cudaMemcpyAsync(&bits, h->v.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return LBM_IMB_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_IMB_ECUDA;
+  if (bits) {
+    cudaMemsetAsync(h->v.err, 0, sizeof(int), h->stream);
+    cudaStreamSynchronize(h->stream);
+  }
+  return map_err(bits);
+}
+
+long long rows_per_chunk(const lbm_imb* h, int comps) {
+  const long long per_row = (long long)h->v.nx * 8 * comps;
+  long long r = (long long)(h->stage_bytes / per_row);
+  return r < 1 ? 1 : r;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_imb_required_bytes(const lbm_imb_config* cfg) {
+  Layout L;
+  if (make_layout(cfg, &L) != LBM_IMB_OK) return 0;
+  return L.total;
+}
+
+int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cuda_stream,
+                 lbm_imb_t** out) {
+  if (!out || !dev_buf) return LBM_IMB_EINVAL;
+  Layout L;
+  int st = make_layout(c, &L);
+  if (st) return st;
+  if (bytes < L.total) return LBM_IMB_ENOMEM;
+  if (((uintptr_t)dev_buf) % kAlign) return LBM_IMB_EINVAL;
+  lbm_imb* h = new (std::nothrow) lbm_imb();
+  if (!h) return LBM_IMB_ENOMEM;
+  unsigned char* base = static_cast<unsigned char*>(dev_buf);
+  const int nz = c->dim == 3 ? c->nz : 1;
+  const int np = (int)c->n_particles;
+  View& v = h->v;
+  memset(&v, 0, sizeof(v));
+  v.dim = c->dim;
+  v.Q = L.Q;
+  v.nx = c->nx;
+  v.ny = c->ny;
+  v.nz = nz;
+  v.pitch = L.pitch;
+  v.plane = L.plane;
+  v.wall_y = c->wall_y;
+  v.storage = c->storage;
+  for (int s = 0; s < lbm::kMaxOwners; s++) {
+    v.own[s] = reinterpret_cast<int*>(base + L.off_own[s]);
+    v.eps[s] = base + L.off_eps[s];
+  }
+  v.np = np;
+  v.pos = reinterpret_cast<double*>(base + L.off_pos);
+  v.vel = reinterpret_cast<double*>(base + L.off_vel);
+  v.omg = reinterpret_cast<double*>(base + L.off_omg);
+  v.rad = reinterpret_cast<double*>(base + L.off_rad);
+  v.mass = reinterpret_cast<double*>(base + L.off_mass);
+  v.inertia = reinterpret_cast<double*>(base + L.off_inertia);
+  v.ff = reinterpret_cast<double*>(base + L.off_ff);
+  v.tf = reinterpret_cast<double*>(base + L.off_tf);
+  v.fc = reinterpret_cast<double*>(base + L.off_fc);
+  v.lo = reinterpret_cast<int*>(base + L.off_lo);
+  v.bin_of = reinterpret_cast<int*>(base + L.off_binof);
+  for (int d = 0; d < 3; d++) {
+    v.nb[d] = L.nb[d];
+    v.bsz[d] = L.bsz[d];
+  }
+  v.bin_count = reinterpret_cast<int*>(base + L.off_bincount);
+  v.bin_slot = reinterpret_cast<int*>(base + L.off_binslot);
+  v.tau = c->tau;
+  v.omega = 1.0 / c->tau;
+  for (int d = 0; d < 3; d++) {
+    v.gf[d] = (d < c->dim) ? c->body_force[d] : 0.0;
+    v.gs[d] = (d < c->dim) ? c->gravity[d] : 0.0;
+  }
+  v.rho0 = c->rho_fluid;
+  v.kn = c->k_n;
+  const double le = log(c->restitution);
+  v.ln_e = le;
+  v.dem_den = M_PI * M_PI + le * le;
+  v.substeps = c->dem_substeps;
+  for (int q = 0; q < 19; q++) {
+    double cg = 0.0, w = 0.0;
+    if (q < L.Q) {
+      if (c->dim == 2) {
+        cg = lbm::D2Q9::c(q, 0) * v.gf[0] + lbm::D2Q9::c(q, 1) * v.gf[1];
+        w = lbm::D2Q9::w(q);
+      } else {
+        cg = lbm::D3Q19::c(q, 0) * v.gf[0] + lbm::D3Q19::c(q, 1) * v.gf[1] + lbm::D3Q19::c(q, 2) * v.gf[2];
+        w = lbm::D3Q19::w(q);
+      }
+    }
+    v.fq[q] = 3.0 * w * cg;
+  }
+  v.err = reinterpret_cast<int*>(base + L.off_err);
+  v.red = reinterpret_cast<double*>(base + L.off_red);
+  h->f[0] = base + L.off_f[0];
+  h->f[1] = base + L.off_f[1];
+  h->cur = 0;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->smem = L.smem;
+  h->dim = c->dim;
+  h->Q = L.Q;
+  h->np = np;
+  h->N = (long long)c->nx * c->ny * nz;
+  h->stage = reinterpret_cast<double*>(base + L.off_stage);
+  h->stage_bytes = L.stage_bytes;
+
+  // particle state on the host first (derived masses as in the method)
+  st = LBM_IMB_OK;
+  if (np > 0) {
+    double* hbuf = (double*)malloc(sizeof(double) * (size_t)np * 15);
+    if (!hbuf) {
+      delete h;
+      return LBM_IMB_ENOMEM;
+    }
+    double *hp = hbuf, *hv = hbuf + 3 * np, *hw = hbuf + 6 * np, *hr = hbuf + 9 * np,
+           *hm = hbuf + 10 * np, *hi = hbuf + 11 * np;
+    for (int p = 0; p < np; p++) {
+      for (int d = 0; d < 3; d++) {
+        hp[3 * p + d] = c->pos[3 * p + d];
+        hv[3 * p + d] = c->vel ? c->vel[3 * p + d] : 0.0;
+        hw[3 * p + d] = c->omega ? c->omega[3 * p + d] : 0.0;
+      }
+      if (c->dim == 2) {
+        hp[3 * p + 2] = 0.0;
+        hv[3 * p + 2] = 0.0;
+        hw[3 * p + 0] = 0.0;
+        hw[3 * p + 1] = 0.0;
+      }
+      const double R = c->radius[p];
+      hr[p] = R;
+      if (c->dim == 2) {
+        hm[p] = c->density[p] * M_PI * R * R;
+        hi[p] = 0.5 * hm[p] * R * R;
+      } else {
+        hm[p] = c->density[p] * (4.0 / 3.0) * M_PI * R * R * R;
+        hi[p] = 0.4 * hm[p] * R * R;
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMemcpyAsync(v.pos, hp, 24ull * np, cudaMemcpyHostToDevice, h->stream);
+    e = e ? e : cudaMemcpyAsync(v.vel, hv, 24ull * np, cudaMemcpyHostToDevice, h->stream);
+    e = e ? e : cudaMemcpyAsync(v.omg, hw, 24ull * np, cudaMemcpyHostToDevice, h->stream);
+    e = e ? e : cudaMemcpyAsync(v.rad, hr, 8ull * np, cudaMemcpyHostToDevice, h->stream);
+    e = e ? e : cudaMemcpyAsync(v.mass, hm, 8ull * np, cudaMemcpyHostToDevice, h->stream);
+    e = e ? e : cudaMemcpyAsync(v.inertia, hi, 8ull * np, cudaMemcpyHostToDevice, h->stream);
+    e = e ? e : cudaMemsetAsync(v.ff, 0, 24ull * np, h->stream);
+    e = e ? e : cudaMemsetAsync(v.tf, 0, 24ull * np, h->stream);
+    e = e ? e : cudaMemsetAsync(v.fc, 0, 24ull * np, h->stream);
+    e = e ? e : cudaStreamSynchronize(h->stream);
+    free(hbuf);
+    if (e != cudaSuccess) st = LBM_IMB_ECUDA;
+    if (!st && L.smem > 48 * 1024 && lbm::eps_raster_set_attrs(L.smem) != 0) st = LBM_IMB_ECUDA;
+  }
+  if (!st) {
+    cudaError_t e = cudaMemsetAsync(v.err, 0, 16, h->stream);
+    for (int s = 0; s < lbm::kMaxOwners && e == cudaSuccess; s++)
+      e = cudaMemsetAsync(v.own[s], 0xff, (size_t)L.plane * 4, h->stream);
+    if (e == cudaSuccess) {
+      View v0 = view_of(h, 0);
+      lbm::launch_init_equilibrium(v0, h->f[0], h->stream);
+      lbm::launch_init_equilibrium(v0, h->f[1], h->stream);
+      lbm::launch_eps_raster(v0, h->smem, h->stream);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = LBM_IMB_ECUDA;
+  }
+  if (!st) st = read_err(h);
+  if (st) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_step(lbm_imb_t* h, int64_t n) {
+  if (!h || n < 0) return LBM_IMB_EINVAL;
+  if (n == 0) return LBM_IMB_OK;
+  if (!h->graphs_tried) try_capture(h);
+  for (int64_t i = 0; i < n; i++) {
+    if (h->graphs_ok) {
+      if (cudaGraphLaunch(h->graph[h->cur], h->stream) != cudaSuccess) return LBM_IMB_ECUDA;
+    } else {
+      enqueue_step(h, h->cur);
+    }
+    h->cur ^= 1;
+    h->steps++;
+  }
+  return check_cuda(cudaGetLastError());
+}
+
+int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* total_ms) {
+  if (!h || n < 1 || n > 4096 || !kernel_ms || !total_ms) return LBM_IMB_EINVAL;
+  const int K = LBM_IMB_NUM_KERNELS;
+  const size_t ne = (size_t)n * (K + 1);
+  cudaEvent_t* ev = (cudaEvent_t*)calloc(ne, sizeof(cudaEvent_t));
+  if (!ev) return LBM_IMB_ENOMEM;
+  cudaError_t e = cudaSuccess;
+  size_t made = 0;
+  for (; made < ne && e == cudaSuccess; made++) e = cudaEventCreate(&ev[made]);
+  for (int64_t i = 0; i < n && e == cudaSuccess; i++) {
+    View v = view_of(h, h->cur);
+    cudaEvent_t* s = ev + i * (K + 1);
+    cudaEventRecord(s[0], h->stream);
+    lbm::launch_eps_clear(v, true, h->stream);
+    cudaEventRecord(s[1], h->stream);
+    lbm::launch_eps_raster(v, h->smem, h->stream);
+    cudaEventRecord(s[2], h->stream);
+    lbm::launch_collide(v, h->stream);
+    cudaEventRecord(s[3], h->stream);
+    lbm::launch_dem(v, h->stream);
+    e = cudaEventRecord(s[4], h->stream);
+    h->cur ^= 1;
+    h->steps++;
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < K; k++) kernel_ms[k] = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+      cudaEvent_t* s = ev + i * (K + 1);
+      for (int k = 0; k < K; k++) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, s[k], s[k + 1]);
+        kernel_ms[k] += ms;
+      }
+    }
+    float tot = 0.f;
+    cudaEventElapsedTime(&tot, ev[0], ev[(n - 1) * (K + 1) + K]);
+    *total_ms = tot;
+  }
+  for (size_t i = 0; i < made; i++) cudaEventDestroy(ev[i]);
+  free(ev);
+  if (e != cudaSuccess) return LBM_IMB_ECUDA;
+  return read_err(h);
+}
+
+int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches) {
+  if (!h || !launches) return LBM_IMB_EINVAL;
+  *launches = h->np > 0 ? 3 + 4 * h->v.substeps : 1;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_sync(lbm_imb_t* h) {
+  if (!h) return LBM_IMB_EINVAL;
+  return read_err(h);
+}
+
+int lbm_imb_particles(lbm_imb_t* h, double* pos, double* vel, double* omega, double* force,
+                      double* torque, int64_t cap) {
+  if (!h || cap < h->np) return LBM_IMB_EINVAL;
+  const size_t b = 24ull * h->np;
+  cudaError_t e = cudaSuccess;
+  if (h->np > 0) {
+    if (pos) e = e ? e : cudaMemcpyAsync(pos, h->v.pos, b, cudaMemcpyDeviceToHost, h->stream);
+    if (vel) e = e ? e : cudaMemcpyAsync(vel, h->v.vel, b, cudaMemcpyDeviceToHost, h->stream);
+    if (omega) e = e ? e : cudaMemcpyAsync(omega, h->v.omg, b, cudaMemcpyDeviceToHost, h->stream);
+    if (force) e = e ? e : cudaMemcpyAsync(force, h->v.ff, b, cudaMemcpyDeviceToHost, h->stream);
+    if (torque) e = e ? e : cudaMemcpyAsync(torque, h->v.tf, b, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e != cudaSuccess) return LBM_IMB_ECUDA;
+  return read_err(h);
+}
+
+int lbm_imb_set_particles(lbm_imb_t* h, const double* pos, const double* vel, const double* omega,
+                          int64_t n) {
+  if (!h || n != h->np) return LBM_IMB_EINVAL;
+  const size_t b = 24ull * h->np;
+  cudaError_t e = cudaSuccess;
+  if (h->np > 0) {
+    if (pos) e = e ? e : cudaMemcpyAsync(h->v.pos, pos, b, cudaMemcpyHostToDevice, h->stream);
+    if (vel) e = e ? e : cudaMemcpyAsync(h->v.vel, vel, b, cudaMemcpyHostToDevice, h->stream);
+    if (omega) e = e ? e : cudaMemcpyAsync(h->v.omg, omega, b, cudaMemcpyHostToDevice, h->stream);
+    e = e ? e : cudaStreamSynchronize(h->stream);
+  }
+  return check_cuda(e);
+}
+
+int lbm_imb_fields(lbm_imb_t* h, double* rho, double* u, double* eps, int64_t cap, int on_device) {
+  if (!h || cap < h->N) return LBM_IMB_EINVAL;
+  View v = view_of(h, h->cur);
+  if (eps) {
+    // solid fraction at the current particle positions
+    lbm::launch_eps_clear(v, false, h->stream);
+    lbm::launch_eps_raster(v, h->smem, h->stream);
+  }
+  const long long rows = (long long)v.ny * v.nz;
+  if (on_device) {
+    lbm::launch_fields(v, 0, rows, rho, u, eps, h->stream);
+    return check_cuda(cudaGetLastError());
+  }
+  const int comps = 1 + h->dim + 1;
+  const long long chunk = rows_per_chunk(h, comps);
+  cudaError_t e = cudaSuccess;
+  for (long long r0 = 0; r0 < rows && e == cudaSuccess; r0 += chunk) {
+    const long long nr = rows - r0 < chunk ? rows - r0 : chunk;
+    const long long cn = nr * v.nx;
+    double* srho = h->stage;
+    double* su = h->stage + cn;
+    double* seps = su + (long long)h->dim * cn;
+    lbm::launch_fields(v, r0, nr, rho ? srho : nullptr, u ? su : nullptr, eps ? seps : nullptr, h->stream);
+    e = cudaGetLastError();
+    const long long off = r0 * v.nx;
+    if (rho && e == cudaSuccess)
+      e = cudaMemcpyAsync(rho + off, srho, 8 * cn, cudaMemcpyDeviceToHost, h->stream);
+    for (int d = 0; u && d < h->dim && e == cudaSuccess; d++)
+      e = cudaMemcpyAsync(u + d * h->N + off, su + d * cn, 8 * cn, cudaMemcpyDeviceToHost, h->stream);
+    if (eps && e == cudaSuccess)
+      e = cudaMemcpyAsync(eps + off, seps, 8 * cn, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) return LBM_IMB_ECUDA;
+  return read_err(h);
+}
+
+int lbm_imb_get_populations(lbm_imb_t* h, double* f, int64_t cap, int on_device) {
+  if (!h || !f || cap < (int64_t)h->Q * h->N) return LBM_IMB_EINVAL;
+  View v = view_of(h, h->cur);
+  const long long rows = (long long)v.ny * v.nz;
+  if (on_device) {
+    lbm::launch_get_populations(v, h->f[h->cur], 0, rows, f, h->stream);
+    return check_cuda(cudaGetLastError());
+  }
+  const long long chunk = rows_per_chunk(h, h->Q);
+  cudaError_t e = cudaSuccess;
+  for (long long r0 = 0; r0 < rows && e == cudaSuccess; r0 += chunk) {
+    const long long nr = rows - r0 < chunk ? rows - r0 : chunk;
+    const long long cn = nr * v.nx;
+    lbm::launch_get_populations(v, h->f[h->cur], r0, nr, h->stage, h->stream);
+    e = cudaGetLastError();
+    for (int q = 0; q < h->Q && e == cudaSuccess; q++)
+      e = cudaMemcpyAsync(f + q * h->N + r0 * v.nx, h->stage + q * cn, 8 * cn, cudaMemcpyDeviceToHost,
+                          h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  return check_cuda(e);
+}
+
+int lbm_imb_set_populations(lbm_imb_t* h, const double* f, int64_t cap, int on_device) {
+  if (!h || !f || cap < (int64_t)h->Q * h->N) return LBM_IMB_EINVAL;
+  View v = view_of(h, h->cur);
+  const long long rows = (long long)v.ny * v.nz;
+  if (on_device) {
+    lbm::launch_set_populations(v, h->f[h->cur], 0, rows, f, h->stream);
+    return check_cuda(cudaGetLastError());
+  }
+  const long long chunk = rows_per_chunk(h, h->Q);
+  cudaError_t e = cudaSuccess;
+  for (long long r0 = 0; r0 < rows && e == cudaSuccess; r0 += chunk) {
+    const long long nr = rows - r0 < chunk ? rows - r0 : chunk;
+    const long long cn = nr * v.nx;
+    for (int q = 0; q < h->Q && e == cudaSuccess; q++)
+      e = cudaMemcpyAsync(h->stage + q * cn, f + q * h->N + r0 * v.nx, 8 * cn, cudaMemcpyHostToDevice,
+                          h->stream);
+    if (e == cudaSuccess) {
+      lbm::launch_set_populations(v, h->f[h->cur], r0, nr, h->stage, h->stream);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  return check_cuda(e);
+}
+
+int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum, double* particle_momentum) {
+  if (!h) return LBM_IMB_EINVAL;
+  View v = view_of(h, h->cur);
+  lbm::launch_totals(v, h->f[h->cur], h->stream);
+  double red[8];
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(red, v.red, sizeof(red), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return LBM_IMB_ECUDA;
+  if (fluid_mass) *fluid_mass = red[0];
+  for (int d = 0; d < 3; d++) {
+    if (fluid_momentum) fluid_momentum[d] = red[1 + d];
+    if (particle_momentum) particle_momentum[d] = red[4 + d];
+  }
+  if (!isfinite(red[0])) return LBM_IMB_ENONFINITE;
+  return read_err(h);
+}
+
+int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps) {
+  if (!h || !steps) return LBM_IMB_EINVAL;
+  *steps = h->steps;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_destroy(lbm_imb_t* h) {
+  if (!h) return LBM_IMB_EINVAL;
+  if (h->graphs_ok) {
+    cudaGraphExecDestroy(h->graph[0]);
+    cudaGraphExecDestroy(h->graph[1]);
+  }
+  delete h;
+  return LBM_IMB_OK;
+}
+
+const char* lbm_imb_strerror(int s) {
+  switch (s) {
+    case LBM_IMB_OK: return "ok";
+    case LBM_IMB_EINVAL: return "invalid argument or configuration";
+    case LBM_IMB_ENOMEM: return "device block smaller than lbm_imb_required_bytes";
+    case LBM_IMB_ECUDA: return "CUDA runtime error";
+    case LBM_IMB_ETIMEOUT: return "a bounded device wait timed out";
+    case LBM_IMB_ENONFINITE: return "non-finite value found";
+    case LBM_IMB_EUNSUPPORTED: return "configuration outside the implemented limits";
+    case LBM_IMB_EOWNERS: return "a lattice cell was covered by more particles than supported";
+    case LBM_IMB_EBIN: return "a DEM cell-list bin or contact list overflowed";
+    default: return "unknown status";
+  }
+}
+
+const char* lbm_imb_version(void) { return "lbm_imb 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// K4: initial equilibrium, macroscopic fields, population import/export and
+// global sums.  The fields are the moments of the populations the next
+// collision sees (the stored post-collision state pulled one step, as in K2),
+// with the fluid velocity u = sum_i f_i c_i / rho + g_f / 2.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// stored value <-> FP64 population
+__device__ __forceinline__ double stored_to_f(const void* f, int storage, long long i, double w,
+                                              double rho0) {
+  if (storage == LBM_IMB_STORE_F64) return static_cast<const double*>(f)[i];
+  if (storage == LBM_IMB_STORE_F32DEV) return w * rho0 + (double)static_cast<const float*>(f)[i];
+  return w * rho0 + w * (double)__half2float(static_cast<const __half*>(f)[i]);
+}
+__device__ __forceinline__ void f_to_stored(void* f, int storage, long long i, double w, double rho0,
+                                            double val) {
+  if (storage == LBM_IMB_STORE_F64) static_cast<double*>(f)[i] = val;
+  else if (storage == LBM_IMB_STORE_F32DEV) static_cast<float*>(f)[i] = (float)(val - w * rho0);
+  else static_cast<__half*>(f)[i] = __float2half_rn((float)((val - w * rho0) / w));
+}
+
+template <class LAT>
+__global__ void init_eq_kernel(View v, void* f) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= v.plane) return;
+#pragma unroll
+  for (int q = 0; q < LAT::Q; q++)
+    f_to_stored(f, v.storage, q * v.plane + i, LAT::w(q), v.rho0, LAT::w(q) * v.rho0);
+}
+
+// Rows are (y, z) pairs flattened as r = z * ny + y; a launch covers rows
+// [row0, row0 + nrows) and writes dense outputs relative to row0 with
+// component stride nrows * nx (so large fields can be staged in chunks).
+template <class LAT>
+__global__ void fields_kernel(View v, long long row0, long long nrows, double* rho_out,
+                              double* u_out, double* eps_out) {
+  const long long r = row0 + blockIdx.x;
+  const int x = blockIdx.y * blockDim.x + threadIdx.x;
+  if (x >= v.nx) return;
+  const int nx = v.nx, ny = v.ny, nz = v.nz;
+  const int y = (int)(r % ny), z = (int)(r / ny);
+  const long long n = r * v.pitch + x;
+  const long long dense = (r - row0) * nx + x;
+  const long long N = nrows * nx;
+  double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < LAT::Q; q++) {
+    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+    const int sx = (x - cx + nx) % nx;
+    const int sz = (z - cz + nz) % nz;
+    int sy = y - cy;
+    double val;
+    if (v.wall_y && (sy < 0 || sy >= ny)) {
+      val = stored_to_f(v.fsrc, v.storage, opp(q) * v.plane + n, LAT::w(opp(q)), v.rho0);
+    } else {
+      sy = (sy + ny) % ny;
+      val = stored_to_f(v.fsrc, v.storage, q * v.plane + ((long long)sz * ny + sy) * v.pitch + sx,
+                        LAT::w(q), v.rho0);
+    }
+    rho += val;
+    j[0] += val * cx;
+    j[1] += val * cy;
+    j[2] += val * cz;
+  }
+  if (rho_out) rho_out[dense] = rho;
+  if (u_out)
+    for (int d = 0; d < LAT::DIM; d++) u_out[d * N + dense] = j[d] / rho + 0.5 * v.gf[d];
+  if (eps_out) {
+    double es = 0.0;
+    for (int s = 0; s < kMaxOwners; s++) {
+      if (v.own[s][n] < 0) break;
+      es += v.storage == LBM_IMB_STORE_F64 ? static_cast<const double*>(v.eps[s])[n]
+                                           : (double)static_cast<const float*>(v.eps[s])[n];
+    }
+    eps_out[dense] = es < 1.0 ? es : 1.0;
+  }
+}
+
+template <class LAT>
+__global__ void get_pop_kernel(View v, const void* f, long long row0, long long nrows, double* out) {
+  const long long r = row0 + blockIdx.x;
+  const int x = blockIdx.y * blockDim.x + threadIdx.x;
+  if (x >= v.nx) return;
+  const long long n = r * v.pitch + x;
+  const long long dense = (r - row0) * v.nx + x;
+  const long long N = nrows * v.nx;
+#pragma unroll
+  for (int q = 0; q < LAT::Q; q++)
+    out[q * N + dense] = stored_to_f(f, v.storage, q * v.plane + n, LAT::w(q), v.rho0);
+}
+
+template <class LAT>
+__global__ void set_pop_kernel(View v, void* f, long long row0, long long nrows, const double* in) {
+  const long long r = row0 + blockIdx.x;
+  const int x = blockIdx.y * blockDim.x + threadIdx.x;
+  if (x >= v.nx) return;
+  const long long n = r * v.pitch + x;
+  const long long dense = (r - row0) * v.nx + x;
+  const long long N = nrows * v.nx;
+#pragma unroll
+  for (int q = 0; q < LAT::Q; q++)
+    f_to_stored(f, v.storage, q * v.plane + n, LAT::w(q), v.rho0, in[q * N + dense]);
+}
+
+// red[0] = mass, red[1..3] = fluid momentum, red[4..6] = particle momentum
+template <class LAT>
+__global__ void totals_kernel(View v, const void* f) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  double m = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+  if (x < v.nx) {
+    const long long n = ((long long)z * v.ny + y) * v.pitch + x;
+#pragma unroll
+    for (int q = 0; q < LAT::Q; q++) {
+      const double val = stored_to_f(f, v.storage, q * v.plane + n, LAT::w(q), v.rho0);
+      m += val;
+      j0 += val * LAT::c(q, 0);
+      j1 += val * LAT::c(q, 1);
+      j2 += val * LAT::c(q, 2);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_down_sync(0xffffffffu, m, o);
+    j0 += __shfl_down_sync(0xffffffffu, j0, o);
+    j1 += __shfl_down_sync(0xffffffffu, j1, o);
+    j2 += __shfl_down_sync(0xffffffffu, j2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(v.red, m);
+    atomicAdd(v.red + 1, j0);
+    atomicAdd(v.red + 2, j1);
+    atomicAdd(v.red + 3, j2);
+  }
+}
+
+__global__ void particle_momentum_kernel(View v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.np) return;
+  for (int d = 0; d < 3; d++) atomicAdd(v.red + 4 + d, v.mass[i] * v.vel[3 * i + d]);
+}
+
+__global__ void zero_red_kernel(double* red) {
+  if (threadIdx.x < 8) red[threadIdx.x] = 0.0;
+}
+
+void launch_init_equilibrium(const View& v, void* f, cudaStream_t s) {
+  const int T = 256;
+  const long long blocks = (v.plane + T - 1) / T;
+  if (v.dim == 2) init_eq_kernel<D2Q9><<<blocks, T, 0, s>>>(v, f);
+  else init_eq_kernel<D3Q19><<<blocks, T, 0, s>>>(v, f);
+}
+
+static dim3 row_grid(const View& v) { return dim3((v.nx + 127) / 128, v.ny, v.nz); }
+static dim3 chunk_grid(const View& v, long long nrows) { return dim3((unsigned)nrows, (v.nx + 127) / 128, 1); }
+
+void launch_fields(const View& v, long long row0, long long nrows, double* rho, double* u, double* eps,
+                   cudaStream_t s) {
+  if (v.dim == 2) fields_kernel<D2Q9><<<chunk_grid(v, nrows), 128, 0, s>>>(v, row0, nrows, rho, u, eps);
+  else fields_kernel<D3Q19><<<chunk_grid(v, nrows), 128, 0, s>>>(v, row0, nrows, rho, u, eps);
+}
+
+void launch_get_populations(const View& v, const void* f, long long row0, long long nrows, double* out,
+                            cudaStream_t s) {
+  if (v.dim == 2) get_pop_kernel<D2Q9><<<chunk_grid(v, nrows), 128, 0, s>>>(v, f, row0, nrows, out);
+  else get_pop_kernel<D3Q19><<<chunk_grid(v, nrows), 128, 0, s>>>(v, f, row0, nrows, out);
+}
+
+void launch_set_populations(const View& v, void* f, long long row0, long long nrows, const double* in,
+                            cudaStream_t s) {
+  if (v.dim == 2) set_pop_kernel<D2Q9><<<chunk_grid(v, nrows), 128, 0, s>>>(v, f, row0, nrows, in);
+  else set_pop_kernel<D3Q19><<<chunk_grid(v, nrows), 128, 0, s>>>(v, f, row0, nrows, in);
+}
+
+void launch_totals(const View& v, const void* f, cudaStream_t s) {
+  zero_red_kernel<<<1, 32, 0, s>>>(v.red);
+  if (v.dim == 2) totals_kernel<D2Q9><<<row_grid(v), 128, 0, s>>>(v, f);
+  else totals_kernel<D3Q19><<<row_grid(v), 128, 0, s>>>(v, f);
+  if (v.np > 0) particle_momentum_kernel<<<(v.np + 127) / 128, 128, 0, s>>>(v);
+}
+
+}  // namespace lbm

@@ -1,0 +1,109 @@
+// Internal declarations shared by the CUDA translation units of liblbm_imb.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm_imb.h"
+
+namespace lbm {
+
+constexpr int kMaxOwners = LBM_IMB_MAX_OWNERS;
+constexpr int kBinCap = 16;  // particles per DEM cell-list bin
+
+// device error word bits
+enum : int { ERR_OWNERS = 1, ERR_BIN = 2, ERR_NONFINITE = 4, ERR_TIMEOUT = 8 };
+
+// ---------------------------------------------------------------------------
+// Lattice descriptors (interface direction order: rest, then opposite pairs).
+// All loops over directions are unrolled, so every lookup folds to a literal.
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+  static constexpr int Q = 9;
+  static constexpr int DIM = 2;
+  __host__ __device__ static constexpr int c(int q, int d) {
+    constexpr int t[9][3] = {{0, 0, 0}, {1, 0, 0},   {-1, 0, 0},
+                             {0, 1, 0}, {0, -1, 0},  {1, 1, 0},
+                             {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+    return t[q][d];
+  }
+  __host__ __device__ static constexpr double w(int q) {
+    return q == 0 ? 4.0 / 9.0 : (q < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+
+struct D3Q19 {
+  static constexpr int Q = 19;
+  static constexpr int DIM = 3;
+  __host__ __device__ static constexpr int c(int q, int d) {
+    constexpr int t[19][3] = {
+        {0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+        {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+        {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+        {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[q][d];
+  }
+  __host__ __device__ static constexpr double w(int q) {
+    return q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+// opposite direction: pairs (1,2), (3,4), ...
+__host__ __device__ constexpr int opp(int q) {
+  return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Device view of one simulation (passed by value to kernels).
+// ---------------------------------------------------------------------------
+struct View {
+  // lattice geometry
+  int dim, Q, nx, ny, nz, pitch, wall_y, storage;
+  long long plane;  // elements per population plane = pitch * ny * nz
+  // populations: src is read (pull), dst written
+  void* fsrc;
+  void* fdst;
+  // solid-fraction slots; eps element type follows the storage (double for
+  // F64, float otherwise)
+  int* own[kMaxOwners];
+  void* eps[kMaxOwners];
+  // particles (FP64 SoA-of-vec3)
+  int np;
+  double *pos, *vel, *omg, *rad, *mass, *inertia;
+  double *ff, *tf, *fc;  // hydrodynamic force/torque (Eq. 3), contact force
+  int* lo;               // [np*3] origin of the last rasterised bounding box
+  int* bin_of;           // [np] DEM bin of each particle
+  // DEM bins
+  int nb[3];
+  double bsz[3];
+  int* bin_count;  // [nbins]
+  int* bin_slot;   // [nbins * kBinCap]
+  // physics
+  double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
+  double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i
+  int substeps;
+  // device error word
+  int* err;
+  // scratch for reductions (totals)
+  double* red;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (one per kernel family; each in its own translation unit).
+// ---------------------------------------------------------------------------
+void launch_init_equilibrium(const View& v, void* f, cudaStream_t s);
+void launch_eps_clear(const View& v, bool zero_forces, cudaStream_t s);
+void launch_eps_raster(const View& v, int smem_bytes, cudaStream_t s);
+int eps_raster_smem_bytes(int dim, int storage, double rmax);
+int eps_raster_set_attrs(int bytes);
+void launch_collide(const View& v, cudaStream_t s);
+void launch_dem(const View& v, cudaStream_t s);
+void launch_fields(const View& v, long long row0, long long nrows, double* rho, double* u, double* eps,
+                   cudaStream_t s);
+void launch_get_populations(const View& v, const void* f, long long row0, long long nrows, double* out,
+                            cudaStream_t s);
+void launch_set_populations(const View& v, void* f, long long row0, long long nrows, const double* in,
+                            cudaStream_t s);
+void launch_totals(const View& v, const void* f, cudaStream_t s);
+
+}  // namespace lbm

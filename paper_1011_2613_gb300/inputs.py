@@ -84,68 +84,66 @@ def random_directions(rng: np.random.Generator, n: int, dim: int) -> np.ndarray:
 
 
 def rsa_place(rng: np.random.Generator, radii: np.ndarray, box, dim: int, periodic,
-              gap: float = 1.0, wall_gap: float = 1.0, max_tries: int = 200) -> np.ndarray:
-    """Random sequential addition of non-overlapping disks/spheres.
+              gap: float = 1.0, wall_gap: float = 1.0, max_tries: int = 500) -> np.ndarray:
+    """Random sequential addition of non-overlapping disks/spheres, largest
+    first.
 
     ``box`` = (nx, ny, nz) in lattice units (node i sits at coordinate i; the
-    domain spans [-1/2, n-1/2) along each axis).  Surfaces keep at least
-    ``gap`` from each other and ``wall_gap`` from a non-periodic boundary.
-    Returns positions (n,3); raises if the packing cannot be completed.
+    domain spans [-1/2, n-1/2) along each axis; periodic axes wrap [0, n)).
+    Surfaces keep at least ``gap`` from each other and ``wall_gap`` from a
+    non-periodic boundary.  An occupancy grid with cells small enough to hold
+    at most one centre makes each trial a fixed-size neighbourhood lookup.
+    Returns positions (n,3); raises if a particle cannot be placed.
     """
     radii = np.asarray(radii, dtype=np.float64)
     n = len(radii)
-    L = np.array([box[0], box[1], box[2] if dim == 3 else 1], dtype=np.float64)
-    rmax = float(radii.max()) if n else 1.0
-    cs = 2.0 * rmax + gap
-    ncell = np.maximum(1, np.floor(L[:dim] / cs).astype(int))
-    csz = L[:dim] / ncell
-    grid = {}
     pos = np.zeros((n, 3))
-    per = list(periodic)
-    lo = np.zeros(3)
-    hi = np.zeros(3)
-    for d in range(dim):
-        if per[d]:
-            lo[d], hi[d] = 0.0, L[d]
-    offsets = np.array(np.meshgrid(*([range(-1, 2)] * dim), indexing="ij")).reshape(dim, -1).T
-    order = np.argsort(-radii, kind="stable")  # large first
+    if n == 0:
+        return pos
+    L = np.array([box[0], box[1], box[2] if dim == 3 else 1], dtype=np.float64)[:dim]
+    per = np.array(list(periodic)[:dim], dtype=bool)
+    rmin, rmax = float(radii.min()), float(radii.max())
+    h = (2.0 * rmin + gap) / math.sqrt(dim) * 0.999  # at most one centre per cell
+    ncell = np.maximum(1, np.floor(L / h).astype(int))
+    h = L / ncell
+    reach = int(math.ceil((2.0 * rmax + gap) / h.min()))
+    grid = -np.ones(tuple(ncell), dtype=np.int64)
+    offs = np.array(np.meshgrid(*([np.arange(-reach, reach + 1)] * dim), indexing="ij")).reshape(dim, -1).T
+    origin = np.where(per, 0.0, -0.5)
+    order = np.argsort(-radii, kind="stable")
     for idx in order:
         R = radii[idx]
-        for d in range(dim):
-            if not per[d]:
-                lo[d], hi[d] = -0.5 + R + wall_gap, L[d] - 0.5 - R - wall_gap
+        lo = np.where(per, 0.0, -0.5 + R + wall_gap)
+        hi = np.where(per, L, L - 0.5 - R - wall_gap)
+        if np.any(hi <= lo):
+            raise RuntimeError("particle does not fit between the walls")
         placed = False
         for _ in range(max_tries):
-            p = np.zeros(3)
-            p[:dim] = lo[:dim] + rng.random(dim) * (hi[:dim] - lo[:dim])
-            c = np.floor(p[:dim] / csz).astype(int)
-            c = np.minimum(c, ncell - 1)
-            ok = True
-            for off in offsets:
-                cc = c + off
-                skip = False
+            p = lo + rng.random(dim) * (hi - lo)
+            c = np.minimum(((p - origin) / h).astype(int), ncell - 1)
+            cc = c + offs
+            ok_rows = np.ones(len(cc), dtype=bool)
+            for d in range(dim):
+                if per[d]:
+                    cc[:, d] %= ncell[d]
+                else:
+                    ok_rows &= (cc[:, d] >= 0) & (cc[:, d] < ncell[d])
+            cc = cc[ok_rows]
+            if grid[tuple(cc.T)].max() >= 0:
+                js = grid[tuple(cc.T)]
+                js = js[js >= 0]
+                dv = pos[js, :dim] - p
                 for d in range(dim):
                     if per[d]:
-                        cc[d] %= ncell[d]
-                    elif cc[d] < 0 or cc[d] >= ncell[d]:
-                        skip = True
-                if skip:
+                        dv[:, d] -= L[d] * np.round(dv[:, d] / L[d])
+                if np.any((dv * dv).sum(axis=1) < (R + radii[js] + gap) ** 2):
                     continue
-                for j in grid.get(tuple(cc), ()):
-                    dv = pos[j, :dim] - p[:dim]
-                    for d in range(dim):
-                        if per[d]:
-                            dv[d] -= L[d] * np.round(dv[d] / L[d])
-                    if np.dot(dv, dv) < (R + radii[j] + gap) ** 2:
-                        ok = False
-                        break
-                if not ok:
-                    break
-            if ok:
-                pos[idx] = p
-                grid.setdefault(tuple(c), []).append(idx)
-                placed = True
-                break
+            if grid[tuple(c)] >= 0:
+                continue  # cell taken (cannot happen with valid spacing)
+            pos[idx, :dim] = p
+            grid[tuple(c)] = idx
+            placed = True
+            break
         if not placed:
             raise RuntimeError("random sequential addition did not converge")
     return pos

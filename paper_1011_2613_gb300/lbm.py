@@ -1,0 +1,271 @@
+"""Thin ctypes binding over liblbm_imb.so (the C ABI in include/lbm_imb.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies the device memory block (one uint8 tensor per
+simulation) and the CUDA stream.  There is no CPU fallback: if the compiled
+library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm_imb.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EOWNERS, EBIN = 0, -1, -2, -3, -4, -5, -6, -7, -8
+MAX_OWNERS = 4
+
+
+class LbmImbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().lbm_imb_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class Config(C.Structure):
+    """Mirror of ``lbm_imb_config``."""
+
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
+        ("nz", C.c_int32), ("wall_y", C.c_int32), ("storage", C.c_int32), ("tau", C.c_double),
+        ("body_force", C.c_double * 3), ("gravity", C.c_double * 3), ("rho_fluid", C.c_double),
+        ("k_n", C.c_double), ("restitution", C.c_double), ("dem_substeps", C.c_int32),
+        ("reserved0", C.c_int32), ("n_particles", C.c_int64), ("pos", _dp), ("vel", _dp),
+        ("omega", _dp), ("radius", _dp), ("density", _dp),
+    ]
+
+
+def lib():
+    """Load liblbm_imb.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    "liblbm_imb.so is not built; run `python -c \"import __graft_entry__ as g; g.build()\"`")
+            L = C.CDLL(LIB_PATH)
+            L.lbm_imb_required_bytes.restype = C.c_size_t
+            L.lbm_imb_required_bytes.argtypes = [C.POINTER(Config)]
+            L.lbm_imb_init.restype = C.c_int
+            L.lbm_imb_init.argtypes = [C.POINTER(Config), C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]
+            L.lbm_imb_step.restype = C.c_int
+            L.lbm_imb_step.argtypes = [C.c_void_p, C.c_int64]
+            L.lbm_imb_step_profiled.restype = C.c_int
+            L.lbm_imb_step_profiled.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
+            L.lbm_imb_launches_per_step.restype = C.c_int
+            L.lbm_imb_launches_per_step.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+            L.lbm_imb_sync.restype = C.c_int
+            L.lbm_imb_sync.argtypes = [C.c_void_p]
+            L.lbm_imb_particles.restype = C.c_int
+            L.lbm_imb_particles.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_int64]
+            L.lbm_imb_set_particles.restype = C.c_int
+            L.lbm_imb_set_particles.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+            L.lbm_imb_fields.restype = C.c_int
+            L.lbm_imb_fields.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
+            L.lbm_imb_get_populations.restype = C.c_int
+            L.lbm_imb_get_populations.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
+            L.lbm_imb_set_populations.restype = C.c_int
+            L.lbm_imb_set_populations.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
+            L.lbm_imb_totals.restype = C.c_int
+            L.lbm_imb_totals.argtypes = [C.c_void_p, _dp, _dp, _dp]
+            L.lbm_imb_steps_done.restype = C.c_int
+            L.lbm_imb_steps_done.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+            L.lbm_imb_destroy.restype = C.c_int
+            L.lbm_imb_destroy.argtypes = [C.c_void_p]
+            L.lbm_imb_strerror.restype = C.c_char_p
+            L.lbm_imb_strerror.argtypes = [C.c_int]
+            L.lbm_imb_version.restype = C.c_char_p
+            L.lbm_imb_version.argtypes = []
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise LbmImbError(status, where)
+
+
+def _arr(x, n3=False):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a
+
+
+def make_config(cfg) -> tuple[Config, list]:
+    """Build the C struct from a SuspensionConfig-like object.  Returns the
+    struct and the list of numpy arrays it points into (keep it alive)."""
+    keep = []
+    np_ = int(len(cfg.radius))
+
+    def ptr(a):
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        keep.append(a)
+        return a.ctypes.data_as(_dp)
+
+    c = Config()
+    c.struct_size = C.sizeof(Config)
+    c.dim = int(cfg.dim)
+    c.nx, c.ny = int(cfg.nx), int(cfg.ny)
+    c.nz = int(cfg.nz) if int(cfg.dim) == 3 else 1
+    c.wall_y = int(cfg.wall_y)
+    st = getattr(cfg, "storage", "f64")
+    c.storage = _inputs.STORAGE[st] if isinstance(st, str) else int(st)
+    c.tau = float(cfg.tau)
+    for d in range(3):
+        c.body_force[d] = float(np.asarray(cfg.body_force, dtype=np.float64)[d])
+        c.gravity[d] = float(np.asarray(cfg.gravity, dtype=np.float64)[d])
+    c.rho_fluid = float(cfg.rho_fluid)
+    c.k_n = float(cfg.k_n)
+    c.restitution = float(cfg.restitution)
+    c.dem_substeps = int(cfg.dem_substeps)
+    c.n_particles = np_
+    if np_:
+        c.pos = ptr(cfg.pos)
+        c.vel = ptr(cfg.vel)
+        c.omega = ptr(cfg.omega)
+        c.radius = ptr(cfg.radius)
+        c.density = ptr(cfg.density)
+    return c, keep
+
+
+def required_bytes(cfg) -> int:
+    c, _keep = make_config(cfg)
+    return int(lib().lbm_imb_required_bytes(C.byref(c)))
+
+
+class Simulation:
+    """One suspension advanced on the GPU by liblbm_imb.
+
+    ``cfg``: :class:`paper_1011_2613_gb300.inputs.SuspensionConfig`.
+    ``stream``: a ``torch.cuda.Stream`` (a new one by default; its graphs are
+    captured on it)."""
+
+    def __init__(self, cfg, device=None, stream=None):
+        import torch
+
+        L = lib()
+        self.cfg = cfg
+        self.dim = int(cfg.dim)
+        self.shape = (int(cfg.nx), int(cfg.ny), int(cfg.nz) if self.dim == 3 else 1)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        self.Q = 9 if self.dim == 2 else 19
+        self.np = int(len(cfg.radius))
+        self.device = torch.device(device if device is not None else "cuda")
+        c, keep = make_config(cfg)
+        nbytes = int(L.lbm_imb_required_bytes(C.byref(c)))
+        if nbytes == 0:
+            raise LbmImbError(EINVAL, "lbm_imb_required_bytes")
+        self.nbytes = nbytes
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.buf.data_ptr()
+            ptr = (base + 255) // 256 * 256
+            h = C.c_void_p()
+            st = L.lbm_imb_init(C.byref(c), C.c_void_p(ptr), nbytes, C.c_void_p(self.stream.cuda_stream),
+                                C.byref(h))
+        del keep
+        _check(st, "lbm_imb_init")
+        self.h = h
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_imb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _check(lib().lbm_imb_step(self.h, int(n)), "lbm_imb_step")
+
+    def step_profiled(self, n: int):
+        """Run n steps with CUDA events between kernel families; returns
+        (per-family ms dict, total ms)."""
+        k = (C.c_double * 4)()
+        t = C.c_double()
+        _check(lib().lbm_imb_step_profiled(self.h, int(n), k, C.byref(t)), "lbm_imb_step_profiled")
+        names = ("eps_clear", "eps_raster", "collide", "dem")
+        return {nm: float(k[i]) for i, nm in enumerate(names)}, float(t.value)
+
+    def launches_per_step(self) -> int:
+        x = C.c_int()
+        _check(lib().lbm_imb_launches_per_step(self.h, C.byref(x)), "lbm_imb_launches_per_step")
+        return int(x.value)
+
+    def sync(self):
+        _check(lib().lbm_imb_sync(self.h), "lbm_imb_sync")
+
+    def steps_done(self) -> int:
+        s = C.c_int64()
+        _check(lib().lbm_imb_steps_done(self.h, C.byref(s)), "lbm_imb_steps_done")
+        return int(s.value)
+
+    def particles(self, out=None):
+        """dict of (np,3) float64 arrays: pos, vel, omega, force, torque
+        (force/torque = hydrodynamic, Eq. 3, of the last step)."""
+        n3 = 3 * max(self.np, 1)
+        a = out if out is not None else {k: np.zeros(n3) for k in ("pos", "vel", "omega", "force", "torque")}
+        p = [a[k].ctypes.data if a.get(k) is not None else None for k in ("pos", "vel", "omega", "force", "torque")]
+        _check(lib().lbm_imb_particles(self.h, *[C.c_void_p(x) if x else None for x in p], max(self.np, 1)),
+               "lbm_imb_particles")
+        if out is not None:
+            return out
+        return {k: v[: 3 * self.np].reshape(self.np, 3) for k, v in a.items()}
+
+    def set_particles(self, pos=None, vel=None, omega=None):
+        arrs = [None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+                for x in (pos, vel, omega)]
+        _check(lib().lbm_imb_set_particles(self.h, *[None if a is None else C.c_void_p(a.ctypes.data) for a in arrs],
+                                           self.np), "lbm_imb_set_particles")
+
+    def fields(self):
+        """(rho (nz,ny,nx), u (dim,nz,ny,nx), eps (nz,ny,nx)) as numpy."""
+        rho = np.zeros(self.N)
+        u = np.zeros(self.dim * self.N)
+        eps = np.zeros(self.N)
+        _check(lib().lbm_imb_fields(self.h, C.c_void_p(rho.ctypes.data), C.c_void_p(u.ctypes.data),
+                                    C.c_void_p(eps.ctypes.data), self.N, 0), "lbm_imb_fields")
+        nx, ny, nz = self.shape
+        return rho.reshape(nz, ny, nx), u.reshape(self.dim, nz, ny, nx), eps.reshape(nz, ny, nx)
+
+    def fields_device(self, rho, u, eps):
+        """Write the fields into caller-owned float64 CUDA tensors (any may be None)."""
+        ptrs = [C.c_void_p(t.data_ptr()) if t is not None else None for t in (rho, u, eps)]
+        _check(lib().lbm_imb_fields(self.h, *ptrs, self.N, 1), "lbm_imb_fields")
+
+    def populations(self) -> np.ndarray:
+        """Stored post-collision populations as FP64, shape (Q, nz, ny, nx)."""
+        f = np.zeros(self.Q * self.N)
+        _check(lib().lbm_imb_get_populations(self.h, C.c_void_p(f.ctypes.data), f.size, 0),
+               "lbm_imb_get_populations")
+        nx, ny, nz = self.shape
+        return f.reshape(self.Q, nz, ny, nx)
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+        assert f.size == self.Q * self.N
+        _check(lib().lbm_imb_set_populations(self.h, C.c_void_p(f.ctypes.data), f.size, 0),
+               "lbm_imb_set_populations")
+
+    def totals(self):
+        m = C.c_double()
+        jf = (C.c_double * 3)()
+        jp = (C.c_double * 3)()
+        _check(lib().lbm_imb_totals(self.h, C.byref(m), jf, jp), "lbm_imb_totals")
+        return float(m.value), np.array(list(jf)), np.array(list(jp))

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances (FP64 storage): populations 1e-10 relative, particle forces 1e-9
+relative to the largest force; the two sides differ only in rounding order
+(FMA contraction in the collision, atomic summation of forces).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1011_2613_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-10
+FORCE_TOL = 1e-9
+
+
+def lbm():
+    from paper_1011_2613_gb300 import lbm as L
+    return L
+
+
+def fluid_cfg(dim, nx, ny, nz=1, wall_y=0, tau=0.6, g=(0.0, 0.0, 0.0), storage="f64"):
+    return I.SuspensionConfig(dim=dim, nx=nx, ny=ny, nz=nz if dim == 3 else 1, wall_y=wall_y, tau=tau,
+                              body_force=np.asarray(g, dtype=float), gravity=np.zeros(3), rho_fluid=1.0,
+                              k_n=1.0, restitution=0.9, dem_substeps=1, pos=np.zeros((0, 3)),
+                              vel=np.zeros((0, 3)), omega=np.zeros((0, 3)), radius=np.zeros(0),
+                              density=np.zeros(0), storage=storage)
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def force_err(pg, pr, key="force"):
+    scale = max(float(np.max(np.abs(pr[key]))), 1e-300)
+    return float(np.max(np.abs(pg[key] - pr[key]))) / scale
+
+
+def run_pair(cfg, steps, f0=None):
+    gpu = lbm().Simulation(cfg)
+    ref = O.OracleSim(cfg)
+    if f0 is not None:
+        gpu.set_populations(f0)
+        ref.set_populations(f0)
+    gpu.step(steps)
+    ref.step(steps)
+    gpu.sync()
+    return gpu, ref
+
+
+# ---------------------------------------------------------------------------
+# fluid only (beta = 0): pull streaming, walls, body force
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,nx,ny,nz,wall", [(2, 37, 29, 1, 0), (2, 130, 64, 1, 1), (3, 19, 23, 17, 0),
+                                               (3, 33, 20, 9, 1)])
+def test_fluid_parity_nonequilibrium(dim, nx, ny, nz, wall):
+    """Ragged sizes (x not a multiple of the 32-wide warp or 128-wide CTA),
+    non-equilibrium start, body force, periodic and wall boundaries."""
+    cfg = fluid_cfg(dim, nx, ny, nz, wall_y=wall, tau=0.71, g=(3e-5, -2e-5, 1e-5 if dim == 3 else 0))
+    f0 = I.random_populations(np.random.default_rng(5), cfg)
+    gpu, ref = run_pair(cfg, 25, f0)
+    assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
+    rg, ug, _ = gpu.fields()
+    rr, ur, _ = ref.fields()
+    assert np.max(np.abs(rg - rr)) < 1e-12 and np.max(np.abs(ug - ur)) < 1e-12
+
+
+def test_population_roundtrip_exact():
+    cfg = fluid_cfg(3, 21, 10, 7)
+    f0 = I.random_populations(np.random.default_rng(1), cfg)
+    gpu = lbm().Simulation(cfg)
+    gpu.set_populations(f0)
+    assert np.array_equal(gpu.populations(), f0)
+
+
+# ---------------------------------------------------------------------------
+# eps rasterisation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_eps_matches_exact_cell_fractions(dim):
+    rng = np.random.default_rng(11 + dim)
+    if dim == 2:
+        cfg = I.periodic2d_config(nx=96, ny=80, phi=0.2, radius=5.3, seed=4, density_ratio=3.0)
+    else:
+        cfg = I.periodic3d_config(nx=40, ny=36, nz=32, phi=0.15, radius=3.75, seed=4)
+    gpu = lbm().Simulation(cfg)
+    ref = O.OracleSim(cfg)
+    _, _, eg = gpu.fields()
+    _, _, er = ref.fields()
+    assert np.max(np.abs(eg - er)) < 1e-12
+    # covered volume: every particle's cells sum to its area/volume
+    vol = (math.pi * cfg.radius ** 2) if dim == 2 else (4 / 3 * math.pi * cfg.radius ** 3)
+    assert abs(eg.sum() - vol.sum()) < 1e-9 * vol.sum()
+    del rng
+
+
+def test_eps_two_owner_cells_and_wrap():
+    """Disks 0.1 lu apart share cells; one straddles the periodic seam."""
+    cfg = I.SuspensionConfig(dim=2, nx=40, ny=32, nz=1, wall_y=0, tau=0.8, body_force=np.zeros(3),
+                             gravity=np.zeros(3), rho_fluid=1.0, k_n=10.0, restitution=0.9, dem_substeps=1,
+                             pos=np.array([[8.0, 12.0, 0], [14.5, 12.3, 0], [0.4, 25.7, 0]]),
+                             vel=np.zeros((3, 3)), omega=np.zeros((3, 3)), radius=np.array([3.2, 3.2, 4.1]),
+                             density=np.full(3, 5.0))
+    gpu = lbm().Simulation(cfg)
+    ref = O.OracleSim(cfg)
+    _, _, eg = gpu.fields()
+    _, _, er = ref.fields()
+    assert np.max(np.abs(eg - er)) < 1e-13
+    assert ref.owners()[0].max() == 2
+
+
+# ---------------------------------------------------------------------------
+# coupled LB-IMB-DEM
+# ---------------------------------------------------------------------------
+def test_config1_1000_steps():
+    """D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6,
+    1000 steps from rest: the parity target."""
+    cfg = I.config1()
+    gpu, ref = run_pair(cfg, 1000)
+    assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
+    pg, pr = gpu.particles(), ref.particles()
+    assert force_err(pg, pr) < FORCE_TOL
+    assert force_err(pg, pr, "torque") < FORCE_TOL or np.max(np.abs(pr["torque"])) < 1e-14
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) < 1e-9
+    assert np.max(np.abs(pg["vel"] - pr["vel"])) < 1e-12
+
+
+def test_periodic_2d_moving_particles_with_contacts():
+    """Fast disks in a dense periodic box collide within the run."""
+    cfg = I.periodic2d_config(nx=100, ny=72, phi=0.25, radius=4.0, seed=9, v0=0.03, density_ratio=4.0)
+    gpu, ref = run_pair(cfg, 150)
+    pg, pr = gpu.particles(), ref.particles()
+    assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
+    assert force_err(pg, pr) < FORCE_TOL
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) < 1e-9
+
+
+def test_spinning_particles_torque_3d():
+    cfg = I.periodic3d_config(nx=28, ny=30, nz=26, phi=0.1, radius=3.75, seed=3, v0=0.01)
+    cfg.omega = 0.003 * np.random.default_rng(2).standard_normal((cfg.n_particles, 3))
+    gpu, ref = run_pair(cfg, 40)
+    pg, pr = gpu.particles(), ref.particles()
+    assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
+    assert force_err(pg, pr) < FORCE_TOL
+    assert force_err(pg, pr, "torque") < FORCE_TOL
+    assert np.max(np.abs(pg["omega"] - pr["omega"])) < 1e-12
+
+
+def test_config3_shape_channel_3d():
+    """Cut-down config 3 (D3Q19, walls in y, spheres R=3.75, ratio 1000)."""
+    cfg = I.config3_scaled(nx=40, ny=48, nz=36)
+    gpu, ref = run_pair(cfg, 30)
+    pg, pr = gpu.particles(), ref.particles()
+    assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
+    assert force_err(pg, pr) < FORCE_TOL
+    assert force_err(pg, pr, "torque") < FORCE_TOL
+
+
+def test_momentum_conserved_on_gpu():
+    cfg = I.periodic3d_config(nx=24, ny=24, nz=24, phi=0.12, radius=3.0, seed=8, v0=0.02, gs=0.0)
+    gpu = lbm().Simulation(cfg)
+    m0, j0, p0 = gpu.totals()
+    gpu.step(20)
+    m1, j1, p1 = gpu.totals()
+    scale = np.abs(p0).sum() + 1e-300
+    assert abs(m1 - m0) < 1e-12 * m0
+    assert np.max(np.abs((j1 + p1) - (j0 + p0))) < 1e-11 * max(scale, 1.0)
+
+
+def test_error_on_too_many_owners():
+    """Four particles stacked on one point exceed nothing; five do."""
+    pos = np.tile([[10.0, 10.0, 0.0]], (5, 1)) + np.array([[0, 0, 0], [0.01, 0, 0], [0, 0.01, 0],
+                                                            [0.01, 0.01, 0], [0.02, 0, 0]])
+    cfg = I.SuspensionConfig(dim=2, nx=24, ny=24, nz=1, wall_y=0, tau=0.8, body_force=np.zeros(3),
+                             gravity=np.zeros(3), rho_fluid=1.0, k_n=10.0, restitution=0.9, dem_substeps=1,
+                             pos=pos, vel=np.zeros((5, 3)), omega=np.zeros((5, 3)), radius=np.full(5, 2.0),
+                             density=np.full(5, 2.0))
+    L = lbm()
+    with pytest.raises(L.LbmImbError) as ei:
+        L.Simulation(cfg)
+    assert ei.value.status == L.EOWNERS
+    L.Simulation(cfg.replace(pos=pos[:4], vel=np.zeros((4, 3)), omega=np.zeros((4, 3)),
+                             radius=np.full(4, 2.0), density=np.full(4, 2.0)))
+
+
+# ---------------------------------------------------------------------------
+# reduced-precision storage: error reported against FP64, bounded loosely
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,tol_u,tol_f", [("f32dev", 1e-4, 1e-3), ("f16dev", 3e-2, 3e-2)])
+def test_reduced_storage_error(storage, tol_u, tol_f):
+    cfg = I.config3_scaled(nx=40, ny=48, nz=36)
+    ref = lbm().Simulation(cfg)
+    red = lbm().Simulation(cfg.replace(storage=storage))
+    ref.step(40)
+    red.step(40)
+    _, u64, _ = ref.fields()
+    _, ulo, _ = red.fields()
+    l2 = float(np.linalg.norm(ulo - u64) / np.linalg.norm(u64))
+    p64, plo = ref.particles(), red.particles()
+    ferr = force_err(plo, p64)
+    m64 = ref.totals()[0]
+    mlo = red.totals()[0]
+    print(f"{storage}: velocity L2 rel {l2:.2e}, force rel {ferr:.2e}, mass drift {abs(mlo - m64) / m64:.2e}")
+    assert l2 < tol_u and ferr < tol_f and abs(mlo - m64) / m64 < 1e-5
