@@ -192,6 +192,27 @@ int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum,
 /* Steps taken since init. */
 int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps);
 
+/* ---- standalone DEM contact forces (Eqs. 4-5) ----
+ * The cell-list contact kernel of the time step, callable on its own: for n
+ * particles (device arrays pos[n][3], vel[n][3], radius[n], mass[n]) in a
+ * lattice of extent[3] nodes (extent[2] = 1 in 2D; periodic except along y
+ * when wall_y = 1, where the walls at y = -1/2 and extent[1] - 1/2 also
+ * push), write the frictionless spring-dashpot contact force on every
+ * particle to fc[n][3] (device).  Pairs are summed in ascending partner id,
+ * then the wall terms.  rmax bounds every radius (it sizes the bins; a
+ * larger radius is reported as LBM_IMB_EBIN).  Needs a caller-owned device
+ * workspace of lbm_imb_dem_workspace_bytes bytes (256-byte aligned; the DEM
+ * bins).  The call is enqueued on `stream` (a cudaStream_t) and then
+ * synchronises it to report LBM_IMB_EBIN (a bin or contact list overflowed,
+ * or a radius above rmax). */
+size_t lbm_imb_dem_workspace_bytes(int32_t dim, const int32_t* extent, int32_t wall_y,
+                                   int64_t n, double rmax);
+int lbm_imb_dem_forces(int32_t dim, const int32_t* extent, int32_t wall_y, int64_t n,
+                       double rmax, const double* pos, const double* vel,
+                       const double* radius, const double* mass, double k_n,
+                       double restitution, double* fc, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */
 int lbm_imb_destroy(lbm_imb_t* h);

@@ -375,6 +375,13 @@ static void dem_contacts(int dim, const int Ld[3], int wall_y, int np,
   }
 }
 
+/* exported for tests: contact forces of the current state */
+void oracle_dem_contacts(int dim, const int* Ld, int wall_y, int np,
+                         const double* pos, const double* vel, const double* rad,
+                         const double* mass, double kn, double e, double* fc) {
+  dem_contacts(dim, Ld, wall_y, np, pos, vel, rad, mass, kn, e, fc);
+}
+
 /* Advance particles by one lattice time step given hydrodynamic force ff and
  * torque tf (reading R7).  fc_out receives the contact force of the last
  * sub-step. */

@@ -58,6 +58,9 @@ def _load():
             lib.oracle_dem_advance.restype = None
             lib.oracle_dem_advance.argtypes = [C.c_int, _ip, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
                                                _dp, _dp, _dp, C.c_double, C.c_double, C.c_int, _dp]
+            lib.oracle_dem_contacts.restype = None
+            lib.oracle_dem_contacts.argtypes = [C.c_int, _ip, C.c_int, C.c_int, _dp, _dp, _dp, _dp, C.c_double,
+                                                C.c_double, _dp]
             lib.oracle_create.restype = C.c_void_p
             lib.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp,
                                           C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
@@ -138,6 +141,16 @@ def dem_advance(dim, n, wall_y, pos, vel, omg, rad, mass, inertia, ff, tf, gs, k
     _load().oracle_dem_advance(dim, Ld, int(wall_y), np_, _p(pos), _p(vel), _p(omg), _p(_f64(rad)),
                                _p(_f64(mass)), _p(_f64(inertia)), _p(_f64(ff)), _p(_f64(tf)),
                                _p(_f64(gs)), kn, e, substeps, _p(fc))
+    return fc[: 3 * np_].reshape(np_, 3)
+
+
+def dem_contacts(dim, n, wall_y, pos, vel, rad, mass, kn, e):
+    """Contact forces (np,3) of the given state (Eqs. 4-5 with reading R7)."""
+    np_ = len(rad)
+    Ld = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    fc = np.zeros(3 * max(np_, 1))
+    _load().oracle_dem_contacts(dim, Ld, int(wall_y), np_, _p(_f64(pos)), _p(_f64(vel)), _p(_f64(rad)),
+                                _p(_f64(mass)), kn, e, _p(fc))
     return fc[: 3 * np_].reshape(np_, 3)
 
 

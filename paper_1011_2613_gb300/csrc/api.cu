@@ -71,20 +71,9 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   for (int64_t p = 0; p < c->n_particles; p++) rmax = c->radius[p] > rmax ? c->radius[p] : rmax;
   L->rmax = rmax;
   const int ext[3] = {c->nx, c->ny, nz};
-  for (int d = 0; d < 3; d++) {
-    L->nb[d] = 1;
-    L->bsz[d] = (double)ext[d];
-    if (d < c->dim && rmax > 0.0) {
-      // a periodic axis must be wide enough that a particle cannot meet its
-      // own image
-      const bool periodic = !(d == 1 && c->wall_y);
-      if (periodic && ext[d] < 2.0 * rmax + 2.0) return LBM_IMB_EUNSUPPORTED;
-      int nb = (int)floor(ext[d] / (2.0 * rmax));
-      if (nb < 1) nb = 1;
-      L->nb[d] = nb;
-      L->bsz[d] = (double)ext[d] / nb;
-    }
-  }
+  st = lbm::dem_bin_geometry(c->dim, ext, c->wall_y, rmax, L->nb, L->bsz);
+  if (st) return st;
+  L->rmax = rmax;
   L->smem = 0;
   if (c->n_particles > 0) {
     if ((c->dim == 3 && rmax > 12.0) || (c->dim == 2 && rmax > 29.0)) return LBM_IMB_EUNSUPPORTED;
@@ -274,6 +263,7 @@ int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cud
   }
   v.bin_count = reinterpret_cast<int*>(base + L.off_bincount);
   v.bin_slot = reinterpret_cast<int*>(base + L.off_binslot);
+  v.rmax_bins = L.rmax;
   v.tau = c->tau;
   v.omega = 1.0 / c->tau;
   for (int d = 0; d < 3; d++) {
@@ -618,6 +608,96 @@ const char* lbm_imb_strerror(int s) {
     case LBM_IMB_EBIN: return "a DEM cell-list bin or contact list overflowed";
     default: return "unknown status";
   }
+}
+
+// ---- standalone DEM contact forces ----
+namespace {
+struct DemWs {
+  size_t off_err, off_binof, off_count, off_slot, total;
+  int nb[3];
+  double bsz[3];
+};
+int dem_ws_layout(int32_t dim, const int32_t* extent, int32_t wall_y, int64_t n, double rmax, DemWs* w) {
+  if ((dim != 2 && dim != 3) || !extent || n < 0 || n > (1ll << 30) || !(rmax > 0.0)) return LBM_IMB_EINVAL;
+  if (wall_y != 0 && wall_y != 1) return LBM_IMB_EINVAL;
+  int ext[3] = {extent[0], extent[1], dim == 3 ? extent[2] : 1};
+  for (int d = 0; d < 3; d++)
+    if (ext[d] < 1) return LBM_IMB_EINVAL;
+  int st = lbm::dem_bin_geometry(dim, ext, wall_y, rmax, w->nb, w->bsz);
+  if (st) return st;
+  const size_t nbins = (size_t)w->nb[0] * w->nb[1] * w->nb[2];
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  w->off_err = take(16);
+  w->off_binof = take((size_t)(n > 0 ? n : 1) * 4);
+  w->off_count = take(nbins * 4);
+  w->off_slot = take(nbins * lbm::kBinCap * 4);
+  w->total = o;
+  return LBM_IMB_OK;
+}
+}  // namespace
+
+size_t lbm_imb_dem_workspace_bytes(int32_t dim, const int32_t* extent, int32_t wall_y, int64_t n, double rmax) {
+  DemWs w;
+  if (dem_ws_layout(dim, extent, wall_y, n, rmax, &w) != LBM_IMB_OK) return 0;
+  return w.total;
+}
+
+int lbm_imb_dem_forces(int32_t dim, const int32_t* extent, int32_t wall_y, int64_t n, double rmax,
+                       const double* pos, const double* vel, const double* radius, const double* mass,
+                       double k_n, double restitution, double* fc, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+  if (n > 0 && (!pos || !vel || !radius || !mass || !fc)) return LBM_IMB_EINVAL;
+  if (!workspace || ((uintptr_t)workspace) % kAlign) return LBM_IMB_EINVAL;
+  if (!(k_n >= 0.0) || !(restitution > 0.0 && restitution <= 1.0)) return LBM_IMB_EINVAL;
+  if (n == 0) return LBM_IMB_OK;
+  DemWs w;
+  int st = dem_ws_layout(dim, extent, wall_y, n, rmax, &w);
+  if (st) return st;
+  if (workspace_bytes < w.total) return LBM_IMB_ENOMEM;
+  unsigned char* base = static_cast<unsigned char*>(workspace);
+  View v;
+  memset(&v, 0, sizeof(v));
+  v.dim = dim;
+  v.nx = extent[0];
+  v.ny = extent[1];
+  v.nz = dim == 3 ? extent[2] : 1;
+  v.wall_y = wall_y;
+  v.np = (int)n;
+  v.pos = const_cast<double*>(pos);
+  v.vel = const_cast<double*>(vel);
+  v.rad = const_cast<double*>(radius);
+  v.mass = const_cast<double*>(mass);
+  v.fc = fc;
+  v.err = reinterpret_cast<int*>(base + w.off_err);
+  v.bin_of = reinterpret_cast<int*>(base + w.off_binof);
+  v.bin_count = reinterpret_cast<int*>(base + w.off_count);
+  v.bin_slot = reinterpret_cast<int*>(base + w.off_slot);
+  for (int d = 0; d < 3; d++) {
+    v.nb[d] = w.nb[d];
+    v.bsz[d] = w.bsz[d];
+  }
+  v.kn = k_n;
+  const double le = log(restitution);
+  v.ln_e = le;
+  v.dem_den = M_PI * M_PI + le * le;
+  v.substeps = 1;
+  v.rmax_bins = rmax;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(v.err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    lbm::launch_dem_contacts(v, s);
+    e = cudaGetLastError();
+  }
+  int bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, v.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return LBM_IMB_ECUDA;
+  return map_err(bits);
 }
 
 const char* lbm_imb_version(void) { return "lbm_imb 0.1 (sm_103a)"; }

@@ -36,6 +36,7 @@ __global__ void dem_bin_kernel(View v) {
   for (int d = 0; d < v.dim; d++) b[d] = bin_coord(v.pos[3 * p + d], d, v);
   const int bin = (b[2] * v.nb[1] + b[1]) * v.nb[0] + b[0];
   v.bin_of[p] = bin;
+  if (v.rad[p] > v.rmax_bins) atomicOr(v.err, ERR_BIN);  // bins too small for it
   const int slot = atomicAdd(v.bin_count + bin, 1);
   if (slot < kBinCap) v.bin_slot[bin * kBinCap + slot] = p;
   else atomicOr(v.err, ERR_BIN);
@@ -174,17 +175,41 @@ __global__ void dem_integrate_kernel(View v, double dt) {
   for (int d = 0; d < 3; d++) v.omg[3 * i + d] += v.tf[3 * i + d] / I * dt;
 }
 
-void launch_dem(const View& v, cudaStream_t s) {
+void launch_dem_contacts(const View& v, cudaStream_t s) {
   if (v.np <= 0) return;
   const int nbins = v.nb[0] * v.nb[1] * v.nb[2];
   const int T = 128;
+  dem_zero_bins_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(v.bin_count, nbins);
+  dem_bin_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
+  dem_contact_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
+}
+
+void launch_dem(const View& v, cudaStream_t s) {
+  if (v.np <= 0) return;
+  const int T = 128;
   const double dt = 1.0 / v.substeps;
   for (int k = 0; k < v.substeps; k++) {
-    dem_zero_bins_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(v.bin_count, nbins);
-    dem_bin_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
-    dem_contact_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
+    launch_dem_contacts(v, s);
     dem_integrate_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v, dt);
   }
+}
+
+// bins of side >= 2 rmax along each axis of the domain (1 bin on an axis
+// shorter than that); returns 0, or a negative status
+int dem_bin_geometry(int dim, const int* ext, int wall_y, double rmax, int nb[3], double bsz[3]) {
+  for (int d = 0; d < 3; d++) {
+    nb[d] = 1;
+    bsz[d] = (double)ext[d];
+    if (d < dim && rmax > 0.0) {
+      const bool periodic = !(d == 1 && wall_y);
+      if (periodic && ext[d] < 2.0 * rmax + 2.0) return LBM_IMB_EUNSUPPORTED;
+      int n = (int)floor(ext[d] / (2.0 * rmax));
+      if (n < 1) n = 1;
+      nb[d] = n;
+      bsz[d] = (double)ext[d] / n;
+    }
+  }
+  return 0;
 }
 
 }  // namespace lbm

@@ -78,6 +78,7 @@ struct View {
   double bsz[3];
   int* bin_count;  // [nbins]
   int* bin_slot;   // [nbins * kBinCap]
+  double rmax_bins;  // largest radius the bins were sized for
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i
@@ -98,6 +99,8 @@ int eps_raster_smem_bytes(int dim, int storage, double rmax);
 int eps_raster_set_attrs(int bytes);
 void launch_collide(const View& v, cudaStream_t s);
 void launch_dem(const View& v, cudaStream_t s);
+void launch_dem_contacts(const View& v, cudaStream_t s);
+int dem_bin_geometry(int dim, const int* ext, int wall_y, double rmax, int nb[3], double bsz[3]);
 void launch_fields(const View& v, long long row0, long long nrows, double* rho, double* u, double* eps,
                    cudaStream_t s);
 void launch_get_populations(const View& v, const void* f, long long row0, long long nrows, double* out,

@@ -82,6 +82,13 @@ def lib():
             L.lbm_imb_totals.argtypes = [C.c_void_p, _dp, _dp, _dp]
             L.lbm_imb_steps_done.restype = C.c_int
             L.lbm_imb_steps_done.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+            L.lbm_imb_dem_workspace_bytes.restype = C.c_size_t
+            L.lbm_imb_dem_workspace_bytes.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int64,
+                                                      C.c_double]
+            L.lbm_imb_dem_forces.restype = C.c_int
+            L.lbm_imb_dem_forces.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int64, C.c_double,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                             C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
             L.lbm_imb_destroy.restype = C.c_int
             L.lbm_imb_destroy.argtypes = [C.c_void_p]
             L.lbm_imb_strerror.restype = C.c_char_p
@@ -269,3 +276,27 @@ class Simulation:
         jp = (C.c_double * 3)()
         _check(lib().lbm_imb_totals(self.h, C.byref(m), jf, jp), "lbm_imb_totals")
         return float(m.value), np.array(list(jf)), np.array(list(jp))
+
+
+def dem_forces(dim, extent, wall_y, pos, vel, radius, mass, k_n, restitution, rmax=None, stream=None):
+    """Contact forces (Eqs. 4-5) of particles held in float64 CUDA tensors
+    (pos/vel (n,3), radius/mass (n,)); returns a new (n,3) CUDA tensor.  The
+    workspace is a torch uint8 tensor sized by lbm_imb_dem_workspace_bytes."""
+    import torch
+
+    n = int(radius.numel())
+    rmax = float(radius.max().item()) if rmax is None else float(rmax)
+    ext = (C.c_int32 * 3)(*[int(x) for x in (list(extent) + [1, 1])[:3]])
+    nb = int(lib().lbm_imb_dem_workspace_bytes(int(dim), ext, int(wall_y), n, rmax))
+    if nb == 0:
+        raise LbmImbError(EINVAL, "lbm_imb_dem_workspace_bytes")
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=radius.device)
+    wp = (ws.data_ptr() + 255) // 256 * 256
+    fc = torch.empty((n, 3), dtype=torch.float64, device=radius.device)
+    s = stream if stream is not None else torch.cuda.current_stream(radius.device)
+    st = lib().lbm_imb_dem_forces(int(dim), ext, int(wall_y), n, rmax, C.c_void_p(pos.data_ptr()),
+                                  C.c_void_p(vel.data_ptr()), C.c_void_p(radius.data_ptr()),
+                                  C.c_void_p(mass.data_ptr()), float(k_n), float(restitution),
+                                  C.c_void_p(fc.data_ptr()), C.c_void_p(wp), nb, C.c_void_p(s.cuda_stream))
+    _check(st, "lbm_imb_dem_forces")
+    return fc
