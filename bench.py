@@ -58,6 +58,9 @@ WORKLOADS = {
     "cfg2": dict(make=lambda seed: I.config2(seed=seed),
                  name="D2Q9 8192x32768 periodic, ~267k disks R=4 phi=0.05, density ratio log-uniform "
                       "[2.5,1500], tau=0.55"),
+    "cfg3s": dict(make=lambda seed: I.config3_scaled(nx=192, ny=384, nz=192, seed=seed),
+                  name="D3Q19 192x384x192 channel (walls y), config-3 solid fraction, spheres R=3.75, "
+                       "density ratio 1000 (profiling case)"),
     "cfg1": dict(make=lambda seed: I.config1(seed=seed),
                  name="D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6, tau=0.6"),
 }
@@ -258,7 +261,7 @@ def run_ours(args):
     wl = WORKLOADS[args.workload]
     # weak scaling: every rank steps its own independent suspension
     cfg = wl["make"](3 + rank)
-    cfg.storage = "f64"
+    cfg.storage = args.storage
 
     sim = L.Simulation(cfg)
     sim.step(args.warmup)
@@ -309,7 +312,7 @@ def run_ours(args):
                "path": "lbm_imb_set_particles -> lbm_imb_step(1) -> lbm_imb_particles, pinned host buffers"}
 
     variants = {}
-    if not args.no_variants and rank == 0:
+    if not args.no_variants and rank == 0 and cfg.storage == "f64":
         steps_done = args.warmup + 2 * args.steps + (args.steps if e2e else 0)
         for st in ("f32dev", "f16dev"):
             try:
@@ -327,13 +330,15 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "storage": "f64", "nodes": cfg.n_nodes,
-                       "particles": cfg.n_particles, "l2": "inputs larger than L2 (two FP64 lattices, "
-                       f"{2 * 19 * 8 * cfg.n_nodes / 1e9:.1f} GB)", "graph": "CUDA graph per step"},
+            "vs_baseline": None, "dtype": {"f64": "f64", "f32dev": "f32", "f16dev": "f32"}[cfg.storage],
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "storage": cfg.storage, "nodes": cfg.n_nodes,
+                       "particles": cfg.n_particles, "l2": "inputs larger than L2 (two lattices, "
+                       f"{2 * (19 if cfg.dim == 3 else 9) * {'f64': 8, 'f32dev': 4, 'f16dev': 2}[cfg.storage] * cfg.n_nodes / 1e9:.1f} GB)", "graph": "CUDA graph per step"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": "collide_kernel<D3Q19,F64>", "bytes_per_lup": bpl,
+                         "kernel": f"collide_kernel<{'D3Q19' if cfg.dim == 3 else 'D2Q9'},{cfg.storage}>",
+                         "bytes_per_lup": bpl,
                          "owned_fraction": fo, "peak_src": peaks["src"]},
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "profiled_ms_per_step": tot / args.steps,
@@ -355,6 +360,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -213,6 +213,26 @@ int lbm_imb_dem_forces(int32_t dim, const int32_t* extent, int32_t wall_y, int64
                        double restitution, double* fc, void* workspace,
                        size_t workspace_bytes, void* stream);
 
+/* lbm_imb_dem_forces without a workspace argument, for callers that cannot
+ * allocate device memory: code running with the device memory already
+ * handed out to another allocator, or hosts that forbid allocation after
+ * start-up (no cudaMalloc, cudaFree or allocating library call happens here).
+ * There is no counterpart in the paper; this only changes where the scratch
+ * lives.  The cell-list bins are taken from a fixed 8 MiB array compiled into
+ * the library (every device that loads the library keeps it until the process
+ * exits); a problem whose bins need more (error word + 4 B per particle +
+ * 68 B per bin, each rounded up to 256 B) is rejected with
+ * LBM_IMB_EUNSUPPORTED.  The first call on a device looks up the array's
+ * device address for that device, so make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU (on
+ * different streams or threads) race and give wrong forces.  Same arguments,
+ * results and errors as lbm_imb_dem_forces otherwise. */
+int lbm_imb_dem_forces_static(int32_t dim, const int32_t* extent, int32_t wall_y,
+                              int64_t n, double rmax, const double* pos,
+                              const double* vel, const double* radius,
+                              const double* mass, double k_n, double restitution,
+                              double* fc, void* stream);
+
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */
 int lbm_imb_destroy(lbm_imb_t* h);

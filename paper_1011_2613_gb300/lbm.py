@@ -89,6 +89,10 @@ def lib():
             L.lbm_imb_dem_forces.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int64, C.c_double,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                              C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.lbm_imb_dem_forces_static.restype = C.c_int
+            L.lbm_imb_dem_forces_static.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int64,
+                                                    C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                    C.c_double, C.c_double, C.c_void_p, C.c_void_p]
             L.lbm_imb_destroy.restype = C.c_int
             L.lbm_imb_destroy.argtypes = [C.c_void_p]
             L.lbm_imb_strerror.restype = C.c_char_p
