@@ -192,6 +192,49 @@ int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum,
 /* Steps taken since init. */
 int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps);
 
+/* ---- batches of independent suspensions ----
+ * A batch advances n independent suspensions (same dim and storage; any
+ * lattice sizes, particle counts, densities; dem_substeps = 1) by one
+ * cooperative persistent kernel launch per time step, replayed from a CUDA
+ * graph.  Inside the launch the CTAs walk shared work lists (particles for
+ * eps and DEM, collision tiles of tile_x x 128/tile_x nodes) and meet at
+ * grid barriers between the phases of the step; each member evolves exactly
+ * as it would alone (up to the order of the FP64 force atomics).  A barrier
+ * wait that does not complete within its poll limit makes the launch end and
+ * the next synchronising call return LBM_IMB_ETIMEOUT.  Not in the paper: a
+ * throughput form for many small suspensions that would underfill the GPU
+ * one at a time. */
+
+/* Device bytes for the batch (0 if a config is invalid). */
+size_t lbm_imb_batch_required_bytes(const lbm_imb_config* cfgs, int n);
+
+/* Initialise a batch of n (1..256) configs in the caller's device block.
+ * tile_x: 32, 64 or 128 (0 = 128); blocks_per_sm: CTAs per SM of the
+ * persistent grid (0 = as many as fit).  The batch handle steps with
+ * lbm_imb_step / lbm_imb_step_profiled (whose time goes to the
+ * LBM_IMB_K_COLLIDE slot) and is released with lbm_imb_destroy. */
+int lbm_imb_batch_init(const lbm_imb_config* cfgs, int n, int tile_x, int blocks_per_sm,
+                       void* dev_buf, size_t bytes, void* cuda_stream, lbm_imb_t** out);
+
+/* Handle of member i for the accessors (lbm_imb_particles, _fields,
+ * _get/_set_populations, _totals, _set_particles).  It shares the batch's
+ * memory and stream, cannot be stepped or destroyed on its own, and lives as
+ * long as the batch. */
+int lbm_imb_batch_member(lbm_imb_t* batch, int i, lbm_imb_t** member);
+
+/* Number of members (1 for a single suspension). */
+int lbm_imb_batch_size(lbm_imb_t* h, int* n);
+
+/* Change / read the launch shape of a batch (tile width, CTAs per SM;
+ * the grid actually used is returned in *grid). */
+int lbm_imb_batch_set_launch(lbm_imb_t* batch, int tile_x, int blocks_per_sm);
+int lbm_imb_batch_get_launch(lbm_imb_t* batch, int* tile_x, int* grid);
+
+/* Test hook for the barrier timeout path: poll limit of every barrier wait
+ * (default 2^25 polls of ~64 ns) and a number of arrivals the barriers wait
+ * for beyond the grid (0 in normal use; > 0 makes every wait run out). */
+int lbm_imb_batch_set_barrier_test(lbm_imb_t* batch, int64_t spin_limit, int phantom_arrivals);
+
 /* ---- standalone DEM contact forces (Eqs. 4-5) ----
  * The cell-list contact kernel of the time step, callable on its own: for n
  * particles (device arrays pos[n][3], vel[n][3], radius[n], mass[n]) in a

@@ -1,9 +1,9 @@
 """Compile liblbm_imb.so (the CUDA library) in-tree with nvcc for sm_103a.
 
 Each translation unit compiles in parallel into ``_build/``; the shared
-library lands next to this file.  ``k_dem.cu`` and ``k_fields.cu`` are built
-without FMA contraction so that the DEM and diagnostic arithmetic is the
-plain IEEE sequence of the source.
+library lands next to this file.  ``k_fields.cu`` (diagnostics) is built
+without FMA contraction; the DEM code guards its own multiply-add sequences
+with non-fusing intrinsics.
 """
 from __future__ import annotations
 
@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "liblbm_imb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-Xptxas", "-warn-spills"]
-NO_FMA = {"k_dem.cu", "k_fields.cu"}
+NO_FMA = {"k_fields.cu"}
 
 
 def nvcc() -> str:

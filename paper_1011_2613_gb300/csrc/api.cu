@@ -11,6 +11,15 @@
 
 using lbm::View;
 
+namespace lbm {
+int batch_max_grid(int dim, int storage, int smem);
+int batch_sm_count();
+cudaError_t launch_batch_step(const View* views, int nm, const int* part_off, const int* tile_off,
+                              const int* bin_off, const int* tiles_x, int tile_x, int dim, int storage,
+                              double rmax, unsigned* bar, int* err, long long spin_limit, int phantom,
+                              int grid, int smem, cudaStream_t s);
+}  // namespace lbm
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -29,7 +38,7 @@ struct Layout {
   int smem;
   size_t off_f[2], off_own[lbm::kMaxOwners], off_eps[lbm::kMaxOwners];
   size_t off_pos, off_vel, off_omg, off_rad, off_mass, off_inertia, off_ff, off_tf, off_fc;
-  size_t off_lo, off_binof, off_bincount, off_binslot, off_err, off_red, off_stage;
+  size_t off_lo, off_kin, off_binof, off_bincount, off_binslot, off_err, off_red, off_stage;
   size_t stage_bytes;
   size_t total;
 };
@@ -65,6 +74,7 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->Q = c->dim == 2 ? 9 : 19;
   L->pitch = (c->nx + 31) / 32 * 32;
   L->plane = (long long)L->pitch * c->ny * nz;
+  if (L->plane >= (1ll << 31)) return LBM_IMB_EUNSUPPORTED;  // 32-bit node offsets
   L->esz_f = c->storage == LBM_IMB_STORE_F64 ? 8 : (c->storage == LBM_IMB_STORE_F32DEV ? 4 : 2);
   L->esz_eps = c->storage == LBM_IMB_STORE_F64 ? 8 : 4;
   double rmax = 0.0;
@@ -76,7 +86,7 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->rmax = rmax;
   L->smem = 0;
   if (c->n_particles > 0) {
-    if ((c->dim == 3 && rmax > 12.0) || (c->dim == 2 && rmax > 29.0)) return LBM_IMB_EUNSUPPORTED;
+    if ((c->dim == 3 && rmax > 8.0) || (c->dim == 2 && rmax > 29.0)) return LBM_IMB_EUNSUPPORTED;
     L->smem = lbm::eps_raster_smem_bytes(c->dim, c->storage, rmax);
     if (L->smem < 0) return LBM_IMB_EUNSUPPORTED;
   }
@@ -101,6 +111,7 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->off_tf = take(np * 24);
   L->off_fc = take(np * 24);
   L->off_lo = take(np * 24);
+  L->off_kin = take(np * 64);
   L->off_binof = take(np * 4);
   L->off_bincount = take((size_t)nbins * 4);
   L->off_binslot = take((size_t)nbins * lbm::kBinCap * 4);
@@ -127,6 +138,19 @@ int map_err(int bits) {
 
 struct lbm_imb {
   View v;  // fsrc/fdst filled per use
+  // batch state (is_batch) or membership of a batch (is_member)
+  bool is_batch, is_member;
+  int nm;
+  lbm_imb* members;
+  lbm_imb* parent;
+  View* d_views[2];  // member views per ping-pong parity (device)
+  int *d_part_off, *d_tile_off, *d_bin_off, *d_tiles_x;
+  unsigned* d_bar;
+  int* d_berr;
+  int tile_x, blocks_per_sm, grid, bsmem;
+  double rmax_all;
+  long long spin_limit;
+  int phantom;
   void* f[2];
   int cur;
   cudaStream_t stream;
@@ -209,24 +233,10 @@ long long rows_per_chunk(const lbm_imb* h, int comps) {
 
 }  // namespace
 
-extern "C" {
-
-size_t lbm_imb_required_bytes(const lbm_imb_config* cfg) {
-  Layout L;
-  if (make_layout(cfg, &L) != LBM_IMB_OK) return 0;
-  return L.total;
-}
-
-int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cuda_stream,
-                 lbm_imb_t** out) {
-  if (!out || !dev_buf) return LBM_IMB_EINVAL;
-  Layout L;
-  int st = make_layout(c, &L);
-  if (st) return st;
-  if (bytes < L.total) return LBM_IMB_ENOMEM;
-  if (((uintptr_t)dev_buf) % kAlign) return LBM_IMB_EINVAL;
-  lbm_imb* h = new (std::nothrow) lbm_imb();
-  if (!h) return LBM_IMB_ENOMEM;
+// lay out one simulation in its device block and initialise it
+static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, const Layout& L,
+                        cudaStream_t stream) {
+  h->stream = stream;
   unsigned char* base = static_cast<unsigned char*>(dev_buf);
   const int nz = c->dim == 3 ? c->nz : 1;
   const int np = (int)c->n_particles;
@@ -256,6 +266,7 @@ int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cud
   v.tf = reinterpret_cast<double*>(base + L.off_tf);
   v.fc = reinterpret_cast<double*>(base + L.off_fc);
   v.lo = reinterpret_cast<int*>(base + L.off_lo);
+  v.kin = reinterpret_cast<float*>(base + L.off_kin);
   v.bin_of = reinterpret_cast<int*>(base + L.off_binof);
   for (int d = 0; d < 3; d++) {
     v.nb[d] = L.nb[d];
@@ -288,13 +299,16 @@ int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cud
       }
     }
     v.fq[q] = 3.0 * w * cg;
+    v.fq_f[q] = (float)v.fq[q];
   }
+  v.tau_f = (float)v.tau;
+  v.omega_f = (float)v.omega;
+  v.rho0_f = (float)v.rho0;
   v.err = reinterpret_cast<int*>(base + L.off_err);
   v.red = reinterpret_cast<double*>(base + L.off_red);
   h->f[0] = base + L.off_f[0];
   h->f[1] = base + L.off_f[1];
   h->cur = 0;
-  h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->smem = L.smem;
   h->dim = c->dim;
   h->Q = L.Q;
@@ -304,13 +318,10 @@ int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cud
   h->stage_bytes = L.stage_bytes;
 
   // particle state on the host first (derived masses as in the method)
-  st = LBM_IMB_OK;
+  int st = LBM_IMB_OK;
   if (np > 0) {
     double* hbuf = (double*)malloc(sizeof(double) * (size_t)np * 15);
-    if (!hbuf) {
-      delete h;
-      return LBM_IMB_ENOMEM;
-    }
+    if (!hbuf) return LBM_IMB_ENOMEM;
     double *hp = hbuf, *hv = hbuf + 3 * np, *hw = hbuf + 6 * np, *hr = hbuf + 9 * np,
            *hm = hbuf + 10 * np, *hi = hbuf + 11 * np;
     for (int p = 0; p < np; p++) {
@@ -365,6 +376,292 @@ int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cud
     if (e != cudaSuccess) st = LBM_IMB_ECUDA;
   }
   if (!st) st = read_err(h);
+  return st;
+}
+
+static void lbm_imb_destroy_member_graphs(lbm_imb* m) {
+  if (m->graphs_ok) {
+    cudaGraphExecDestroy(m->graph[0]);
+    cudaGraphExecDestroy(m->graph[1]);
+  }
+  m->graphs_ok = false;
+}
+
+// ---- batch plumbing ----
+struct BatchLayout {
+  size_t off_views[2], off_part, off_tile, off_bin, off_tx, off_bar, off_berr, header;
+  size_t member_off[256];
+  Layout member[256];
+  size_t total;
+};
+
+static int batch_layout(const lbm_imb_config* cfgs, int n, BatchLayout* B) {
+  if (!cfgs || n < 1 || n > 256) return LBM_IMB_EINVAL;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  B->off_views[0] = take(sizeof(View) * n);
+  B->off_views[1] = take(sizeof(View) * n);
+  B->off_part = take(4 * (n + 1));
+  B->off_tile = take(4 * (n + 1));
+  B->off_bin = take(4 * (n + 1));
+  B->off_tx = take(4 * n);
+  B->off_bar = take(16);
+  B->off_berr = take(16);
+  B->header = o;
+  for (int i = 0; i < n; i++) {
+    const lbm_imb_config* c = cfgs + i;
+    int st = make_layout(c, &B->member[i]);
+    if (st) return st;
+    if (c->dim != cfgs[0].dim || c->storage != cfgs[0].storage) return LBM_IMB_EINVAL;
+    if (c->dem_substeps != 1) return LBM_IMB_EUNSUPPORTED;
+    B->member_off[i] = take(B->member[i].total);
+  }
+  B->total = o;
+  return LBM_IMB_OK;
+}
+
+static void batch_drop_graphs(lbm_imb* h) {
+  if (h->graphs_ok) {
+    cudaGraphExecDestroy(h->graph[0]);
+    cudaGraphExecDestroy(h->graph[1]);
+  }
+  h->graphs_ok = false;
+  h->graphs_tried = false;
+}
+
+// member views for both parities and the work-list prefixes for tile_x
+static int batch_upload(lbm_imb* h) {
+  const int n = h->nm;
+  View* hv = (View*)malloc(sizeof(View) * n * 2);
+  int* hi = (int*)malloc(sizeof(int) * (4 * (n + 1)));
+  if (!hv || !hi) {
+    free(hv);
+    free(hi);
+    return LBM_IMB_ENOMEM;
+  }
+  int *part = hi, *tile = hi + (n + 1), *bin = hi + 2 * (n + 1), *tx = hi + 3 * (n + 1);
+  part[0] = tile[0] = bin[0] = 0;
+  const int ty = 128 / h->tile_x;
+  for (int i = 0; i < n; i++) {
+    lbm_imb* m = h->members + i;
+    for (int k = 0; k < 2; k++) hv[k * n + i] = view_of(m, k);
+    const int rows = m->v.ny * m->v.nz;
+    tx[i] = (m->v.nx + h->tile_x - 1) / h->tile_x;
+    part[i + 1] = part[i] + m->np;
+    tile[i + 1] = tile[i] + tx[i] * ((rows + ty - 1) / ty);
+    bin[i + 1] = bin[i] + (m->np > 0 ? m->v.nb[0] * m->v.nb[1] * m->v.nb[2] : 0);
+  }
+  cudaError_t e = cudaMemcpyAsync(h->d_views[0], hv, sizeof(View) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_views[1], hv + n, sizeof(View) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_part_off, part, 4 * (n + 1), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_tile_off, tile, 4 * (n + 1), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_bin_off, bin, 4 * (n + 1), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_tiles_x, tx, 4 * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_bar, 0, 16, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_berr, 0, 16, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free(hv);
+  free(hi);
+  return e == cudaSuccess ? LBM_IMB_OK : LBM_IMB_ECUDA;
+}
+
+static int batch_configure(lbm_imb* h, int tile_x, int blocks_per_sm) {
+  if (tile_x == 0) tile_x = 128;
+  if (tile_x != 32 && tile_x != 64 && tile_x != 128) return LBM_IMB_EINVAL;
+  if (blocks_per_sm < 0) return LBM_IMB_EINVAL;
+  const int max_grid = lbm::batch_max_grid(h->dim, h->v.storage, h->bsmem);
+  if (max_grid <= 0) return LBM_IMB_ECUDA;
+  const int sms = lbm::batch_sm_count();
+  int grid = blocks_per_sm > 0 ? blocks_per_sm * sms : max_grid;
+  if (grid > max_grid) grid = max_grid;
+  if (grid < 1) return LBM_IMB_EUNSUPPORTED;
+  batch_drop_graphs(h);
+  h->tile_x = tile_x;
+  h->blocks_per_sm = blocks_per_sm;
+  h->grid = grid;
+  return batch_upload(h);
+}
+
+static cudaError_t batch_enqueue(lbm_imb* h, int parity) {
+  return lbm::launch_batch_step(h->d_views[parity], h->nm, h->d_part_off, h->d_tile_off, h->d_bin_off,
+                                h->d_tiles_x, h->tile_x, h->dim, h->v.storage, h->rmax_all, h->d_bar,
+                                h->d_berr, h->spin_limit, h->phantom, h->grid, h->bsmem, h->stream);
+}
+
+static void batch_try_capture(lbm_imb* h) {
+  h->graphs_tried = true;
+  h->graphs_ok = false;
+  if (h->stream == nullptr) return;
+  for (int k = 0; k < 2; k++) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      if (k == 1) cudaGraphExecDestroy(h->graph[0]);
+      return;
+    }
+    cudaError_t e1 = batch_enqueue(h, k);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e1 != cudaSuccess || e != cudaSuccess || g == nullptr ||
+        cudaGraphInstantiate(&h->graph[k], g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      if (k == 1) cudaGraphExecDestroy(h->graph[0]);
+      return;
+    }
+    cudaGraphDestroy(g);
+  }
+  h->graphs_ok = true;
+}
+
+static int batch_read_err(lbm_imb* h) {
+  int st = LBM_IMB_OK;
+  int bits = 0;
+  if (cudaMemcpyAsync(&bits, h->d_berr, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LBM_IMB_ECUDA;
+  if (bits) {
+    // a timed-out barrier leaves its counters mid-way: reset them
+    cudaMemsetAsync(h->d_bar, 0, 16, h->stream);
+    cudaMemsetAsync(h->d_berr, 0, 16, h->stream);
+    cudaStreamSynchronize(h->stream);
+    st = map_err(bits);
+  }
+  for (int i = 0; i < h->nm; i++) {
+    const int s2 = read_err(h->members + i);
+    if (!st) st = s2;
+  }
+  return st;
+}
+
+extern "C" {
+
+size_t lbm_imb_batch_required_bytes(const lbm_imb_config* cfgs, int n) {
+  BatchLayout* B = (BatchLayout*)malloc(sizeof(BatchLayout));
+  if (!B) return 0;
+  size_t t = batch_layout(cfgs, n, B) == LBM_IMB_OK ? B->total : 0;
+  free(B);
+  return t;
+}
+
+int lbm_imb_batch_init(const lbm_imb_config* cfgs, int n, int tile_x, int blocks_per_sm, void* dev_buf,
+                       size_t bytes, void* cuda_stream, lbm_imb_t** out) {
+  if (!out || !dev_buf || ((uintptr_t)dev_buf) % kAlign) return LBM_IMB_EINVAL;
+  BatchLayout* B = (BatchLayout*)malloc(sizeof(BatchLayout));
+  if (!B) return LBM_IMB_ENOMEM;
+  int st = batch_layout(cfgs, n, B);
+  if (!st && bytes < B->total) st = LBM_IMB_ENOMEM;
+  lbm_imb* h = nullptr;
+  if (!st) {
+    h = new (std::nothrow) lbm_imb();
+    if (!h) st = LBM_IMB_ENOMEM;
+  }
+  if (!st) {
+    h->members = new (std::nothrow) lbm_imb[n]();
+    if (!h->members) st = LBM_IMB_ENOMEM;
+  }
+  unsigned char* base = static_cast<unsigned char*>(dev_buf);
+  if (!st) {
+    h->is_batch = true;
+    h->nm = n;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->dim = cfgs[0].dim;
+    h->v.storage = cfgs[0].storage;
+    h->d_views[0] = reinterpret_cast<View*>(base + B->off_views[0]);
+    h->d_views[1] = reinterpret_cast<View*>(base + B->off_views[1]);
+    h->d_part_off = reinterpret_cast<int*>(base + B->off_part);
+    h->d_tile_off = reinterpret_cast<int*>(base + B->off_tile);
+    h->d_bin_off = reinterpret_cast<int*>(base + B->off_bin);
+    h->d_tiles_x = reinterpret_cast<int*>(base + B->off_tx);
+    h->d_bar = reinterpret_cast<unsigned*>(base + B->off_bar);
+    h->d_berr = reinterpret_cast<int*>(base + B->off_berr);
+    h->spin_limit = 1ll << 25;
+    h->rmax_all = 0.0;
+    for (int i = 0; i < n && !st; i++) {
+      lbm_imb* m = h->members + i;
+      st = setup_handle(m, cfgs + i, base + B->member_off[i], B->member[i], h->stream);
+      m->is_member = true;
+      m->parent = h;
+      if (B->member[i].rmax > h->rmax_all) h->rmax_all = B->member[i].rmax;
+    }
+  }
+  if (!st) {
+    h->bsmem = 0;
+    if (h->rmax_all > 0.0) {
+      h->bsmem = lbm::eps_raster_smem_bytes(h->dim, h->v.storage, h->rmax_all);
+      if (h->bsmem < 0) st = LBM_IMB_EUNSUPPORTED;
+    }
+  }
+  if (!st) st = batch_configure(h, tile_x, blocks_per_sm);
+  free(B);
+  if (st) {
+    if (h) {
+      delete[] h->members;
+      delete h;
+    }
+    return st;
+  }
+  *out = h;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_batch_member(lbm_imb_t* h, int i, lbm_imb_t** member) {
+  if (!h || !member || !h->is_batch || i < 0 || i >= h->nm) return LBM_IMB_EINVAL;
+  *member = h->members + i;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_batch_size(lbm_imb_t* h, int* n) {
+  if (!h || !n) return LBM_IMB_EINVAL;
+  *n = h->is_batch ? h->nm : 1;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_batch_set_launch(lbm_imb_t* h, int tile_x, int blocks_per_sm) {
+  if (!h || !h->is_batch) return LBM_IMB_EINVAL;
+  return batch_configure(h, tile_x, blocks_per_sm);
+}
+
+int lbm_imb_batch_get_launch(lbm_imb_t* h, int* tile_x, int* grid) {
+  if (!h || !h->is_batch) return LBM_IMB_EINVAL;
+  if (tile_x) *tile_x = h->tile_x;
+  if (grid) *grid = h->grid;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_batch_set_barrier_test(lbm_imb_t* h, int64_t spin_limit, int phantom_arrivals) {
+  if (!h || !h->is_batch || spin_limit < 1 || phantom_arrivals < 0) return LBM_IMB_EINVAL;
+  batch_drop_graphs(h);
+  h->spin_limit = spin_limit;
+  h->phantom = phantom_arrivals;
+  return LBM_IMB_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+size_t lbm_imb_required_bytes(const lbm_imb_config* cfg) {
+  Layout L;
+  if (make_layout(cfg, &L) != LBM_IMB_OK) return 0;
+  return L.total;
+}
+
+int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cuda_stream,
+                 lbm_imb_t** out) {
+  if (!out || !dev_buf) return LBM_IMB_EINVAL;
+  Layout L;
+  int st = make_layout(c, &L);
+  if (st) return st;
+  if (bytes < L.total) return LBM_IMB_ENOMEM;
+  if (((uintptr_t)dev_buf) % kAlign) return LBM_IMB_EINVAL;
+  lbm_imb* h = new (std::nothrow) lbm_imb();
+  if (!h) return LBM_IMB_ENOMEM;
+  st = setup_handle(h, c, dev_buf, L, static_cast<cudaStream_t>(cuda_stream));
   if (st) {
     delete h;
     return st;
@@ -374,8 +671,22 @@ int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cud
 }
 
 int lbm_imb_step(lbm_imb_t* h, int64_t n) {
-  if (!h || n < 0) return LBM_IMB_EINVAL;
+  if (!h || n < 0 || h->is_member) return LBM_IMB_EINVAL;
   if (n == 0) return LBM_IMB_OK;
+  if (h->is_batch) {
+    if (!h->graphs_tried) batch_try_capture(h);
+    for (int64_t i = 0; i < n; i++) {
+      cudaError_t e = h->graphs_ok ? cudaGraphLaunch(h->graph[h->cur], h->stream) : batch_enqueue(h, h->cur);
+      if (e != cudaSuccess) return LBM_IMB_ECUDA;
+      h->cur ^= 1;
+      h->steps++;
+      for (int k = 0; k < h->nm; k++) {
+        h->members[k].cur = h->cur;
+        h->members[k].steps = h->steps;
+      }
+    }
+    return check_cuda(cudaGetLastError());
+  }
   if (!h->graphs_tried) try_capture(h);
   for (int64_t i = 0; i < n; i++) {
     if (h->graphs_ok) {
@@ -390,7 +701,30 @@ int lbm_imb_step(lbm_imb_t* h, int64_t n) {
 }
 
 int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* total_ms) {
-  if (!h || n < 1 || n > 4096 || !kernel_ms || !total_ms) return LBM_IMB_EINVAL;
+  if (!h || n < 1 || n > 4096 || !kernel_ms || !total_ms || h->is_member) return LBM_IMB_EINVAL;
+  if (h->is_batch) {
+    // one persistent launch per step: its time goes to the collide slot
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LBM_IMB_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return LBM_IMB_ECUDA;
+    }
+    cudaEventRecord(e0, h->stream);
+    int st = lbm_imb_step(h, n);
+    cudaEventRecord(e1, h->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (e != cudaSuccess) return LBM_IMB_ECUDA;
+    for (int k = 0; k < LBM_IMB_NUM_KERNELS; k++) kernel_ms[k] = 0.0;
+    kernel_ms[LBM_IMB_K_COLLIDE] = ms;
+    *total_ms = ms;
+    return batch_read_err(h);
+  }
   const int K = LBM_IMB_NUM_KERNELS;
   const size_t ne = (size_t)n * (K + 1);
   cudaEvent_t* ev = (cudaEvent_t*)calloc(ne, sizeof(cudaEvent_t));
@@ -437,12 +771,17 @@ int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* to
 
 int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches) {
   if (!h || !launches) return LBM_IMB_EINVAL;
+  if (h->is_batch) {
+    *launches = 1;
+    return LBM_IMB_OK;
+  }
   *launches = h->np > 0 ? 3 + 4 * h->v.substeps : 1;
   return LBM_IMB_OK;
 }
 
 int lbm_imb_sync(lbm_imb_t* h) {
   if (!h) return LBM_IMB_EINVAL;
+  if (h->is_batch) return batch_read_err(h);
   return read_err(h);
 }
 
@@ -586,7 +925,14 @@ int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps) {
 }
 
 int lbm_imb_destroy(lbm_imb_t* h) {
-  if (!h) return LBM_IMB_EINVAL;
+  if (!h || h->is_member) return LBM_IMB_EINVAL;
+  if (h->is_batch) {
+    batch_drop_graphs(h);
+    for (int i = 0; i < h->nm; i++) lbm_imb_destroy_member_graphs(h->members + i);
+    delete[] h->members;
+    delete h;
+    return LBM_IMB_OK;
+  }
   if (h->graphs_ok) {
     cudaGraphExecDestroy(h->graph[0]);
     cudaGraphExecDestroy(h->graph[1]);

@@ -1,0 +1,330 @@
+// K1 device code: solid-fraction rasterisation and footprint clearing,
+// shared by the per-step kernels (k_eps.cu) and the batched persistent
+// kernel (k_batch.cu).
+#pragma once
+#include <math.h>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// --------------------------------------------------------------------------
+// clear the previous footprint (all owner slots) and zero the force sums
+// --------------------------------------------------------------------------
+// one warp per particle
+__device__ __forceinline__ void eps_clear_particle(const View& v, const int p, const int lane,
+                                                   const bool zero_forces) {
+  const int* box = v.lo + 6 * p;
+  const int lx = box[0], ly = box[1], lz = box[2];
+  const int ex = box[3], ey = box[4], ez = box[5];
+  const int total = ex * ey * ez;
+  for (int t = lane; t < total; t += 32) {
+    int i = lx + t % ex;
+    int j = ly + (t / ex) % ey;
+    int k = lz + t / (ex * ey);
+    if (v.wall_y) {
+      if (j < 0 || j >= v.ny) continue;
+    } else {
+      j = ((j % v.ny) + v.ny) % v.ny;
+    }
+    i = ((i % v.nx) + v.nx) % v.nx;
+    k = ((k % v.nz) + v.nz) % v.nz;
+    const long long n = ((long long)k * v.ny + j) * v.pitch + i;
+#pragma unroll
+    for (int s = 0; s < kMaxOwners; s++) v.own[s][n] = -1;
+  }
+  // FP32 kinematics record of the particle for the reduced-precision
+  // collision: position split into the nearest node (int) and the offset
+  // from it (float), velocity and spin (float)
+  if (v.kin != nullptr && lane < 16) {
+    const int d = lane & 3, part = lane >> 2;
+    float* rec = v.kin + 16 * p;
+    if (d == 3) {
+      rec[lane] = 0.f;
+    } else if (part == 0 || part == 1) {
+      const double x = v.pos[3 * p + d];
+      const double xi = floor(x + 0.5);
+      if (part == 0) rec[lane] = (float)(x - xi);
+      else reinterpret_cast<int*>(rec)[lane] = (int)xi;
+    } else if (part == 2) {
+      rec[lane] = (float)v.vel[3 * p + d];
+    } else {
+      rec[lane] = (float)v.omg[3 * p + d];
+    }
+  }
+  if (zero_forces && lane < 3) {
+    v.ff[3 * p + lane] = 0.0;
+    v.tf[3 * p + lane] = 0.0;
+  }
+}
+
+// --------------------------------------------------------------------------
+// rasterise one particle per CTA
+//
+// Corner values come from small tables: with s(v) = sqrt(R^2 - v^2) and
+// psi(v) = atan2(s(v), v) per axis value v, the disk corner area is
+//   U(a,b) = R^2/2 (psi(a) + psi(b) - pi/2) - (a s(a) + b s(b))/2 + a b.
+// For the ball every angle of the Gauss-Bonnet form depends on two of the
+// three coordinates: for a pair (u,v) with z = sqrt(R^2 - u^2 - v^2) the
+// vertex angle alpha = atan2(R z, u v) and the polar angles phi_u =
+// atan2(z, u), phi_v = atan2(z, v) give the three face arcs
+//   th_a = phi_b(ab) + phi_c(ac) - pi/2   (and cyclically),
+// the solid angle Omega = alpha_ab + alpha_ac + alpha_bc - pi
+//   - (a th_a + b th_b + c th_c)/R, the faces
+//   A_a = (R^2 - a^2) th_a / 2 - (b z_ab + c z_ac)/2 + b c,
+// and P = (R^3 Omega - a A_a - b A_b - c A_c)/3.
+// --------------------------------------------------------------------------
+struct RasterSmem {
+  int tab_cap, pair_cap, cell_cap;
+};
+
+template <typename T>
+__device__ __forceinline__ int classify_cell(const T (*bnd)[64], const float (*bndf)[64], const int idx[3],
+                                             int dim, double R2, float R2f) {
+  // exact decision in T; the FP64 instantiation first tries FP32 copies of
+  // the offsets with a relative margin that cannot flip a decision
+  if (sizeof(T) == 8) {
+    float n2 = 0.f, f2 = 0.f;
+    for (int d = 0; d < dim; d++) {
+      const float bl = bndf[d][idx[d]], bh = bndf[d][idx[d] + 1];
+      const float nd = bl > 0.f ? bl : (bh < 0.f ? -bh : 0.f);
+      const float fd = fmaxf(fabsf(bl), fabsf(bh));
+      n2 += nd * nd;
+      f2 += fd * fd;
+    }
+    if (n2 >= R2f * 1.0001f) return 0;
+    if (f2 <= R2f * 0.9999f) return 1;
+  }
+  T near2 = T(0), far2 = T(0);
+  for (int d = 0; d < dim; d++) {
+    const T bl = bnd[d][idx[d]], bh = bnd[d][idx[d] + 1];
+    const T nd = bl > T(0) ? bl : (bh < T(0) ? -bh : T(0));
+    const T fd = fabs(bl) > fabs(bh) ? fabs(bl) : fabs(bh);
+    near2 += nd * nd;
+    far2 += fd * fd;
+  }
+  if (near2 >= T(R2)) return 0;
+  if (far2 <= T(R2)) return 1;
+  return 2;
+}
+
+// per-axis decomposition of cell i into (lower, upper) value indices of boxes
+// on the non-negative half-axis; returns the number of boxes (1 or 2)
+template <typename T>
+__device__ __forceinline__ int split_axis(const T* b, int i, int zero, int (&lo_i)[2], int (&hi_i)[2]) {
+  const T bl = b[i], bh = b[i + 1];
+  if (bl >= T(0)) { lo_i[0] = i; hi_i[0] = i + 1; return 1; }
+  if (bh <= T(0)) { lo_i[0] = i + 1; hi_i[0] = i; return 1; }
+  lo_i[0] = zero; hi_i[0] = i;
+  lo_i[1] = zero; hi_i[1] = i + 1;
+  return 2;
+}
+
+// one CTA per particle (block-uniform p); smem = dynamic shared memory of the
+// size raster_bytes gives
+template <int DIM, typename T>
+__device__ __forceinline__ void eps_raster_particle(const View& v, const int p, const RasterSmem cap,
+                                                    unsigned char* smem) {
+  __syncthreads();  // the block may still be reading the previous particle's tables
+  const double R64 = v.rad[p];
+  const T R = T(R64);
+  const double c[3] = {v.pos[3 * p], v.pos[3 * p + 1], v.pos[3 * p + 2]};
+  int lo[3] = {0, 0, 0}, ne[3] = {1, 1, 1};
+#pragma unroll
+  for (int d = 0; d < DIM; d++) {
+    lo[d] = (int)ceil(c[d] - R64 - 0.5);
+    ne[d] = (int)floor(c[d] + R64 + 0.5) - lo[d] + 1;
+  }
+  // value lists per axis: |cell boundary - centre| (ne+1 of them), then 0
+  const int tx = ne[0] + 2, ty = ne[1] + 2, tz = DIM == 3 ? ne[2] + 2 : 1;
+  const int tsize = tx * ty * tz;
+  const int ncell = ne[0] * ne[1] * ne[2];
+  if (tsize > cap.tab_cap || ncell > cap.cell_cap || ne[0] > 62 || ne[1] > 62 || ne[2] > 62 ||
+      (DIM == 3 && (tx * ty > cap.pair_cap || tx * tz > cap.pair_cap || ty * tz > cap.pair_cap))) {
+    if (threadIdx.x == 0) atomicOr(v.err, ERR_OWNERS);  // radius beyond the launch's capacity
+    return;
+  }
+  T* tab = reinterpret_cast<T*>(smem);
+  T* pr = tab + cap.tab_cap;                          // 3D: 3 pair tables x 4 values
+  int* clist = reinterpret_cast<int*>(pr + 12 * cap.pair_cap);
+  int* cells = clist + cap.tab_cap;
+  unsigned char* need = reinterpret_cast<unsigned char*>(cells + cap.cell_cap);
+  __shared__ T bnd[3][64];  // signed boundary offsets
+  __shared__ float bndf[3][64];
+  __shared__ T val[3][64];  // value lists
+  __shared__ T ax_s[2][64], ax_psi[2][64];  // 2D per-axis tables
+  __shared__ int n_part, n_need;
+  const double R2 = R64 * R64;
+  const float R2f = (float)R2;
+
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < 3; d++) {
+      v.lo[6 * p + d] = lo[d];
+      v.lo[6 * p + 3 + d] = ne[d];
+    }
+    n_part = 0;
+    n_need = 0;
+  }
+  for (int t = threadIdx.x; t < 3 * 64; t += blockDim.x) {
+    const int d = t / 64, i = t % 64;
+    const T b = (d < DIM && i <= ne[d]) ? T(((double)(lo[d] + i) - 0.5) - c[d]) : T(0);
+    bnd[d][i] = b;
+    bndf[d][i] = (float)b;
+    val[d][i] = (d < DIM && i <= ne[d]) ? fabs(b) : T(0);
+  }
+  for (int t = threadIdx.x; t < tsize; t += blockDim.x) need[t] = 0;
+  __syncthreads();
+
+  // pass 1: full cells claim their node at once; partial cells are listed
+  // and mark the corner values they combine
+  auto claim = [&](int ci, int cj, int ck, T e) {
+    int i = lo[0] + ci, j = lo[1] + cj, k = lo[2] + ck;
+    if (v.wall_y) {
+      if (j < 0 || j >= v.ny) return;
+    } else {
+      j = ((j % v.ny) + v.ny) % v.ny;
+    }
+    i = ((i % v.nx) + v.nx) % v.nx;
+    k = ((k % v.nz) + v.nz) % v.nz;
+    const long long n = ((long long)k * v.ny + j) * v.pitch + i;
+#pragma unroll
+    for (int s = 0; s < kMaxOwners; s++) {
+      if (atomicCAS(&v.own[s][n], -1, p) == -1) {
+        static_cast<T*>(v.eps[s])[n] = e;
+        return;
+      }
+    }
+    atomicOr(v.err, ERR_OWNERS);
+  };
+  for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+    const int idx[3] = {t % ne[0], (t / ne[0]) % ne[1], t / (ne[0] * ne[1])};
+    const int cls = classify_cell<T>(bnd, bndf, idx, DIM, R2, R2f);
+    if (cls == 0) continue;
+    if (cls == 1) {
+      claim(idx[0], idx[1], idx[2], T(1));
+      continue;
+    }
+    cells[atomicAdd(&n_part, 1)] = t;
+    int al[2], ah[2], bl[2], bh[2], cl[2] = {0, 0}, ch[2] = {0, 0};
+    const int na = split_axis<T>(bnd[0], idx[0], ne[0] + 1, al, ah);
+    const int nb = split_axis<T>(bnd[1], idx[1], ne[1] + 1, bl, bh);
+    const int nc = DIM == 3 ? split_axis<T>(bnd[2], idx[2], ne[2] + 1, cl, ch) : 1;
+    for (int ia = 0; ia < na; ia++)
+      for (int ib = 0; ib < nb; ib++)
+        for (int ic = 0; ic < nc; ic++) {
+          const int xs[2] = {al[ia], ah[ia]}, ys[2] = {bl[ib], bh[ib]}, zs[2] = {cl[ic], ch[ic]};
+          for (int s = 0; s < (DIM == 3 ? 8 : 4); s++)
+            need[(zs[(s >> 2) & 1] * ty + ys[(s >> 1) & 1]) * tx + xs[s & 1]] = 1;
+        }
+  }
+  // per-axis (2D) or per-pair (3D) angle tables
+  const T hpi = T(1.57079632679489661923);
+  if (DIM == 2) {
+    for (int t = threadIdx.x; t < tx + ty; t += blockDim.x) {
+      const int d = t < tx ? 0 : 1, i = t < tx ? t : t - tx;
+      const T u = val[d][i];
+      const T su = u < R ? sqrt((R - u) * (R + u)) : T(0);
+      ax_s[d][i] = su;
+      ax_psi[d][i] = atan2(su, u);
+    }
+  } else {
+    const int dims[3][2] = {{tx, ty}, {tx, tz}, {ty, tz}};
+    const int axes[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    const int n01 = tx * ty, n02 = tx * tz, n12 = ty * tz;
+    for (int t = threadIdx.x; t < n01 + n02 + n12; t += blockDim.x) {
+      const int g = t < n01 ? 0 : (t < n01 + n02 ? 1 : 2);
+      const int r = t - (g == 0 ? 0 : (g == 1 ? n01 : n01 + n02));
+      const int i = r % dims[g][0], j = r / dims[g][0];
+      const T u = val[axes[g][0]][i], w = val[axes[g][1]][j];
+      const T z2 = (R * R - u * u) - w * w;
+      T* e = pr + 4 * (g * cap.pair_cap + r);
+      if (z2 > T(0)) {
+        const T z = sqrt(z2);
+        e[0] = z;
+        e[1] = atan2(R * z, u * w);
+        e[2] = atan2(z, u);
+        e[3] = atan2(z, w);
+      } else {  // edge line outside the ball: the limit z -> 0 of the angles
+        e[0] = e[1] = e[2] = e[3] = T(0);
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tsize; t += blockDim.x)
+    if (need[t]) clist[atomicAdd(&n_need, 1)] = t;
+  __syncthreads();
+
+  // pass 2: the needed corner values
+  for (int q = threadIdx.x; q < n_need; q += blockDim.x) {
+    const int t = clist[q];
+    const int i = t % tx, j = (t / tx) % ty, k = t / (tx * ty);
+    const T a = val[0][i], b = val[1][j];
+    T out = T(0);
+    if (DIM == 2) {
+      if (a * a + b * b < R * R)
+        out = T(0.5) * R * R * (ax_psi[0][i] + ax_psi[1][j] - hpi) -
+              T(0.5) * (a * ax_s[0][i] + b * ax_s[1][j]) + a * b;
+    } else {
+      const T cc = val[2][k];
+      if ((a * a + b * b) + cc * cc < R * R) {
+        const T* ab = pr + 4 * (0 * cap.pair_cap + j * tx + i);
+        const T* ac = pr + 4 * (1 * cap.pair_cap + k * tx + i);
+        const T* bc = pr + 4 * (2 * cap.pair_cap + k * ty + j);
+        const T zab = ab[0], zac = ac[0], zbc = bc[0];
+        const T tha = ab[3] + ac[3] - hpi;
+        const T thb = ab[2] + bc[3] - hpi;
+        const T thc = ac[2] + bc[2] - hpi;
+        const T om = ab[1] + ac[1] + bc[1] - T(2) * hpi - (a * tha + b * thb + cc * thc) / R;
+        const T R2t = R * R;
+        const T Aa = T(0.5) * (R2t - a * a) * tha - T(0.5) * (b * zab + cc * zac) + b * cc;
+        const T Ab = T(0.5) * (R2t - b * b) * thb - T(0.5) * (a * zab + cc * zbc) + a * cc;
+        const T Ac = T(0.5) * (R2t - cc * cc) * thc - T(0.5) * (a * zac + b * zbc) + a * b;
+        out = (R2t * R * om - a * Aa - b * Ab - cc * Ac) / T(3);
+      }
+    }
+    tab[t] = out;
+  }
+  __syncthreads();
+
+  // pass 3: partially covered cells
+  for (int q = threadIdx.x; q < n_part; q += blockDim.x) {
+    const int t = cells[q];
+    const int idx[3] = {t % ne[0], (t / ne[0]) % ne[1], t / (ne[0] * ne[1])};
+    int al[2], ah[2], bl[2], bh[2], cl[2] = {0, 0}, ch[2] = {0, 0};
+    const int na = split_axis<T>(bnd[0], idx[0], ne[0] + 1, al, ah);
+    const int nb = split_axis<T>(bnd[1], idx[1], ne[1] + 1, bl, bh);
+    const int nc = DIM == 3 ? split_axis<T>(bnd[2], idx[2], ne[2] + 1, cl, ch) : 1;
+    T sum = T(0);
+    for (int ia = 0; ia < na; ia++)
+      for (int ib = 0; ib < nb; ib++)
+        for (int ic = 0; ic < nc; ic++) {
+          const int xs[2] = {al[ia], ah[ia]}, ys[2] = {bl[ib], bh[ib]}, zs[2] = {cl[ic], ch[ic]};
+          for (int s = 0; s < (DIM == 3 ? 8 : 4); s++) {
+            const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+            const T vv = tab[(zs[sz] * ty + ys[sy]) * tx + xs[sx]];
+            sum += ((sx + sy + sz) & 1) ? -vv : vv;
+          }
+        }
+    const T e = sum < T(0) ? T(0) : (sum > T(1) ? T(1) : sum);
+    if (e > T(0)) claim(idx[0], idx[1], idx[2], e);
+  }
+}
+
+static inline RasterSmem raster_caps(int dim, double rmax) {
+  const int nmax = (int)(2.0 * rmax) + 3;
+  const int t = nmax + 2;
+  RasterSmem c;
+  c.tab_cap = dim == 3 ? t * t * t : t * t;
+  c.pair_cap = dim == 3 ? t * t : 0;
+  c.cell_cap = dim == 3 ? nmax * nmax * nmax : nmax * nmax;
+  return c;
+}
+
+static inline long long raster_bytes(int dim, int esz, double rmax) {
+  const RasterSmem c = raster_caps(dim, rmax);
+  long long b = (long long)c.tab_cap * esz + 12LL * c.pair_cap * esz + (long long)c.tab_cap * 4 +
+                (long long)c.cell_cap * 4 + c.tab_cap;
+  return (b + 15) & ~15LL;
+}
+
+}  // namespace lbm

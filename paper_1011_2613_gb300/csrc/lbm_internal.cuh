@@ -71,7 +71,8 @@ struct View {
   int np;
   double *pos, *vel, *omg, *rad, *mass, *inertia;
   double *ff, *tf, *fc;  // hydrodynamic force/torque (Eq. 3), contact force
-  int* lo;               // [np*3] origin of the last rasterised bounding box
+  int* lo;               // [np*6] origin and extent of the last rasterised box
+  float* kin;            // [np*16] FP32 kinematics: frac pos, int pos, v, omega
   int* bin_of;           // [np] DEM bin of each particle
   // DEM bins
   int nb[3];
@@ -82,6 +83,10 @@ struct View {
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i
+  // FP32 copies for the reduced-precision kernels (a double -> float
+  // conversion runs on the FP64 pipe, so none happens per node)
+  float tau_f, omega_f, rho0_f;
+  float fq_f[19];
   int substeps;
   // device error word
   int* err;

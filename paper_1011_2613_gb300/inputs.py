@@ -253,3 +253,31 @@ def random_populations(rng: np.random.Generator, cfg: SuspensionConfig, amp: flo
     Q = 9 if cfg.dim == 2 else 19
     nz = cfg.nz if cfg.dim == 3 else 1
     return cfg.rho_fluid / Q * (1.0 + amp * rng.standard_normal((Q, nz, cfg.ny, cfg.nx)))
+
+
+def batch_configs(n: int = 32, seed: int = 4, nx_range=(256, 1024), ny_range=(512, 4096), np_range=(10, 2000),
+                  r_range=(4.0, 8.0), ratio_range=(2.5, 1500.0), phi_max=0.25, tau=0.6, gs=1.176e-7, v0=5e-3,
+                  e=0.9, storage="f64"):
+    """Independent 2D periodic gravity-driven suspensions of uneven sizes:
+    nx and ny drawn log-uniformly in their ranges (ny >= nx), particle count
+    log-uniform in np_range (capped at solid fraction phi_max), radii uniform
+    in r_range, one density ratio per lattice log-uniform in ratio_range."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nx = int(round(math.exp(rng.uniform(math.log(nx_range[0]), math.log(nx_range[1])))))
+        ny = int(round(math.exp(rng.uniform(math.log(max(ny_range[0], nx)), math.log(ny_range[1])))))
+        ratio = float(math.exp(rng.uniform(math.log(ratio_range[0]), math.log(ratio_range[1]))))
+        k = int(round(math.exp(rng.uniform(math.log(np_range[0]), math.log(np_range[1])))))
+        radii = rng.uniform(r_range[0], r_range[1], k)
+        area = math.pi * (radii ** 2)
+        while area.sum() > phi_max * nx * ny and k > 1:
+            k -= 1
+            area = area[:k]
+        radii = radii[:k]
+        pos = rsa_place(rng, radii, (nx, ny, 1), 2, (True, True, True))
+        vel = v0 * random_directions(rng, k, 2)
+        out.append(_finish(2, nx, ny, 1, 0, tau, (0.0, -gs, 0.0), 1.0, e, radii, np.full(k, ratio), pos, vel,
+                           f"batch member {i}: D2Q9 {nx}x{ny}, {k} disks R in [{r_range[0]}, {r_range[1]}], "
+                           f"ratio {ratio:.1f}", storage=storage))
+    return out

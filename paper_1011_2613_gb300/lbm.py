@@ -93,6 +93,21 @@ def lib():
             L.lbm_imb_dem_forces_static.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int64,
                                                     C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                                     C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+            L.lbm_imb_batch_required_bytes.restype = C.c_size_t
+            L.lbm_imb_batch_required_bytes.argtypes = [C.POINTER(Config), C.c_int]
+            L.lbm_imb_batch_init.restype = C.c_int
+            L.lbm_imb_batch_init.argtypes = [C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
+                                             C.c_void_p, C.POINTER(C.c_void_p)]
+            L.lbm_imb_batch_member.restype = C.c_int
+            L.lbm_imb_batch_member.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
+            L.lbm_imb_batch_size.restype = C.c_int
+            L.lbm_imb_batch_size.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+            L.lbm_imb_batch_set_launch.restype = C.c_int
+            L.lbm_imb_batch_set_launch.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.lbm_imb_batch_get_launch.restype = C.c_int
+            L.lbm_imb_batch_get_launch.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.lbm_imb_batch_set_barrier_test.restype = C.c_int
+            L.lbm_imb_batch_set_barrier_test.argtypes = [C.c_void_p, C.c_int64, C.c_int]
             L.lbm_imb_destroy.restype = C.c_int
             L.lbm_imb_destroy.argtypes = [C.c_void_p]
             L.lbm_imb_strerror.restype = C.c_char_p
@@ -156,7 +171,8 @@ def required_bytes(cfg) -> int:
 
 
 class Simulation:
-    """One suspension advanced on the GPU by liblbm_imb.
+    """One suspension advanced on the GPU by liblbm_imb (or a member view of
+    a :class:`Batch`).
 
     ``cfg``: :class:`paper_1011_2613_gb300.inputs.SuspensionConfig`.
     ``stream``: a ``torch.cuda.Stream`` (a new one by default; its graphs are
@@ -191,7 +207,28 @@ class Simulation:
         self.h = h
 
     # ------------------------------------------------------------------
+    @classmethod
+    def _member(cls, batch, i, cfg):
+        self = cls.__new__(cls)
+        self.cfg = cfg
+        self.dim = int(cfg.dim)
+        self.shape = (int(cfg.nx), int(cfg.ny), int(cfg.nz) if self.dim == 3 else 1)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        self.Q = 9 if self.dim == 2 else 19
+        self.np = int(len(cfg.radius))
+        self.device = batch.device
+        self.stream = batch.stream
+        self.batch = batch  # keeps the batch (and its memory) alive
+        h = C.c_void_p()
+        _check(lib().lbm_imb_batch_member(batch.h, i, C.byref(h)), "lbm_imb_batch_member")
+        self.h = h
+        self._member_of = batch
+        return self
+
     def close(self):
+        if getattr(self, "_member_of", None) is not None:
+            self.h = None
+            return
         if getattr(self, "h", None):
             lib().lbm_imb_destroy(self.h)
             self.h = None
@@ -304,3 +341,77 @@ def dem_forces(dim, extent, wall_y, pos, vel, radius, mass, k_n, restitution, rm
                                   C.c_void_p(fc.data_ptr()), C.c_void_p(wp), nb, C.c_void_p(s.cuda_stream))
     _check(st, "lbm_imb_dem_forces")
     return fc
+
+
+class Batch:
+    """Many independent suspensions advanced by one persistent kernel launch
+    per step (lbm_imb_batch_* in the C ABI).  ``members[i]`` gives the
+    accessors of suspension i."""
+
+    def __init__(self, cfgs, tile_x=0, blocks_per_sm=0, device=None, stream=None):
+        import torch
+
+        L = lib()
+        self.cfgs = list(cfgs)
+        n = len(self.cfgs)
+        arr = (Config * n)()
+        keeps = []
+        for i, cfg in enumerate(self.cfgs):
+            c, keep = make_config(cfg)
+            arr[i] = c
+            keeps.append(keep)
+        nbytes = int(L.lbm_imb_batch_required_bytes(arr, n))
+        if nbytes == 0:
+            raise LbmImbError(EINVAL, "lbm_imb_batch_required_bytes")
+        self.nbytes = nbytes
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            ptr = (self.buf.data_ptr() + 255) // 256 * 256
+            h = C.c_void_p()
+            st = L.lbm_imb_batch_init(arr, n, int(tile_x), int(blocks_per_sm), C.c_void_p(ptr), nbytes,
+                                      C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        del keeps
+        _check(st, "lbm_imb_batch_init")
+        self.h = h
+        self.members = [Simulation._member(self, i, cfg) for i, cfg in enumerate(self.cfgs)]
+        self.n_nodes = sum(m.N for m in self.members)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            lib().lbm_imb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _check(lib().lbm_imb_step(self.h, int(n)), "lbm_imb_step")
+
+    def sync(self):
+        _check(lib().lbm_imb_sync(self.h), "lbm_imb_sync")
+
+    def step_profiled(self, n: int):
+        k = (C.c_double * 4)()
+        t = C.c_double()
+        _check(lib().lbm_imb_step_profiled(self.h, int(n), k, C.byref(t)), "lbm_imb_step_profiled")
+        return float(t.value)
+
+    def set_launch(self, tile_x: int, blocks_per_sm: int):
+        _check(lib().lbm_imb_batch_set_launch(self.h, int(tile_x), int(blocks_per_sm)), "lbm_imb_batch_set_launch")
+
+    def launch(self):
+        tx = C.c_int()
+        g = C.c_int()
+        _check(lib().lbm_imb_batch_get_launch(self.h, C.byref(tx), C.byref(g)), "lbm_imb_batch_get_launch")
+        return int(tx.value), int(g.value)
+
+    def set_barrier_test(self, spin_limit: int, phantom: int):
+        _check(lib().lbm_imb_batch_set_barrier_test(self.h, int(spin_limit), int(phantom)),
+               "lbm_imb_batch_set_barrier_test")
