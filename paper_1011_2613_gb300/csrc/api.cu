@@ -171,6 +171,12 @@ View view_of(const lbm_imb* h, int src) {
   View v = h->v;
   v.fsrc = h->f[src];
   v.fdst = h->f[src ^ 1];
+  const size_t esz = v.storage == LBM_IMB_STORE_F64 ? 8 : (v.storage == LBM_IMB_STORE_F32DEV ? 4 : 2);
+  for (int q = 0; q < 19; q++) {
+    const size_t off = q < v.Q ? (size_t)q * (size_t)v.plane * esz : 0;
+    v.src_q[q] = static_cast<const unsigned char*>(v.fsrc) + off;
+    v.dst_q[q] = static_cast<unsigned char*>(v.fdst) + off;
+  }
   return v;
 }
 

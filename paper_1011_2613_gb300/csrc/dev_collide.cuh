@@ -131,16 +131,19 @@ __device__ __forceinline__ double min_image(double d, int n, bool periodic) {
   return d;
 }
 
-// One node of the fused pull-stream + collision.  Every lane of the warp must
-// call it (warp collectives); lanes outside the lattice pass active = false
-// with in-range coordinates.  Node offsets within a population plane are
-// 32-bit (the library rejects planes of 2^31 nodes or more).
+// One node per thread of the fused pull-stream + collision; the whole CTA
+// (128 threads, 4 full warps) calls it together.  Lanes outside the lattice
+// pass active = false with in-range coordinates.  Node offsets within a
+// population plane are 32-bit (the library rejects planes of 2^31 nodes or
+// more).
 //
-// The plain BGK update is computed for every lane; a warp with any covered
-// node then adds the immersed-boundary correction
+// Every thread computes the plain BGK update and stores it unless its node
+// is covered.  Covered nodes are then packed into the first lanes of the CTA
+// through shared memory (f - f^eq, rho, u per node), so the immersed-boundary
+// work runs on full warps; it adds the correction
 //   f*_i - f*_i(plain) = beta (omega (f_i - f^eq_i) + Omega^S_i),
-// with Omega^S_i = (f - f^eq)_{-i} - (f - f^eq)_i + f^eq_i(rho, V_S) - f^eq_i(rho, u)
-// (the same Eq. 1 rearranged), reusing f - f^eq and the pair terms A, B.
+//   Omega^S_i = (f - f^eq)_{-i} - (f - f^eq)_i + f^eq_i(rho, V_S) - f^eq_i(rho, u)
+// (Eq. 1 with the Omega^S term rearranged) and the Eq. 3 force/torque.
 template <class LAT, int STORE>
 __device__ __forceinline__ void collide_node(const View& v, const int xx, const int y, const int z,
                                              const bool active) {
@@ -151,43 +154,14 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
   constexpr int Q = LAT::Q;
   constexpr int NP = (Q - 1) / 2;  // opposite pairs
   constexpr bool D3 = LAT::DIM == 3;
+  constexpr int NS = Q + 5;        // packed state: f - f^eq, rho, drho, u
 
   const int nx = v.nx, ny = v.ny, nz = v.nz, pitch = v.pitch;
   const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
   const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-  const long long plane = v.plane;
   const int n = (z * ny + y) * pitch + xx;
-  const Elem* __restrict__ src = static_cast<const Elem*>(v.fsrc);
-  Elem* __restrict__ dst = static_cast<Elem*>(v.fdst);
 
-  // ---- pull streaming (halfway bounce-back at y walls) ----
-  T f[Q];
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
-    const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
-    const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
-    const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
-    const bool bounce = v.wall_y && ((cy == 1 && y == 0) || (cy == -1 && y == ny - 1));
-    if (bounce)
-      f[q] = S::load(src + opp(q) * plane, n, LAT::w(opp(q)));
-    else
-      f[q] = S::load(src + q * plane, (sz * ny + sy) * pitch + sx, LAT::w(q));
-  }
-
-  // ---- moments ----
-  T s0 = f[0], jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-  for (int q = 1; q < Q; q++) {
-    s0 += f[q];
-    if (LAT::c(q, 0) == 1) jx += f[q];
-    if (LAT::c(q, 0) == -1) jx -= f[q];
-    if (LAT::c(q, 1) == 1) jy += f[q];
-    if (LAT::c(q, 1) == -1) jy -= f[q];
-    if (D3 && LAT::c(q, 2) == 1) jz += f[q];
-    if (D3 && LAT::c(q, 2) == -1) jz -= f[q];
-  }
   T rho0p, om, tau_t;
   if constexpr (S::DEV) {
     rho0p = v.rho0_f;
@@ -198,39 +172,8 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
     om = v.omega;
     tau_t = v.tau;
   }
-  const T drho = S::DEV ? s0 : T(0);        // deviation of density
-  const T rho = S::DEV ? rho0p + s0 : s0;   // density
-  const T irho = T(1) / rho;
-  const T ux = jx * irho, uy = jy * irho, uz = jz * irho;
-  const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
 
-  // ---- plain BGK (all lanes); keep f - f^eq and the pair terms ----
-  T out[Q], neq[Q], A[NP + 1], B[NP + 1];
-  {
-    const T w0r = T(LAT::w(0)) * rho;
-    A[0] = pair_A<S::DEV, T>(T(LAT::w(0)), w0r, drho, usq15, T(0));
-    B[0] = T(0);
-    neq[0] = f[0] - A[0];
-    out[0] = f[0] - om * neq[0];
-  }
-#pragma unroll
-  for (int k = 0; k < NP; k++) {
-    const int q = 2 * k + 1;
-    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
-    const T cu = cdot<T>(cx, cy, cz, ux, uy, uz);
-    const T wr = T(LAT::w(q)) * rho;
-    const T a = pair_A<S::DEV, T>(T(LAT::w(q)), wr, drho, usq15, cu);
-    const T b = (T(3) * wr) * cu;
-    const T fr = fq_of<S::DEV, T>(v, q) * rho;
-    A[k + 1] = a;
-    B[k + 1] = b;
-    neq[q] = f[q] - (a + b);
-    neq[q + 1] = f[q + 1] - (a - b);
-    out[q] = f[q] - om * neq[q] + fr;
-    out[q + 1] = f[q + 1] - om * neq[q + 1] - fr;
-  }
-
-  // ---- owners of this node (ascending particle id) ----
+  // ---- owners of this node (slot s+1 is read only where slot s is taken) ----
   int own[kMaxOwners];
   E eown[kMaxOwners];
   int no = 0;
@@ -247,25 +190,152 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
       }
     }
   }
-  const unsigned FULL = 0xffffffffu;
-  if (__any_sync(FULL, no > 0)) {
-    // ---------------- NT immersed moving boundary correction ----------------
-    // sort owners by id
+
+  // ---- pull streaming; rows are whole warps, so the wall test is uniform ----
+  const int ry[3] = {y * pitch, ym * pitch, yp * pitch};
+  const int rz[3] = {z * ny * pitch, zm * ny * pitch, zp * ny * pitch};
+  T f[Q];
+  const bool wall_row = v.wall_y && (y == 0 || y == ny - 1);
+  if (!wall_row) {
 #pragma unroll
-    for (int a = 1; a < kMaxOwners; a++) {
-      if (a < no) {
-        int k = own[a];
-        E ek = eown[a];
-        int b = a - 1;
-        while (b >= 0 && own[b] > k) {
-          own[b + 1] = own[b];
-          eown[b + 1] = eown[b];
-          b--;
-        }
-        own[b + 1] = k;
-        eown[b + 1] = ek;
-      }
+    for (int q = 0; q < Q; q++) {
+      const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+      const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
+      const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
+      f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
     }
+  } else {
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+      const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
+      const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
+      const bool bounce = (cy == 1 && y == 0) || (cy == -1 && y == ny - 1);
+      if (bounce)  // halfway bounce-back: the opposite population of this node
+        f[q] = S::load(static_cast<const Elem*>(v.src_q[opp(q)]), n, LAT::w(opp(q)));
+      else
+        f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
+    }
+  }
+
+  // ---- moments ----
+  T s0 = f[0], jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int q = 1; q < Q; q++) {
+    s0 += f[q];
+    if (LAT::c(q, 0) == 1) jx += f[q];
+    if (LAT::c(q, 0) == -1) jx -= f[q];
+    if (LAT::c(q, 1) == 1) jy += f[q];
+    if (LAT::c(q, 1) == -1) jy -= f[q];
+    if (D3 && LAT::c(q, 2) == 1) jz += f[q];
+    if (D3 && LAT::c(q, 2) == -1) jz -= f[q];
+  }
+  const T drho = S::DEV ? s0 : T(0);        // deviation of density
+  const T rho = S::DEV ? rho0p + s0 : s0;   // density
+  const T irho = T(1) / rho;
+  const T ux = jx * irho, uy = jy * irho, uz = jz * irho;
+  const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
+
+  // ---- plain BGK; f becomes f - f^eq ----
+  T out[Q];
+  {
+    const T a = pair_A<S::DEV, T>(T(LAT::w(0)), T(LAT::w(0)) * rho, drho, usq15, T(0));
+    f[0] -= a;
+    out[0] = (f[0] + a) - om * f[0];
+  }
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    const int q = 2 * k + 1;
+    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+    const T cu = cdot<T>(cx, cy, cz, ux, uy, uz);
+    const T wr = T(LAT::w(q)) * rho;
+    const T a = pair_A<S::DEV, T>(T(LAT::w(q)), wr, drho, usq15, cu);
+    const T b = (T(3) * wr) * cu;
+    const T fr = fq_of<S::DEV, T>(v, q) * rho;
+    const T fp = f[q], fm = f[q + 1];
+    f[q] = fp - (a + b);
+    f[q + 1] = fm - (a - b);
+    out[q] = fp - om * f[q] + fr;
+    out[q + 1] = fm - om * f[q + 1] - fr;
+  }
+  if (active && no == 0) {
+#pragma unroll
+    for (int q = 0; q < Q; q++) S::store(static_cast<Elem*>(v.dst_q[q]), n, out[q], LAT::w(q));
+  }
+
+  // ---- pack the covered nodes of the CTA ----
+  __shared__ T s_st[NS][128];
+  __shared__ int s_n[128], s_xyz[128], s_no[128], s_own[kMaxOwners][128];
+  __shared__ E s_e[kMaxOwners][128];
+  __shared__ int s_cnt[4];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned covered = __ballot_sync(FULL, no > 0);
+  __syncthreads();  // the previous call's packed state has been consumed
+  if (lane == 0) s_cnt[warp] = __popc(covered);
+  __syncthreads();
+  int base = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < 4; w++) {
+    base += w < warp ? s_cnt[w] : 0;
+    total += s_cnt[w];
+  }
+  if (no > 0) {
+    const int slot = base + __popc(covered & ((1u << lane) - 1u));
+#pragma unroll
+    for (int q = 0; q < Q; q++) s_st[q][slot] = f[q];
+    s_st[Q][slot] = rho;
+    s_st[Q + 1][slot] = drho;
+    s_st[Q + 2][slot] = ux;
+    s_st[Q + 3][slot] = uy;
+    s_st[Q + 4][slot] = uz;
+    s_n[slot] = n;
+    s_xyz[slot] = xx | (y << 16);  // x, y < 65536
+    s_no[slot] = no | (z << 8);
+#pragma unroll
+    for (int s = 0; s < kMaxOwners; s++) {
+      s_own[s][slot] = s < no ? own[s] : -1;
+      s_e[s][slot] = s < no ? eown[s] : E(0);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x >= ((total + 31) & ~31)) return;  // whole warps beyond the packed nodes
+
+  // ---------------- NT immersed moving boundary on packed nodes ----------------
+  const int slot = threadIdx.x;
+  const bool mine = slot < total;
+  const int ps = mine ? slot : 0;
+  const int cn = s_n[ps];
+  const int cx_ = s_xyz[ps] & 0xffff, cy_ = s_xyz[ps] >> 16, cz_ = s_no[ps] >> 8;
+  no = mine ? (s_no[ps] & 0xff) : 0;
+#pragma unroll
+  for (int s = 0; s < kMaxOwners; s++) {
+    own[s] = s_own[s][ps];
+    eown[s] = s_e[s][ps];
+  }
+  // sort owners by id
+#pragma unroll
+  for (int a = 1; a < kMaxOwners; a++) {
+    if (a < no) {
+      int k = own[a];
+      E ek = eown[a];
+      int b = a - 1;
+      while (b >= 0 && own[b] > k) {
+        own[b + 1] = own[b];
+        eown[b + 1] = eown[b];
+        b--;
+      }
+      own[b + 1] = k;
+      eown[b + 1] = ek;
+    }
+  }
+  T g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) g[q] = s_st[q][ps];
+  const T crho = s_st[Q][ps], cdrho = s_st[Q + 1][ps];
+  const T cux = s_st[Q + 2][ps], cuy = s_st[Q + 3][ps], cuz = s_st[Q + 4][ps];
+  const T cusq15 = T(1.5) * (cux * cux + cuy * cuy + cuz * cuz);
+  {
     // solid velocity at the node; particle arithmetic in FP64 for FP64
     // storage, in FP32 (from the per-particle FP32 kinematics record)
     // otherwise
@@ -282,16 +352,16 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
         const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
         const float4 vp = __ldg(kp + 2);
         const float4 wp = __ldg(kp + 3);
-        r0 = min_image_f(float(xx - ir.x) - fr.x, nx, true);
-        r1 = min_image_f(float(y - ir.y) - fr.y, ny, !v.wall_y);
-        r2 = D3 ? min_image_f(float(z - ir.z) - fr.z, nz, true) : 0.f;
+        r0 = min_image_f(float(cx_ - ir.x) - fr.x, nx, true);
+        r1 = min_image_f(float(cy_ - ir.y) - fr.y, ny, !v.wall_y);
+        r2 = D3 ? min_image_f(float(cz_ - ir.z) - fr.z, nz, true) : 0.f;
         V0 = vp.x + (wp.y * r2 - wp.z * r1);
         Vy = vp.y + (wp.z * r0 - wp.x * r2);
         V2 = vp.z + (wp.x * r1 - wp.y * r0);
       } else {
-        r0 = min_image((double)xx - v.pos[3 * p], nx, true);
-        r1 = min_image((double)y - v.pos[3 * p + 1], ny, !v.wall_y);
-        r2 = D3 ? min_image((double)z - v.pos[3 * p + 2], nz, true) : 0.0;
+        r0 = min_image((double)cx_ - v.pos[3 * p], nx, true);
+        r1 = min_image((double)cy_ - v.pos[3 * p + 1], ny, !v.wall_y);
+        r2 = D3 ? min_image((double)cz_ - v.pos[3 * p + 2], nz, true) : 0.0;
         const double* w = v.omg + 3 * p;
         const double* vp = v.vel + 3 * p;
         V0 = vp[0] + (w[1] * r2 - w[2] * r1);
@@ -331,29 +401,40 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
     }
     const T vsq15 = T(1.5) * (VSx * VSx + VSy * VSy + VSz * VSz);
     T mx = T(0), my = T(0), mz = T(0);
+    T res[Q];
     {
-      const T AS0 = pair_A<S::DEV, T>(T(LAT::w(0)), T(LAT::w(0)) * rho, drho, vsq15, T(0));
-      const T Om0 = AS0 - A[0];  // f_0 - f_0 cancels
-      out[0] += beta * (om * neq[0] + Om0);
+      const T w0r = T(LAT::w(0)) * crho;
+      const T a = pair_A<S::DEV, T>(T(LAT::w(0)), w0r, cdrho, cusq15, T(0));
+      const T AS0 = pair_A<S::DEV, T>(T(LAT::w(0)), w0r, cdrho, vsq15, T(0));
+      const T Om0 = AS0 - a;  // f_0 - f_0 cancels
+      res[0] = (g[0] + a) - om * g[0] + beta * (om * g[0] + Om0);
     }
 #pragma unroll
     for (int k = 0; k < NP; k++) {
       const int q = 2 * k + 1;
       const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
-      const T wr = T(LAT::w(q)) * rho;
+      const T wr = T(LAT::w(q)) * crho;
+      const T cu = cdot<T>(cx, cy, cz, cux, cuy, cuz);
+      const T a = pair_A<S::DEV, T>(T(LAT::w(q)), wr, cdrho, cusq15, cu);
+      const T b = (T(3) * wr) * cu;
       const T cv = cdot<T>(cx, cy, cz, VSx, VSy, VSz);
-      const T AS = pair_A<S::DEV, T>(T(LAT::w(q)), wr, drho, vsq15, cv);
+      const T AS = pair_A<S::DEV, T>(T(LAT::w(q)), wr, cdrho, vsq15, cv);
       const T BS = (T(3) * wr) * cv;
+      const T fr = fq_of<S::DEV, T>(v, q) * crho;
       // Omega^S_q = f_{-q} - f_q + feq_q(rho, V_S) - feq_{-q}(rho, u)
-      const T dA = AS - A[k + 1];
-      const T Omp = (neq[q + 1] - neq[q]) + (dA + (BS - B[k + 1]));
-      const T Omm = (neq[q] - neq[q + 1]) + (dA - (BS - B[k + 1]));
-      out[q] += beta * (om * neq[q] + Omp);
-      out[q + 1] += beta * (om * neq[q + 1] + Omm);
+      const T dA = AS - a;
+      const T Omp = (g[q + 1] - g[q]) + (dA + (BS - b));
+      const T Omm = (g[q] - g[q + 1]) + (dA - (BS - b));
+      res[q] = (g[q] + (a + b)) - om * g[q] + fr + beta * (om * g[q] + Omp);
+      res[q + 1] = (g[q + 1] + (a - b)) - om * g[q + 1] - fr + beta * (om * g[q + 1] + Omm);
       const T dm = Omp - Omm;  // c_{q+1} = -c_q
       if (cx) mx += T(cx) * dm;
       if (cy) my += T(cy) * dm;
       if (cz) mz += T(cz) * dm;
+    }
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < Q; q++) S::store(static_cast<Elem*>(v.dst_q[q]), cn, res[q], LAT::w(q));
     }
     // momentum given to the fluid m = beta sum_i Omega_i^S c_i; the force on
     // the particles is -m, split by covered fraction (Eq. 3 and reading)
@@ -385,12 +466,8 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
     }
     if (!(esum > PT(0))) key = -1;
     warp_reduce_to_particles<PT>(key, val, v.ff, v.tf);
-  }
+}
 
-  if (active) {
-#pragma unroll
-    for (int q = 0; q < Q; q++) S::store(dst + q * plane, n, out[q], LAT::w(q));
-  }
 }
 
 }  // namespace lbm

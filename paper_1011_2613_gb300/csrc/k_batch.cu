@@ -110,11 +110,22 @@ __global__ void __launch_bounds__(128) batch_step_kernel(BatchArgs a) {
   }
   if (!grid_barrier(a)) return;
 
-  // C: collision tiles, contacts
+  // C: collision tiles, contacts.  The member's view is staged in shared
+  // memory (the collision reads its per-direction plane pointers per access).
+  __shared__ View sv;
+  int cached = -1;
   const int ty = 128 / a.tile_x;
   for (int t = blockIdx.x; t < NT; t += gridDim.x) {
     const int m = member_of(a.tile_off, a.nm, t);
-    const View& v = a.views[m];
+    if (m != cached) {
+      __syncthreads();
+      const int* from = reinterpret_cast<const int*>(a.views + m);
+      int* to = reinterpret_cast<int*>(&sv);
+      for (int w = threadIdx.x; w < (int)(sizeof(View) / sizeof(int)); w += blockDim.x) to[w] = from[w];
+      __syncthreads();
+      cached = m;
+    }
+    const View& v = sv;
     const int local = t - a.tile_off[m];
     const int tx = a.tiles_x[m];
     const int x = (local % tx) * a.tile_x + threadIdx.x % a.tile_x;
@@ -163,9 +174,9 @@ static const void* batch_kernel(int dim, int storage) {
 // co-resident CTAs of the batch kernel (0 on error)
 int batch_max_grid(int dim, int storage, int smem) {
   const void* k = batch_kernel(dim, storage);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-    return 0;
+  // static shared memory (collision packing, raster tables) comes on top of
+  // the dynamic raster tables: always opt in to the dynamic size
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, (size_t)smem) != cudaSuccess) return 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;

@@ -60,9 +60,12 @@ struct View {
   // lattice geometry
   int dim, Q, nx, ny, nz, pitch, wall_y, storage;
   long long plane;  // elements per population plane = pitch * ny * nz
-  // populations: src is read (pull), dst written
+  // populations: src is read (pull), dst written; per-direction plane
+  // bases (fsrc + q * plane elements), filled by the host with fsrc/fdst
   void* fsrc;
   void* fdst;
+  const void* src_q[19];
+  void* dst_q[19];
   // solid-fraction slots; eps element type follows the storage (double for
   // F64, float otherwise)
   int* own[kMaxOwners];
@@ -93,6 +96,8 @@ struct View {
   // scratch for reductions (totals)
   double* red;
 };
+
+static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
 
 // ---------------------------------------------------------------------------
 // Launchers (one per kernel family; each in its own translation unit).
