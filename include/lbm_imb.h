@@ -276,6 +276,64 @@ int lbm_imb_dem_forces_static(int32_t dim, const int32_t* extent, int32_t wall_y
                               const double* mass, double k_n, double restitution,
                               double* fc, void* stream);
 
+/* ---- learned drag closure ----
+ * Not in the paper.  The paper compares the drag it resolves with Wen-Yu and
+ * EMMS closures (section "Simulation results"); here the resolved forces of
+ * the method are used to train a small network that predicts a particle's
+ * drag from its surroundings, and the resolved solve judges its error.
+ *
+ * Drag samples: for every particle of a simulation, features
+ *   [0] mean solid fraction eps over the nodes at distance (R, R + shell]
+ *       from the centre (minimum image),
+ *   [1..3] slip velocity u_shell - v_p, where u_shell is the (1 - eps)
+ *       weighted mean fluid velocity over the same nodes,
+ *   [4] particle Reynolds number |slip| 2R / nu, nu = (tau - 1/2)/3,
+ *   [5] density ratio rho_s / rho_fluid,
+ * and target F_f / (6 pi rho_fluid nu R) (3D) or F_f / (4 pi rho_fluid nu)
+ * (2D), with F_f the hydrodynamic force of the last step (Eq. 3).  u_dev and
+ * eps_dev are device arrays from lbm_imb_fields(..., on_device = 1): u
+ * [dim][N], eps [N].  feats [n][6], target [n][3]: device FP32, caller-owned,
+ * cap >= n particles.  Enqueued on the handle's stream. */
+int lbm_imb_drag_samples(lbm_imb_t* h, const double* u_dev, const double* eps_dev, double shell,
+                         float* feats, float* target, int64_t cap);
+
+/* The network: 6 -> 128 -> 128 -> 128 -> 128 -> 3, ReLU, BF16 tensor-core
+ * products with FP32 accumulation, FP32 master weights trained by Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error of normalised
+ * targets.  Inputs and outputs are normalised inside with the statistics set
+ * by lbm_imb_mlp_set_normalization (identity until then).  Parameters
+ * (FP32, flat): for each layer l = 1..5, W_l [out][in] then b_l [out]. */
+typedef struct lbm_imb_mlp lbm_imb_mlp_t;
+
+/* Device bytes for a network that trains on minibatches of up to max_batch. */
+size_t lbm_imb_mlp_required_bytes(int64_t max_batch);
+/* Lay out the network in the caller's device block (256-byte aligned), He
+ * initial weights from seed.  Calls run on cuda_stream. */
+int lbm_imb_mlp_init(void* dev_buf, size_t bytes, int64_t max_batch, uint64_t seed,
+                     void* cuda_stream, lbm_imb_mlp_t** out);
+int lbm_imb_mlp_num_params(int* n);
+int lbm_imb_mlp_set_params(lbm_imb_mlp_t* m, const float* host_params);
+int lbm_imb_mlp_get_params(lbm_imb_mlp_t* m, float* host_params);
+int lbm_imb_mlp_set_normalization(lbm_imb_mlp_t* m, const float* x_mean, const float* x_std,
+                                  const float* y_mean, const float* y_std);
+/* y [n][3] (device) = network(x [n][6] device), denormalised.  Synchronises. */
+int lbm_imb_mlp_predict(lbm_imb_mlp_t* m, const float* x, float* y, int64_t n);
+/* Gradients of the minibatch loss w.r.t. the parameters (host, flat order)
+ * and the loss, without changing the parameters. */
+int lbm_imb_mlp_gradients(lbm_imb_mlp_t* m, const float* x, const float* t, int64_t batch,
+                          float* host_grads, float* host_loss);
+/* steps Adam steps on consecutive minibatches of the device dataset x [n][6],
+ * t [n][3] (wrapping at the end); *last_loss = loss of the last minibatch. */
+int lbm_imb_mlp_train_steps(lbm_imb_mlp_t* m, const float* x, const float* t, int64_t n,
+                            int64_t batch, int64_t steps, float lr, float* last_loss);
+int lbm_imb_mlp_destroy(lbm_imb_mlp_t* m);
+/* Test hook for the tensor-core operand layout: D [128][N] = A [128][K] *
+ * B [N][K]^T with BF16 host inputs (raw bits, row-major) and FP32 host
+ * output, through one tcgen05 product; dev_scratch >= 128 KB + 256,
+ * 256-byte aligned; N, K in {16, 32, ..., 128}. */
+int lbm_imb_mlp_probe_gemm(const uint16_t* a_host, const uint16_t* b_host, int N, int K,
+                           float* d_host, void* dev_scratch, size_t scratch_bytes, void* stream);
+
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */
 int lbm_imb_destroy(lbm_imb_t* h);

@@ -95,3 +95,46 @@ class Adam:
             v *= self.beta2
             v += (1.0 - self.beta2) * g * g
             p -= lr * (m / c1) / (np.sqrt(v / c2) + self.eps)
+
+
+def drag_samples(sim, shell: float = 5.0):
+    """Features and targets of every particle of an OracleSim, by their
+    definition (see the library header): nodes at distance (R, R + shell]
+    from the centre (minimum image; outside walls skipped), mean eps,
+    (1 - eps)-weighted mean fluid velocity, slip, Reynolds number, density
+    ratio; target = force / Stokes scale."""
+    rho, u, eps = sim.fields()
+    p = sim.particles()
+    m, _ = sim.masses()
+    dim = sim.dim
+    nx, ny, nz = sim.shape
+    tau = sim.tau
+    nu = (tau - 0.5) / 3.0
+    rho0 = sim.rho0
+    wall = sim.wall_y
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    coords = [X, Y, Z]
+    feats = np.zeros((sim.np, 6))
+    tgt = np.zeros((sim.np, 3))
+    for k in range(sim.np):
+        R = float(sim.radius[k])
+        c = p["pos"][k]
+        d2 = np.zeros(X.shape)
+        for d in range(dim):
+            r = coords[d] - c[d]
+            if not (d == 1 and wall):
+                L = (nx, ny, nz)[d]
+                r = np.where(r > L / 2, r - L, np.where(r < -L / 2, r + L, r))
+            d2 += r * r
+        sel = (d2 > R * R) & (d2 <= (R + shell) ** 2)
+        e = eps[sel]
+        wgt = 1.0 - e
+        us = np.array([(wgt * u[d][sel]).sum() / wgt.sum() if wgt.sum() > 0 else 0.0 for d in range(dim)]
+                      + [0.0] * (3 - dim))
+        slip = us - p["vel"][k]
+        vol = 4.0 / 3.0 * np.pi * R ** 3 if dim == 3 else np.pi * R * R
+        scale = 6 * np.pi * rho0 * nu * R if dim == 3 else 4 * np.pi * rho0 * nu
+        feats[k] = [e.mean() if e.size else 0.0, slip[0], slip[1], slip[2],
+                    np.linalg.norm(slip) * 2 * R / nu, m[k] / vol / rho0]
+        tgt[k] = p["force"][k] / scale
+    return feats, tgt

@@ -186,6 +186,10 @@ class OracleSim:
                                    _p(pos), _p(vel), _p(omg), _p(rad), _p(rhos))
         self.N = lib.oracle_num_nodes(self.h)
         self.Q = lib.oracle_num_dirs(self.h)
+        self.tau = float(cfg.tau)
+        self.rho0 = float(cfg.rho_fluid)
+        self.wall_y = int(cfg.wall_y)
+        self.radius = np.asarray(cfg.radius, dtype=np.float64).copy()
         self.steps_done = 0
         del npa
 

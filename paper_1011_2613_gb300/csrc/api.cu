@@ -924,6 +924,15 @@ int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum, dou
   return read_err(h);
 }
 
+int lbm_imb_drag_samples(lbm_imb_t* h, const double* u_dev, const double* eps_dev, double shell, float* feats,
+                         float* target, int64_t cap) {
+  if (!h || h->is_batch || !u_dev || !eps_dev || !feats || !target || cap < h->np || !(shell > 0.0))
+    return LBM_IMB_EINVAL;
+  View v = view_of(h, h->cur);
+  lbm::launch_drag_samples(v, u_dev, eps_dev, shell, feats, target, h->stream);
+  return check_cuda(cudaGetLastError());
+}
+
 int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps) {
   if (!h || !steps) return LBM_IMB_EINVAL;
   *steps = h->steps;

@@ -118,5 +118,7 @@ void launch_get_populations(const View& v, const void* f, long long row0, long l
 void launch_set_populations(const View& v, void* f, long long row0, long long nrows, const double* in,
                             cudaStream_t s);
 void launch_totals(const View& v, const void* f, cudaStream_t s);
+void launch_drag_samples(const View& v, const double* u, const double* eps, double shell, float* feats,
+                         float* target, cudaStream_t s);
 
 }  // namespace lbm
