@@ -190,3 +190,107 @@ def flat_to_layers(flat, sizes=(6, 128, 128, 128, 128, 3)):
 
 def layers_to_flat(W, b):
     return np.concatenate([np.concatenate([w.reshape(-1), bb]) for w, bb in zip(W, b)]).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# the closure experiment: samples from resolved runs, training, evaluation
+# ---------------------------------------------------------------------------
+def drag_dataset(phis, seeds, n=128, transient=2000, every=200, snapshots=10, shell=5.0, storage="f32dev"):
+    """Resolved D3Q19 periodic suspensions at each solid fraction and seed;
+    after ``transient`` steps, drag samples of every particle every ``every``
+    steps, ``snapshots`` times.  Returns (features (S,6), targets (S,3),
+    seed label (S,), phi label (S,)) as CUDA tensors / numpy labels, and the
+    resolved cost in seconds per particle-step."""
+    import time
+
+    import torch
+
+    from . import inputs as I
+    from .lbm import Simulation
+
+    feats, tgts, sl, pl = [], [], [], []
+    t_steps = 0.0
+    particle_steps = 0
+    for phi in phis:
+        for sd in seeds:
+            cfg = I.closure_config(phi, sd, n=n, storage=storage)
+            sim = Simulation(cfg)
+            sim.step(transient)
+            for _ in range(snapshots):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sim.step(every)
+                sim.sync()
+                t_steps += time.perf_counter() - t0
+                particle_steps += every * cfg.n_particles
+                f, t = drag_samples(sim, shell)
+                feats.append(f.clone())
+                tgts.append(t.clone())
+                sl.append(np.full(cfg.n_particles, sd))
+                pl.append(np.full(cfg.n_particles, phi))
+            sim.close()
+            del sim
+    return (torch.cat(feats), torch.cat(tgts), np.concatenate(sl), np.concatenate(pl),
+            t_steps / max(particle_steps, 1))
+
+
+def wen_yu_fit(x, t):
+    """Least-squares fit of a Wen-Yu-form drag law to the samples:
+    F / (6 pi mu R) = s (1 - phi)^(-k) (1 + 0.15 Re^0.687) + c,
+    with s the slip vector, fitting the voidage exponent k by a scan and the
+    constant vector c (pressure-gradient part) by least squares.  Returns a
+    predictor f(x) -> (n,3)."""
+    x = np.asarray(x, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    phi, s, re = x[:, 0], x[:, 1:4], x[:, 4]
+    base = (1.0 + 0.15 * np.power(np.maximum(re, 0.0), 0.687))[:, None] * s
+    best = None
+    for k in np.linspace(0.0, 6.0, 121):
+        g = base * np.power(np.clip(1.0 - phi, 1e-3, 1.0), -k)[:, None]
+        c = (t - g).mean(axis=0)
+        err = np.sum((t - g - c) ** 2)
+        if best is None or err < best[0]:
+            best = (err, k, c)
+    _, k, c = best
+
+    def predict(xx):
+        xx = np.asarray(xx, dtype=np.float64)
+        gg = (1.0 + 0.15 * np.power(np.maximum(xx[:, 4], 0.0), 0.687))[:, None] * xx[:, 1:4]
+        return gg * np.power(np.clip(1.0 - xx[:, 0], 1e-3, 1.0), -k)[:, None] + c
+
+    predict.k = k
+    predict.c = c
+    return predict
+
+
+def rel_error(pred, t) -> float:
+    """|| pred - t || / || t || over all samples and components."""
+    pred = np.asarray(pred, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    return float(np.linalg.norm(pred - t) / np.linalg.norm(t))
+
+
+def train_closure(x, t, batch=8192, epochs=30, lr=1e-3, seed=0, max_batch=None):
+    """Train the network on CUDA tensors x (S,6), t (S,3): normalisation from
+    the training set (zero spreads replaced by 1), shuffled once, then
+    consecutive minibatches.  Returns (mlp, seconds, last loss)."""
+    import time
+
+    import torch
+
+    S = x.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    perm = torch.randperm(S, generator=g).to(x.device)
+    xs, ts = x[perm].contiguous(), t[perm].contiguous()
+    xm, xsd = xs.mean(0).cpu().numpy(), xs.std(0).cpu().numpy()
+    ym, ysd = ts.mean(0).cpu().numpy(), ts.std(0).cpu().numpy()
+    xsd[xsd <= 1e-12] = 1.0
+    ysd[ysd <= 1e-12] = 1.0
+    mlp = MLP(max_batch=max_batch or batch, seed=seed)
+    mlp.set_normalization(xm, xsd, ym, ysd)
+    steps = max(1, epochs * S // batch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = mlp.train(xs, ts, batch=min(batch, S), steps=steps, lr=lr)
+    torch.cuda.synchronize()
+    return mlp, time.perf_counter() - t0, loss
