@@ -174,6 +174,19 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def job_value(ms_local, nodes_local, steps, world, dist=None, device=None):
+    """Whole-job throughput under weak scaling: every rank advances its own
+    suspension of nodes_local nodes for ``steps`` steps; the job time is the
+    slowest rank's (all-reduce MAX).  Returns (MLUPS of the job, job ms)."""
+    ms = float(ms_local)
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * nodes_local * steps / (ms * 1e-3) / 1e6, ms
+
+
 def time_graph_steps(sim, torch, steps):
     s = sim.stream
     e0 = torch.cuda.Event(enable_timing=True)
@@ -197,8 +210,14 @@ def owned_fraction(sim, torch):
 
 
 def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=None):
+    """One storage form on the same workload: tuned collide kernel form,
+    graph-timed steps, per-kernel times, and (with ref_sim) its error against
+    the FP64 run at the same step count."""
     from paper_1011_2613_gb300 import lbm as L
+    from paper_1011_2613_gb300 import autotune
     sim = L.Simulation(cfg)
+    tune, cached = autotune.tuned_collide(sim)
+    done = 0 if cached else 3 * len(autotune.COLLIDE_VARIANTS)
     sim.step(args.warmup)
     sim.sync()
     ms = time_graph_steps(sim, torch, args.steps)
@@ -209,18 +228,23 @@ def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=N
     achieved = bpl * cfg.n_nodes / (t_coll * 1e-3) / 1e9
     res = {"mlups": cfg.n_nodes * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
            "collide_ms": t_coll, "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
-           "bytes_per_lup": bpl, "collide_gbs": achieved, "hbm_frac": achieved / peaks["hbm_gbs"]}
+           "bytes_per_lup": bpl, "collide_gbs": achieved, "hbm_frac": achieved / peaks["hbm_gbs"],
+           "collide_variant": tune["variant"], "collide_tuning": tune.get("table")}
     if ref_sim is not None:
-        done = args.warmup + 2 * args.steps
+        done += args.warmup + 2 * args.steps
         if steps_target > done:
             sim.step(steps_target - done)
+        elif done > steps_target:  # tuning ran extra steps: bring the FP64 run level
+            ref_sim.step(done - steps_target)
+            steps_target = done
         sim.sync()
+        ref_sim.sync()
         res.update(compare_to(ref_sim, sim, torch))
         res["error_after_steps"] = steps_target
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    return res
+    return res, steps_target
 
 
 def measure_batch(args, torch, peaks, n=32, seed=4):
@@ -351,7 +375,10 @@ def run_ours(args):
     cfg = wl["make"](3 + rank)
     cfg.storage = args.storage
 
+    from paper_1011_2613_gb300 import autotune
     sim = L.Simulation(cfg)
+    tune, cached = autotune.tuned_collide(sim)
+    tuned_steps = 0 if cached else 3 * len(autotune.COLLIDE_VARIANTS)
     sim.step(args.warmup)
     sim.sync()
     launches = sim.launches_per_step() * args.steps
@@ -360,12 +387,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         ms = time_graph_steps(sim, torch, args.steps)
+    value, ms = job_value(ms, cfg.n_nodes, args.steps, world, dist if world > 1 else None, "cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * cfg.n_nodes * args.steps / (ms * 1e-3) / 1e6
 
     # per-kernel device times (events between kernel families)
     kms, tot = sim.step_profiled(args.steps)
@@ -401,10 +425,11 @@ def run_ours(args):
 
     variants = {}
     if not args.no_variants and rank == 0 and cfg.storage == "f64":
-        steps_done = args.warmup + 2 * args.steps + (args.steps if e2e else 0)
+        steps_done = tuned_steps + args.warmup + 2 * args.steps + (args.steps if e2e else 0)
         for st in ("f32dev", "f16dev"):
             try:
-                variants[st] = measure_variant(cfg.replace(storage=st), args, torch, peaks, st, sim, steps_done)
+                variants[st], steps_done = measure_variant(cfg.replace(storage=st), args, torch, peaks, st, sim,
+                                                           steps_done)
             except Exception as ex:  # report, keep the headline line
                 variants[st] = {"error": str(ex)}
 
@@ -442,6 +467,7 @@ def run_ours(args):
                          "owned_fraction": fo, "peak_src": peaks["src"]},
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "profiled_ms_per_step": tot / args.steps,
+            "collide_variant": tune["variant"], "collide_tuning": tune.get("table"),
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": e2e,

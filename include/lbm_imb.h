@@ -153,6 +153,15 @@ int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* to
 /* Number of kernel launches one time step issues (for launch accounting). */
 int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
 
+/* Kernel form of the collision step (results are the same; the speed
+ * depends on lattice, storage and GPU; the autotuner times them):
+ *   0 one node per thread (default), 1 the same with a register budget for
+ *   8 CTAs per SM, 2 a persistent form that bulk-copies (TMA) the next row
+ *   tile's source rows into shared memory while colliding the current one
+ *   (reduced-precision storages only; FP64 falls back to 0).
+ * Not for batch members or batches. */
+int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
+
 /* Wait for the handle's stream and report device-side errors. */
 int lbm_imb_sync(lbm_imb_t* h);
 

@@ -97,3 +97,49 @@ def tuned_batch(cfgs, device=None, path: str | None = None, steps: int = 3):
     cache[key] = {k: rec[k] for k in ("tile_x", "blocks_per_sm", "ms_per_step")}
     save_cache(cache, path)
     return batch, rec, False
+
+
+COLLIDE_VARIANTS = (0, 1, 2)
+
+
+def collide_signature(cfg, device_name: str) -> str:
+    return "|".join(["collide", device_name, f"d{cfg.dim}", str(cfg.storage),
+                     f"n{int(math.log2(max(cfg.n_nodes, 1)))}", f"p{int(math.log2(max(cfg.n_particles, 1)))}"])
+
+
+def tune_collide(sim, steps: int = 2, variants=COLLIDE_VARIANTS) -> dict:
+    """Time every collide kernel form on ``sim`` (real steps: the simulation
+    advances) and leave it on the fastest.  Returns {"variant", "table"}."""
+    table = []
+    for var in variants:
+        try:
+            sim.set_collide_variant(var)
+            sim.step(1)
+            sim.sync()
+            kms, _ = sim.step_profiled(steps)
+        except Exception as ex:
+            table.append({"variant": var, "error": str(ex)})
+            continue
+        table.append({"variant": var, "collide_ms": kms["collide"] / steps})
+    ok = [r for r in table if "collide_ms" in r]
+    if not ok:
+        raise RuntimeError("no collide variant could be timed")
+    best = min(ok, key=lambda r: r["collide_ms"])
+    sim.set_collide_variant(best["variant"])
+    return {"variant": best["variant"], "table": table}
+
+
+def tuned_collide(sim, path: str | None = None, steps: int = 2) -> tuple[dict, bool]:
+    """Apply the cached collide variant for this configuration, or tune and
+    cache it.  Returns (record, from_cache)."""
+    import torch
+
+    key = collide_signature(sim.cfg, torch.cuda.get_device_name(sim.device))
+    cache = load_cache(path)
+    if key in cache:
+        sim.set_collide_variant(cache[key]["variant"])
+        return cache[key], True
+    rec = tune_collide(sim, steps=steps)
+    cache[key] = {"variant": rec["variant"], "table": rec["table"]}
+    save_cache(cache, path)
+    return rec, False

@@ -933,6 +933,19 @@ int lbm_imb_drag_samples(lbm_imb_t* h, const double* u_dev, const double* eps_de
   return check_cuda(cudaGetLastError());
 }
 
+int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant) {
+  if (!h || h->is_member || variant < 0 || variant > 2) return LBM_IMB_EINVAL;
+  if (h->is_batch) return LBM_IMB_EUNSUPPORTED;
+  if (h->graphs_ok) {
+    cudaGraphExecDestroy(h->graph[0]);
+    cudaGraphExecDestroy(h->graph[1]);
+  }
+  h->graphs_ok = false;
+  h->graphs_tried = false;
+  h->v.collide_variant = variant;
+  return LBM_IMB_OK;
+}
+
 int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps) {
   if (!h || !steps) return LBM_IMB_EINVAL;
   *steps = h->steps;

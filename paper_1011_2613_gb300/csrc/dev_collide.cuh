@@ -15,6 +15,7 @@ struct Storage<LBM_IMB_STORE_F64> {
   using E = double;  // eps slot element
   static constexpr bool DEV = false;
   __device__ static __forceinline__ T load(const Elem* p, int i, double) { return __ldg(p + i); }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i, double) { return p[i]; }
   __device__ static __forceinline__ void store(Elem* p, int i, T v, double) { p[i] = v; }
 };
 template <>
@@ -24,6 +25,7 @@ struct Storage<LBM_IMB_STORE_F32DEV> {
   using E = float;
   static constexpr bool DEV = true;
   __device__ static __forceinline__ T load(const Elem* p, int i, double) { return __ldg(p + i); }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i, double) { return p[i]; }
   __device__ static __forceinline__ void store(Elem* p, int i, T v, double) { p[i] = v; }
 };
 template <>
@@ -35,6 +37,9 @@ struct Storage<LBM_IMB_STORE_F16DEV> {
   // stored value = g / w (keeps the diagonal deviations out of subnormals)
   __device__ static __forceinline__ T load(const Elem* p, int i, double w) {
     return __half2float(__ldg(p + i)) * float(w);
+  }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i, double w) {
+    return __half2float(p[i]) * float(w);
   }
   __device__ static __forceinline__ void store(Elem* p, int i, T v, double w) {
     p[i] = __float2half_rn(v * float(1.0 / w));
@@ -144,9 +149,11 @@ __device__ __forceinline__ double min_image(double d, int n, bool periodic) {
 //   f*_i - f*_i(plain) = beta (omega (f_i - f^eq_i) + Omega^S_i),
 //   Omega^S_i = (f - f^eq)_{-i} - (f - f^eq)_i + f^eq_i(rho, V_S) - f^eq_i(rho, u)
 // (Eq. 1 with the Omega^S term rearranged) and the Eq. 3 force/torque.
+// The collision of one node from its pulled populations f (see collide_node).
 template <class LAT, int STORE>
-__device__ __forceinline__ void collide_node(const View& v, const int xx, const int y, const int z,
-                                             const bool active) {
+__device__ __forceinline__ void collide_core(const View& v, const int xx, const int y, const int z,
+                                             const bool active, const int n,
+                                             typename Storage<STORE>::T (&f)[LAT::Q]) {
   using S = Storage<STORE>;
   using T = typename S::T;
   using E = typename S::E;
@@ -155,13 +162,10 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
   constexpr int NP = (Q - 1) / 2;  // opposite pairs
   constexpr bool D3 = LAT::DIM == 3;
   constexpr int NS = Q + 5;        // packed state: f - f^eq, rho, drho, u
-
-  const int nx = v.nx, ny = v.ny, nz = v.nz, pitch = v.pitch;
-  const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
-  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-  const int n = (z * ny + y) * pitch + xx;
-
+  const int nx = v.nx, ny = v.ny, nz = v.nz;
+  (void)nx;
+  (void)ny;
+  (void)nz;
   T rho0p, om, tau_t;
   if constexpr (S::DEV) {
     rho0p = v.rho0_f;
@@ -172,7 +176,6 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
     om = v.omega;
     tau_t = v.tau;
   }
-
   // ---- owners of this node (slot s+1 is read only where slot s is taken) ----
   int own[kMaxOwners];
   E eown[kMaxOwners];
@@ -188,33 +191,6 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
           no = s + 1;
         }
       }
-    }
-  }
-
-  // ---- pull streaming; rows are whole warps, so the wall test is uniform ----
-  const int ry[3] = {y * pitch, ym * pitch, yp * pitch};
-  const int rz[3] = {z * ny * pitch, zm * ny * pitch, zp * ny * pitch};
-  T f[Q];
-  const bool wall_row = v.wall_y && (y == 0 || y == ny - 1);
-  if (!wall_row) {
-#pragma unroll
-    for (int q = 0; q < Q; q++) {
-      const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
-      const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
-      const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
-      f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < Q; q++) {
-      const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
-      const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
-      const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
-      const bool bounce = (cy == 1 && y == 0) || (cy == -1 && y == ny - 1);
-      if (bounce)  // halfway bounce-back: the opposite population of this node
-        f[q] = S::load(static_cast<const Elem*>(v.src_q[opp(q)]), n, LAT::w(opp(q)));
-      else
-        f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
     }
   }
 
@@ -468,6 +444,48 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
     warp_reduce_to_particles<PT>(key, val, v.ff, v.tf);
 }
 
+}
+
+template <class LAT, int STORE>
+__device__ __forceinline__ void collide_node(const View& v, const int xx, const int y, const int z,
+                                             const bool active) {
+  using S = Storage<STORE>;
+  using T = typename S::T;
+  using Elem = typename S::Elem;
+  constexpr int Q = LAT::Q;
+  const int nx = v.nx, ny = v.ny, nz = v.nz, pitch = v.pitch;
+  const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+  const int n = (z * ny + y) * pitch + xx;
+  // ---- pull streaming; rows are whole warps, so the wall test is uniform ----
+  const int ry[3] = {y * pitch, ym * pitch, yp * pitch};
+  const int rz[3] = {z * ny * pitch, zm * ny * pitch, zp * ny * pitch};
+  T f[Q];
+  const bool wall_row = v.wall_y && (y == 0 || y == ny - 1);
+  if (!wall_row) {
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+      const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
+      const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
+      f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+      const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
+      const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
+      const bool bounce = (cy == 1 && y == 0) || (cy == -1 && y == ny - 1);
+      if (bounce)  // halfway bounce-back: the opposite population of this node
+        f[q] = S::load(static_cast<const Elem*>(v.src_q[opp(q)]), n, LAT::w(opp(q)));
+      else
+        f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
+    }
+  }
+
+  collide_core<LAT, STORE>(v, xx, y, z, active, n, f);
 }
 
 }  // namespace lbm

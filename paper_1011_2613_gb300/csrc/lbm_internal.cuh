@@ -91,6 +91,7 @@ struct View {
   float tau_f, omega_f, rho0_f;
   float fq_f[19];
   int substeps;
+  int collide_variant;  // kernel form of the collision (0, 1, 2)
   // device error word
   int* err;
   // scratch for reductions (totals)

@@ -65,6 +65,8 @@ def lib():
             L.lbm_imb_step_profiled.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
             L.lbm_imb_launches_per_step.restype = C.c_int
             L.lbm_imb_launches_per_step.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+            L.lbm_imb_set_collide_variant.restype = C.c_int
+            L.lbm_imb_set_collide_variant.argtypes = [C.c_void_p, C.c_int]
             L.lbm_imb_sync.restype = C.c_int
             L.lbm_imb_sync.argtypes = [C.c_void_p]
             L.lbm_imb_particles.restype = C.c_int
@@ -250,6 +252,9 @@ class Simulation:
         _check(lib().lbm_imb_step_profiled(self.h, int(n), k, C.byref(t)), "lbm_imb_step_profiled")
         names = ("eps_clear", "eps_raster", "collide", "dem")
         return {nm: float(k[i]) for i, nm in enumerate(names)}, float(t.value)
+
+    def set_collide_variant(self, variant: int):
+        _check(lib().lbm_imb_set_collide_variant(self.h, int(variant)), "lbm_imb_set_collide_variant")
 
     def launches_per_step(self) -> int:
         x = C.c_int()
