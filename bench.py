@@ -209,6 +209,17 @@ def owned_fraction(sim, torch):
     return frac
 
 
+def pick_collide(sim, args):
+    """Collide kernel form: the one given on the command line, else the
+    autotuner's (cached or tuned now).  Returns (record, steps run by tuning)."""
+    from paper_1011_2613_gb300 import autotune
+    if args.collide_variant is not None:
+        sim.set_collide_variant(args.collide_variant)
+        return {"variant": args.collide_variant, "table": None}, 0
+    tune, cached = autotune.tuned_collide(sim)
+    return tune, 0 if cached else 3 * len(autotune.COLLIDE_VARIANTS)
+
+
 def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=None):
     """One storage form on the same workload: tuned collide kernel form,
     graph-timed steps, per-kernel times, and (with ref_sim) its error against
@@ -216,8 +227,7 @@ def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=N
     from paper_1011_2613_gb300 import lbm as L
     from paper_1011_2613_gb300 import autotune
     sim = L.Simulation(cfg)
-    tune, cached = autotune.tuned_collide(sim)
-    done = 0 if cached else 3 * len(autotune.COLLIDE_VARIANTS)
+    tune, done = pick_collide(sim, args)
     sim.step(args.warmup)
     sim.sync()
     ms = time_graph_steps(sim, torch, args.steps)
@@ -377,8 +387,7 @@ def run_ours(args):
 
     from paper_1011_2613_gb300 import autotune
     sim = L.Simulation(cfg)
-    tune, cached = autotune.tuned_collide(sim)
-    tuned_steps = 0 if cached else 3 * len(autotune.COLLIDE_VARIANTS)
+    tune, tuned_steps = pick_collide(sim, args)
     sim.step(args.warmup)
     sim.sync()
     launches = sim.launches_per_step() * args.steps
@@ -488,6 +497,8 @@ def main():
     ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS))
     ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--collide-variant", type=int, default=None,
+                    help="fix the collide kernel form instead of autotuning it")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -155,11 +155,19 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
 
 /* Kernel form of the collision step (results are the same; the speed
  * depends on lattice, storage and GPU; the autotuner times them):
- *   0 one node per thread (default), 1 the same with a register budget for
- *   8 CTAs per SM, 2 a persistent form that bulk-copies (TMA) the next row
- *   tile's source rows into shared memory while colliding the current one
- *   (reduced-precision storages only; FP64 falls back to 0).
- * Not for batch members or batches. */
+ *   0 persistent CTAs walking row tiles, each warp queueing its covered
+ *   nodes in shared memory for the immersed-boundary update, with a
+ *   register budget for 4 CTAs per SM (default),
+ *   1 the same with a register budget for 8 CTAs per SM, 2 a form that
+ *   bulk-copies (TMA) the next row tile's source rows into shared memory
+ *   while colliding the current one (reduced-precision storages only; FP64
+ *   falls back to 0), 3 as 0 with a register budget for 6 CTAs per SM,
+ *   4 as 0 with the next row tile's populations pulled into registers
+ *   before the current one is collided, 5 the same with a budget for 3
+ *   CTAs per SM, 6 one CTA per row tile that packs its covered nodes into
+ *   full warps through shared memory (register budget for 8 CTAs per SM),
+ *   7 the same with a budget for 5 CTAs per SM.
+ * Returns EINVAL outside 0..7.  Not for batch members or batches. */
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
 
 /* Wait for the handle's stream and report device-side errors. */

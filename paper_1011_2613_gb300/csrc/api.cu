@@ -13,6 +13,7 @@ using lbm::View;
 
 namespace lbm {
 int batch_max_grid(int dim, int storage, int smem);
+int batch_queue_smem(int dim, int storage);
 int batch_sm_count();
 cudaError_t launch_batch_step(const View* views, int nm, const int* part_off, const int* tile_off,
                               const int* bin_off, const int* tiles_x, int tile_x, int dim, int storage,
@@ -306,7 +307,11 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
     }
     v.fq[q] = 3.0 * w * cg;
     v.fq_f[q] = (float)v.fq[q];
+    v.cg3[q] = 3.0 * cg;
+    v.cg3_f[q] = (float)v.cg3[q];
   }
+  v.omc = 1.0 - v.omega;
+  v.omc_f = (float)v.omc;
   v.tau_f = (float)v.tau;
   v.omega_f = (float)v.omega;
   v.rho0_f = (float)v.rho0;
@@ -601,6 +606,9 @@ int lbm_imb_batch_init(const lbm_imb_config* cfgs, int n, int tile_x, int blocks
       h->bsmem = lbm::eps_raster_smem_bytes(h->dim, h->v.storage, h->rmax_all);
       if (h->bsmem < 0) st = LBM_IMB_EUNSUPPORTED;
     }
+    // the collision phase reuses the dynamic shared memory for its queues
+    const int qb = lbm::batch_queue_smem(h->dim, h->v.storage);
+    if (!st && h->bsmem < qb) h->bsmem = qb;
   }
   if (!st) st = batch_configure(h, tile_x, blocks_per_sm);
   free(B);
@@ -934,7 +942,7 @@ int lbm_imb_drag_samples(lbm_imb_t* h, const double* u_dev, const double* eps_de
 }
 
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant) {
-  if (!h || h->is_member || variant < 0 || variant > 2) return LBM_IMB_EINVAL;
+  if (!h || h->is_member || variant < 0 || variant > 7) return LBM_IMB_EINVAL;
   if (h->is_batch) return LBM_IMB_EUNSUPPORTED;
   if (h->graphs_ok) {
     cudaGraphExecDestroy(h->graph[0]);

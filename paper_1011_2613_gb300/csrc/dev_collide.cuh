@@ -8,15 +8,23 @@ namespace lbm {
 
 template <int STORE>
 struct Storage;
+// load/store move the stored form; SCALED storages hold g_q / w_q (the
+// collision then works on h_q = g_q / w_q and never multiplies by w_q except
+// in the density and momentum sums)
 template <>
 struct Storage<LBM_IMB_STORE_F64> {
   using Elem = double;
   using T = double;
   using E = double;  // eps slot element
   static constexpr bool DEV = false;
-  __device__ static __forceinline__ T load(const Elem* p, int i, double) { return __ldg(p + i); }
-  __device__ static __forceinline__ T load_shared(const Elem* p, int i, double) { return p[i]; }
-  __device__ static __forceinline__ void store(Elem* p, int i, T v, double) { p[i] = v; }
+  static constexpr bool SCALED = false;
+  __device__ static __forceinline__ T load(const Elem* p, int i) { return __ldg(p + i); }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return p[i]; }
+  __device__ static __forceinline__ void store(Elem* p, int i, T v) { p[i] = v; }
+  __device__ static __forceinline__ void store2(Elem* p, Elem* r, int i, T a, T b) {
+    p[i] = a;
+    r[i] = b;
+  }
 };
 template <>
 struct Storage<LBM_IMB_STORE_F32DEV> {
@@ -24,9 +32,14 @@ struct Storage<LBM_IMB_STORE_F32DEV> {
   using T = float;
   using E = float;
   static constexpr bool DEV = true;
-  __device__ static __forceinline__ T load(const Elem* p, int i, double) { return __ldg(p + i); }
-  __device__ static __forceinline__ T load_shared(const Elem* p, int i, double) { return p[i]; }
-  __device__ static __forceinline__ void store(Elem* p, int i, T v, double) { p[i] = v; }
+  static constexpr bool SCALED = false;
+  __device__ static __forceinline__ T load(const Elem* p, int i) { return __ldg(p + i); }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return p[i]; }
+  __device__ static __forceinline__ void store(Elem* p, int i, T v) { p[i] = v; }
+  __device__ static __forceinline__ void store2(Elem* p, Elem* r, int i, T a, T b) {
+    p[i] = a;
+    r[i] = b;
+  }
 };
 template <>
 struct Storage<LBM_IMB_STORE_F16DEV> {
@@ -34,15 +47,16 @@ struct Storage<LBM_IMB_STORE_F16DEV> {
   using T = float;
   using E = float;
   static constexpr bool DEV = true;
-  // stored value = g / w (keeps the diagonal deviations out of subnormals)
-  __device__ static __forceinline__ T load(const Elem* p, int i, double w) {
-    return __half2float(__ldg(p + i)) * float(w);
-  }
-  __device__ static __forceinline__ T load_shared(const Elem* p, int i, double w) {
-    return __half2float(p[i]) * float(w);
-  }
-  __device__ static __forceinline__ void store(Elem* p, int i, T v, double w) {
-    p[i] = __float2half_rn(v * float(1.0 / w));
+  // stored value h = g / w (keeps the diagonal deviations out of subnormals)
+  static constexpr bool SCALED = true;
+  __device__ static __forceinline__ T load(const Elem* p, int i) { return __half2float(__ldg(p + i)); }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return __half2float(p[i]); }
+  __device__ static __forceinline__ void store(Elem* p, int i, T v) { p[i] = __float2half_rn(v); }
+  // two values converted by one paired instruction
+  __device__ static __forceinline__ void store2(Elem* p, Elem* r, int i, T a, T b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    p[i] = __low2half(h);
+    r[i] = __high2half(h);
   }
 };
 
@@ -106,18 +120,30 @@ __device__ __forceinline__ T cdot(int cx, int cy, int cz, T ux, T uy, T uz) {
   return r;
 }
 
-// feq_q = A +- B for the pair (q, q+1):  A = w rho (1 - 1.5 u.u + 4.5 cu^2)
-// (+ w drho in deviation form, without the w rho0 rest part)
-template <bool DEV, typename T>
-__device__ __forceinline__ T pair_A(T w, T wr, T drho, T usq15, T cu) {
-  if constexpr (DEV) return w * drho + wr * (T(4.5) * cu * cu - usq15);
-  else return wr * ((T(1) - usq15) + T(4.5) * cu * cu);
-}
-
 template <bool DEV, typename T>
 __device__ __forceinline__ T fq_of(const View& v, int q) {
   if constexpr (DEV) return v.fq_f[q];
   else return v.fq[q];
+}
+
+template <bool DEV, typename T>
+__device__ __forceinline__ T cg3_of(const View& v, int q) {
+  if constexpr (DEV) return v.cg3_f[q];
+  else return v.cg3[q];
+}
+
+// j_a += c_a (w) m for one opposite pair; the first non-zero term assigns
+// (after unrolling, `have` and the branches fold)
+template <bool SCALED, typename T>
+__device__ __forceinline__ void axis_acc(T& j, bool& have, int c, T wq, T m) {
+  if (c == 0) return;
+  if (SCALED) {
+    const T cw = c > 0 ? wq : -wq;
+    j = have ? fma(cw, m, j) : cw * m;
+  } else {
+    j = have ? (c > 0 ? j + m : j - m) : (c > 0 ? m : -m);
+  }
+  have = true;
 }
 
 __device__ __forceinline__ float min_image_f(float d, int n, bool periodic) {
@@ -136,319 +162,16 @@ __device__ __forceinline__ double min_image(double d, int n, bool periodic) {
   return d;
 }
 
-// One node per thread of the fused pull-stream + collision; the whole CTA
-// (128 threads, 4 full warps) calls it together.  Lanes outside the lattice
-// pass active = false with in-range coordinates.  Node offsets within a
-// population plane are 32-bit (the library rejects planes of 2^31 nodes or
-// more).
-//
-// Every thread computes the plain BGK update and stores it unless its node
-// is covered.  Covered nodes are then packed into the first lanes of the CTA
-// through shared memory (f - f^eq, rho, u per node), so the immersed-boundary
-// work runs on full warps; it adds the correction
-//   f*_i - f*_i(plain) = beta (omega (f_i - f^eq_i) + Omega^S_i),
-//   Omega^S_i = (f - f^eq)_{-i} - (f - f^eq)_i + f^eq_i(rho, V_S) - f^eq_i(rho, u)
-// (Eq. 1 with the Omega^S term rearranged) and the Eq. 3 force/torque.
-// The collision of one node from its pulled populations f (see collide_node).
+// ---------------------------------------------------------------------------
+// Pull streaming of one node: f_q(x) = f_q(x - c_q) of the source lattice,
+// or the halfway bounce-back f_q(x) = f_{-q}(x) where x - c_q lies beyond a
+// wall in y.  Node offsets within a population plane are 32-bit (the library
+// rejects planes of 2^31 nodes or more).  Lanes with load = false read
+// nothing (their f is zero).
+// ---------------------------------------------------------------------------
 template <class LAT, int STORE>
-__device__ __forceinline__ void collide_core(const View& v, const int xx, const int y, const int z,
-                                             const bool active, const int n,
-                                             typename Storage<STORE>::T (&f)[LAT::Q]) {
-  using S = Storage<STORE>;
-  using T = typename S::T;
-  using E = typename S::E;
-  using Elem = typename S::Elem;
-  constexpr int Q = LAT::Q;
-  constexpr int NP = (Q - 1) / 2;  // opposite pairs
-  constexpr bool D3 = LAT::DIM == 3;
-  constexpr int NS = Q + 5;        // packed state: f - f^eq, rho, drho, u
-  const int nx = v.nx, ny = v.ny, nz = v.nz;
-  (void)nx;
-  (void)ny;
-  (void)nz;
-  T rho0p, om, tau_t;
-  if constexpr (S::DEV) {
-    rho0p = v.rho0_f;
-    om = v.omega_f;
-    tau_t = v.tau_f;
-  } else {
-    rho0p = T(0);
-    om = v.omega;
-    tau_t = v.tau;
-  }
-  // ---- owners of this node (slot s+1 is read only where slot s is taken) ----
-  int own[kMaxOwners];
-  E eown[kMaxOwners];
-  int no = 0;
-  if (active) {
-#pragma unroll
-    for (int s = 0; s < kMaxOwners; s++) {
-      if (s == no) {
-        const int o = v.own[s][n];
-        if (o >= 0) {
-          own[s] = o;
-          eown[s] = static_cast<const E*>(v.eps[s])[n];
-          no = s + 1;
-        }
-      }
-    }
-  }
-
-  // ---- moments ----
-  T s0 = f[0], jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-  for (int q = 1; q < Q; q++) {
-    s0 += f[q];
-    if (LAT::c(q, 0) == 1) jx += f[q];
-    if (LAT::c(q, 0) == -1) jx -= f[q];
-    if (LAT::c(q, 1) == 1) jy += f[q];
-    if (LAT::c(q, 1) == -1) jy -= f[q];
-    if (D3 && LAT::c(q, 2) == 1) jz += f[q];
-    if (D3 && LAT::c(q, 2) == -1) jz -= f[q];
-  }
-  const T drho = S::DEV ? s0 : T(0);        // deviation of density
-  const T rho = S::DEV ? rho0p + s0 : s0;   // density
-  const T irho = T(1) / rho;
-  const T ux = jx * irho, uy = jy * irho, uz = jz * irho;
-  const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-
-  // ---- plain BGK; f becomes f - f^eq ----
-  T out[Q];
-  {
-    const T a = pair_A<S::DEV, T>(T(LAT::w(0)), T(LAT::w(0)) * rho, drho, usq15, T(0));
-    f[0] -= a;
-    out[0] = (f[0] + a) - om * f[0];
-  }
-#pragma unroll
-  for (int k = 0; k < NP; k++) {
-    const int q = 2 * k + 1;
-    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
-    const T cu = cdot<T>(cx, cy, cz, ux, uy, uz);
-    const T wr = T(LAT::w(q)) * rho;
-    const T a = pair_A<S::DEV, T>(T(LAT::w(q)), wr, drho, usq15, cu);
-    const T b = (T(3) * wr) * cu;
-    const T fr = fq_of<S::DEV, T>(v, q) * rho;
-    const T fp = f[q], fm = f[q + 1];
-    f[q] = fp - (a + b);
-    f[q + 1] = fm - (a - b);
-    out[q] = fp - om * f[q] + fr;
-    out[q + 1] = fm - om * f[q + 1] - fr;
-  }
-  if (active && no == 0) {
-#pragma unroll
-    for (int q = 0; q < Q; q++) S::store(static_cast<Elem*>(v.dst_q[q]), n, out[q], LAT::w(q));
-  }
-
-  // ---- pack the covered nodes of the CTA ----
-  __shared__ T s_st[NS][128];
-  __shared__ int s_n[128], s_xyz[128], s_no[128], s_own[kMaxOwners][128];
-  __shared__ E s_e[kMaxOwners][128];
-  __shared__ int s_cnt[4];
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned covered = __ballot_sync(FULL, no > 0);
-  __syncthreads();  // the previous call's packed state has been consumed
-  if (lane == 0) s_cnt[warp] = __popc(covered);
-  __syncthreads();
-  int base = 0, total = 0;
-#pragma unroll
-  for (int w = 0; w < 4; w++) {
-    base += w < warp ? s_cnt[w] : 0;
-    total += s_cnt[w];
-  }
-  if (no > 0) {
-    const int slot = base + __popc(covered & ((1u << lane) - 1u));
-#pragma unroll
-    for (int q = 0; q < Q; q++) s_st[q][slot] = f[q];
-    s_st[Q][slot] = rho;
-    s_st[Q + 1][slot] = drho;
-    s_st[Q + 2][slot] = ux;
-    s_st[Q + 3][slot] = uy;
-    s_st[Q + 4][slot] = uz;
-    s_n[slot] = n;
-    s_xyz[slot] = xx | (y << 16);  // x, y < 65536
-    s_no[slot] = no | (z << 8);
-#pragma unroll
-    for (int s = 0; s < kMaxOwners; s++) {
-      s_own[s][slot] = s < no ? own[s] : -1;
-      s_e[s][slot] = s < no ? eown[s] : E(0);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x >= ((total + 31) & ~31)) return;  // whole warps beyond the packed nodes
-
-  // ---------------- NT immersed moving boundary on packed nodes ----------------
-  const int slot = threadIdx.x;
-  const bool mine = slot < total;
-  const int ps = mine ? slot : 0;
-  const int cn = s_n[ps];
-  const int cx_ = s_xyz[ps] & 0xffff, cy_ = s_xyz[ps] >> 16, cz_ = s_no[ps] >> 8;
-  no = mine ? (s_no[ps] & 0xff) : 0;
-#pragma unroll
-  for (int s = 0; s < kMaxOwners; s++) {
-    own[s] = s_own[s][ps];
-    eown[s] = s_e[s][ps];
-  }
-  // sort owners by id
-#pragma unroll
-  for (int a = 1; a < kMaxOwners; a++) {
-    if (a < no) {
-      int k = own[a];
-      E ek = eown[a];
-      int b = a - 1;
-      while (b >= 0 && own[b] > k) {
-        own[b + 1] = own[b];
-        eown[b + 1] = eown[b];
-        b--;
-      }
-      own[b + 1] = k;
-      eown[b + 1] = ek;
-    }
-  }
-  T g[Q];
-#pragma unroll
-  for (int q = 0; q < Q; q++) g[q] = s_st[q][ps];
-  const T crho = s_st[Q][ps], cdrho = s_st[Q + 1][ps];
-  const T cux = s_st[Q + 2][ps], cuy = s_st[Q + 3][ps], cuz = s_st[Q + 4][ps];
-  const T cusq15 = T(1.5) * (cux * cux + cuy * cuy + cuz * cuz);
-  {
-    // solid velocity at the node; particle arithmetic in FP64 for FP64
-    // storage, in FP32 (from the per-particle FP32 kinematics record)
-    // otherwise
-    using PT = typename S::T;
-    PT esum = PT(0), vs0 = PT(0), vs1 = PT(0), vs2 = PT(0);
-    PT rk[kMaxOwners][3];
-    PT V1x = PT(0), V1y = PT(0), V1z = PT(0);
-    for (int k = 0; k < no; k++) {
-      const int p = own[k];
-      PT r0, r1, r2, V0, Vy, V2;
-      if constexpr (S::DEV) {
-        const float4* kp = reinterpret_cast<const float4*>(v.kin) + 4 * p;
-        const float4 fr = __ldg(kp);
-        const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
-        const float4 vp = __ldg(kp + 2);
-        const float4 wp = __ldg(kp + 3);
-        r0 = min_image_f(float(cx_ - ir.x) - fr.x, nx, true);
-        r1 = min_image_f(float(cy_ - ir.y) - fr.y, ny, !v.wall_y);
-        r2 = D3 ? min_image_f(float(cz_ - ir.z) - fr.z, nz, true) : 0.f;
-        V0 = vp.x + (wp.y * r2 - wp.z * r1);
-        Vy = vp.y + (wp.z * r0 - wp.x * r2);
-        V2 = vp.z + (wp.x * r1 - wp.y * r0);
-      } else {
-        r0 = min_image((double)cx_ - v.pos[3 * p], nx, true);
-        r1 = min_image((double)cy_ - v.pos[3 * p + 1], ny, !v.wall_y);
-        r2 = D3 ? min_image((double)cz_ - v.pos[3 * p + 2], nz, true) : 0.0;
-        const double* w = v.omg + 3 * p;
-        const double* vp = v.vel + 3 * p;
-        V0 = vp[0] + (w[1] * r2 - w[2] * r1);
-        Vy = vp[1] + (w[2] * r0 - w[0] * r2);
-        V2 = vp[2] + (w[0] * r1 - w[1] * r0);
-      }
-      rk[k][0] = r0;
-      rk[k][1] = r1;
-      rk[k][2] = r2;
-      const PT e = (PT)eown[k];
-      if (k == 0) {
-        V1x = V0;
-        V1y = Vy;
-        V1z = V2;
-      }
-      esum += e;
-      vs0 += e * V0;
-      vs1 += e * Vy;
-      vs2 += e * V2;
-    }
-    T beta = T(0), VSx = T(0), VSy = T(0), VSz = T(0);
-    PT inv_esum = PT(1);
-    if (no == 1) {
-      VSx = T(V1x);  // one owner: V_S is its velocity, the split factor 1
-      VSy = T(V1y);
-      VSz = T(V1z);
-    } else if (no > 1) {
-      inv_esum = PT(1) / esum;
-      VSx = T(vs0 * inv_esum);
-      VSy = T(vs1 * inv_esum);
-      VSz = T(vs2 * inv_esum);
-    }
-    if (no > 0 && esum > PT(0)) {
-      const T eps = esum < PT(1) ? T(esum) : T(1);
-      const T th = tau_t - T(0.5);
-      beta = eps * th / ((T(1) - eps) + th);  // Eq. (2)
-    }
-    const T vsq15 = T(1.5) * (VSx * VSx + VSy * VSy + VSz * VSz);
-    T mx = T(0), my = T(0), mz = T(0);
-    T res[Q];
-    {
-      const T w0r = T(LAT::w(0)) * crho;
-      const T a = pair_A<S::DEV, T>(T(LAT::w(0)), w0r, cdrho, cusq15, T(0));
-      const T AS0 = pair_A<S::DEV, T>(T(LAT::w(0)), w0r, cdrho, vsq15, T(0));
-      const T Om0 = AS0 - a;  // f_0 - f_0 cancels
-      res[0] = (g[0] + a) - om * g[0] + beta * (om * g[0] + Om0);
-    }
-#pragma unroll
-    for (int k = 0; k < NP; k++) {
-      const int q = 2 * k + 1;
-      const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
-      const T wr = T(LAT::w(q)) * crho;
-      const T cu = cdot<T>(cx, cy, cz, cux, cuy, cuz);
-      const T a = pair_A<S::DEV, T>(T(LAT::w(q)), wr, cdrho, cusq15, cu);
-      const T b = (T(3) * wr) * cu;
-      const T cv = cdot<T>(cx, cy, cz, VSx, VSy, VSz);
-      const T AS = pair_A<S::DEV, T>(T(LAT::w(q)), wr, cdrho, vsq15, cv);
-      const T BS = (T(3) * wr) * cv;
-      const T fr = fq_of<S::DEV, T>(v, q) * crho;
-      // Omega^S_q = f_{-q} - f_q + feq_q(rho, V_S) - feq_{-q}(rho, u)
-      const T dA = AS - a;
-      const T Omp = (g[q + 1] - g[q]) + (dA + (BS - b));
-      const T Omm = (g[q] - g[q + 1]) + (dA - (BS - b));
-      res[q] = (g[q] + (a + b)) - om * g[q] + fr + beta * (om * g[q] + Omp);
-      res[q + 1] = (g[q + 1] + (a - b)) - om * g[q + 1] - fr + beta * (om * g[q + 1] + Omm);
-      const T dm = Omp - Omm;  // c_{q+1} = -c_q
-      if (cx) mx += T(cx) * dm;
-      if (cy) my += T(cy) * dm;
-      if (cz) mz += T(cz) * dm;
-    }
-    if (mine) {
-#pragma unroll
-      for (int q = 0; q < Q; q++) S::store(static_cast<Elem*>(v.dst_q[q]), cn, res[q], LAT::w(q));
-    }
-    // momentum given to the fluid m = beta sum_i Omega_i^S c_i; the force on
-    // the particles is -m, split by covered fraction (Eq. 3 and reading)
-    const PT m0 = PT(beta * mx), m1 = PT(beta * my), m2 = PT(beta * mz);
-    PT val[6] = {PT(0), PT(0), PT(0), PT(0), PT(0), PT(0)};
-    int key = -1;
-    for (int k = 0; k < no; k++) {
-      const PT a = no == 1 ? PT(1) : PT(eown[k]) * inv_esum;
-      const PT p0 = a * m0, p1 = a * m1, p2 = a * m2;
-      const PT F0 = -p0, F1 = -p1, F2 = -p2;
-      const PT T0 = -(rk[k][1] * p2 - rk[k][2] * p1);
-      const PT T1 = -(rk[k][2] * p0 - rk[k][0] * p2);
-      const PT T2 = -(rk[k][0] * p1 - rk[k][1] * p0);
-      if (k == 0) {
-        key = own[0];
-        val[0] = F0; val[1] = F1; val[2] = F2;
-        val[3] = T0; val[4] = T1; val[5] = T2;
-      } else {
-        const int p = own[k];
-        atomicAdd(v.ff + 3 * p, (double)F0);
-        atomicAdd(v.ff + 3 * p + 1, (double)F1);
-        if (D3) atomicAdd(v.ff + 3 * p + 2, (double)F2);
-        if (D3) {
-          atomicAdd(v.tf + 3 * p, (double)T0);
-          atomicAdd(v.tf + 3 * p + 1, (double)T1);
-        }
-        atomicAdd(v.tf + 3 * p + 2, (double)T2);
-      }
-    }
-    if (!(esum > PT(0))) key = -1;
-    warp_reduce_to_particles<PT>(key, val, v.ff, v.tf);
-}
-
-}
-
-template <class LAT, int STORE>
-__device__ __forceinline__ void collide_node(const View& v, const int xx, const int y, const int z,
-                                             const bool active) {
+__device__ __forceinline__ void pull(const View& v, const int xx, const int y, const int z, const int n,
+                                     const bool load, typename Storage<STORE>::T (&f)[LAT::Q]) {
   using S = Storage<STORE>;
   using T = typename S::T;
   using Elem = typename S::Elem;
@@ -457,19 +180,16 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
   const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
   const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-  const int n = (z * ny + y) * pitch + xx;
-  // ---- pull streaming; rows are whole warps, so the wall test is uniform ----
   const int ry[3] = {y * pitch, ym * pitch, yp * pitch};
   const int rz[3] = {z * ny * pitch, zm * ny * pitch, zp * ny * pitch};
-  T f[Q];
   const bool wall_row = v.wall_y && (y == 0 || y == ny - 1);
-  if (!wall_row) {
+  if (!wall_row) {  // rows are whole warps: the test is warp-uniform in the row kernel
 #pragma unroll
     for (int q = 0; q < Q; q++) {
       const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
       const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
       const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
-      f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
+      f[q] = load ? S::load(static_cast<const Elem*>(v.src_q[q]), idx) : T(0);
     }
   } else {
 #pragma unroll
@@ -479,13 +199,546 @@ __device__ __forceinline__ void collide_node(const View& v, const int xx, const 
       const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
       const bool bounce = (cy == 1 && y == 0) || (cy == -1 && y == ny - 1);
       if (bounce)  // halfway bounce-back: the opposite population of this node
-        f[q] = S::load(static_cast<const Elem*>(v.src_q[opp(q)]), n, LAT::w(opp(q)));
+        f[q] = load ? S::load(static_cast<const Elem*>(v.src_q[opp(q)]), n) : T(0);
       else
-        f[q] = S::load(static_cast<const Elem*>(v.src_q[q]), idx, LAT::w(q));
+        f[q] = load ? S::load(static_cast<const Elem*>(v.src_q[q]), idx) : T(0);
     }
   }
+}
 
-  collide_core<LAT, STORE>(v, xx, y, z, active, n, f);
+// Velocities are carried scaled, u_s = sqrt(4.5) u, so that in
+//   f^eq_i = w rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+//          = w rho (1 + sqrt(2) c.u_s + (c.u_s)^2 - u_s.u_s / 3)
+// the square needs no extra factor.
+constexpr double kSqrt45 = 2.12132034355964257320;  // sqrt(4.5)
+constexpr double kSqrt2 = 1.41421356237309504880;
+
+// Density deviation, density and scaled velocity of a node from the sums and
+// differences of its opposite pairs (SCALED: f holds h = g / w, so the sums
+// carry the weights).  k is the velocity term of the bracket above:
+// 1 - u_s.u_s / 3 for full populations, -u_s.u_s / 3 in deviation form.
+template <typename T>
+struct Moments {
+  T drho, rho, ux, uy, uz, k;
+};
+
+template <class LAT, int STORE>
+__device__ __forceinline__ typename Storage<STORE>::T k_of(const typename Storage<STORE>::T ux,
+                                                           const typename Storage<STORE>::T uy,
+                                                           const typename Storage<STORE>::T uz) {
+  using T = typename Storage<STORE>::T;
+  const T usq = LAT::DIM == 3 ? fma(ux, ux, fma(uy, uy, uz * uz)) : fma(ux, ux, uy * uy);
+  return Storage<STORE>::DEV ? usq * T(-1.0 / 3.0) : fma(usq, T(-1.0 / 3.0), T(1));
+}
+
+template <class LAT, int STORE>
+__device__ __forceinline__ Moments<typename Storage<STORE>::T> moments(
+    const View& v, const typename Storage<STORE>::T (&f)[LAT::Q]) {
+  using S = Storage<STORE>;
+  using T = typename S::T;
+  constexpr int NP = (LAT::Q - 1) / 2;
+  constexpr bool D3 = LAT::DIM == 3;
+  T s0 = S::SCALED ? T(LAT::w(0)) * f[0] : f[0];
+  T jx = T(0), jy = T(0), jz = T(0);
+  bool hx = false, hy = false, hz = false;
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    const int q = 2 * k + 1;
+    const T wq = T(LAT::w(q));
+    const T p = f[q] + f[q + 1], m = f[q] - f[q + 1];
+    s0 = S::SCALED ? fma(wq, p, s0) : s0 + p;
+    axis_acc<S::SCALED>(jx, hx, LAT::c(q, 0), wq, m);
+    axis_acc<S::SCALED>(jy, hy, LAT::c(q, 1), wq, m);
+    if (D3) axis_acc<S::SCALED>(jz, hz, LAT::c(q, 2), wq, m);
+  }
+  Moments<T> r;
+  r.drho = S::DEV ? s0 : T(0);
+  r.rho = S::DEV ? T(v.rho0_f) + s0 : s0;
+  T irho;
+  if constexpr (sizeof(T) == 4) irho = __frcp_rn(r.rho);
+  else irho = T(1) / r.rho;
+  const T is = T(kSqrt45) * irho;
+  r.ux = jx * is;
+  r.uy = jy * is;
+  r.uz = D3 ? jz * is : T(0);
+  r.k = k_of<LAT, STORE>(r.ux, r.uy, r.uz);
+  return r;
+}
+
+// Plain BGK in the stored form: out_i = (1 - omega) f_i + omega f^eq_i + F_i.
+// For the pair (q, q+1 = -q), omega f^eq + F is A + B and A - B with
+//   A = omega W (k + (c.u_s)^2)            (+ omega w drho in deviation form)
+//   B = W (sqrt(2) omega c.u_s + 3 c.g_f),  W = w rho
+// (w = 1 in the scaled form).  The weight products fold per weight class.
+template <class LAT, int STORE>
+__device__ __forceinline__ void bgk(const View& v, const Moments<typename Storage<STORE>::T>& m,
+                                    const typename Storage<STORE>::T (&f)[LAT::Q],
+                                    typename Storage<STORE>::T (&out)[LAT::Q]) {
+  using S = Storage<STORE>;
+  using T = typename S::T;
+  constexpr int NP = (LAT::Q - 1) / 2;
+  const T om = S::DEV ? T(v.omega_f) : T(v.omega);
+  const T omc = S::DEV ? T(v.omc_f) : T(v.omc);
+  const T omb = T(kSqrt2) * om;
+  auto A_of = [&](T wq, T t) -> T {
+    const T ow = om * (S::SCALED ? T(1) : wq);
+    if constexpr (S::DEV) return fma(ow * m.rho, t, ow * m.drho);
+    else return (ow * m.rho) * t;
+  };
+  out[0] = fma(omc, f[0], A_of(T(LAT::w(0)), m.k));
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    const int q = 2 * k + 1;
+    const T wq = T(LAT::w(q));
+    const T cu = cdot<T>(LAT::c(q, 0), LAT::c(q, 1), LAT::c(q, 2), m.ux, m.uy, m.uz);
+    const T A = A_of(wq, fma(cu, cu, m.k));
+    const T B = ((S::SCALED ? T(1) : wq) * m.rho) * fma(omb, cu, cg3_of<S::DEV, T>(v, q));
+    out[q] = fma(omc, f[q], A + B);
+    out[q + 1] = fma(omc, f[q + 1], A - B);
+  }
+}
+
+// Plain update of a node whose pulled populations are f; stored where go.
+// Returns the moments (the immersed-boundary update reuses them).
+template <class LAT, int STORE>
+__device__ __forceinline__ Moments<typename Storage<STORE>::T> plain_core(
+    const View& v, const int n, const bool go, const typename Storage<STORE>::T (&f)[LAT::Q]) {
+  using S = Storage<STORE>;
+  using T = typename S::T;
+  using Elem = typename S::Elem;
+  constexpr int NP = (LAT::Q - 1) / 2;
+  const Moments<T> m = moments<LAT, STORE>(v, f);
+  T out[LAT::Q];
+  bgk<LAT, STORE>(v, m, f, out);
+  if (go) {
+    S::store(static_cast<Elem*>(v.dst_q[0]), n, out[0]);
+#pragma unroll
+    for (int k = 0; k < NP; k++)
+      S::store2(static_cast<Elem*>(v.dst_q[2 * k + 1]), static_cast<Elem*>(v.dst_q[2 * k + 2]), n, out[2 * k + 1],
+                out[2 * k + 2]);
+  }
+  return m;
+}
+
+// Particle kinematics for the solid velocity: FP64 position, velocity and
+// spin (FP64 storage), or the FP32 record (nearest node as int, offset,
+// velocity, spin) for the reduced-precision storages.
+template <typename PT>
+struct Kin {
+  PT c[3], vel[3], w[3];  // centre (FP64) or offset from ic (FP32)
+  int ic[3];
+};
+
+template <int STORE>
+__device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& v, const int q) {
+  Kin<typename Storage<STORE>::T> k;
+  if constexpr (Storage<STORE>::DEV) {
+    const float4* kp = reinterpret_cast<const float4*>(v.kin) + 4 * q;
+    const float4 fr = __ldg(kp);
+    const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
+    const float4 vp = __ldg(kp + 2);
+    const float4 wp = __ldg(kp + 3);
+    k.c[0] = fr.x; k.c[1] = fr.y; k.c[2] = fr.z;
+    k.ic[0] = ir.x; k.ic[1] = ir.y; k.ic[2] = ir.z;
+    k.vel[0] = vp.x; k.vel[1] = vp.y; k.vel[2] = vp.z;
+    k.w[0] = wp.x; k.w[1] = wp.y; k.w[2] = wp.z;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      k.c[d] = v.pos[3 * q + d];
+      k.vel[d] = v.vel[3 * q + d];
+      k.w[d] = v.omg[3 * q + d];
+      k.ic[d] = 0;
+    }
+  }
+  return k;
+}
+
+// node position relative to the particle (minimum image) and the rigid-body
+// velocity V = v + w x r there
+template <bool D3, typename PT>
+__device__ __forceinline__ void node_rel(const View& v, const Kin<PT>& k, const int x, const int y, const int z,
+                                         PT (&r)[3], PT (&V)[3]) {
+  if constexpr (sizeof(PT) == 4) {
+    r[0] = min_image_f(float(x - k.ic[0]) - k.c[0], v.nx, true);
+    r[1] = min_image_f(float(y - k.ic[1]) - k.c[1], v.ny, !v.wall_y);
+    r[2] = D3 ? min_image_f(float(z - k.ic[2]) - k.c[2], v.nz, true) : 0.f;
+  } else {
+    r[0] = min_image((double)x - k.c[0], v.nx, true);
+    r[1] = min_image((double)y - k.c[1], v.ny, !v.wall_y);
+    r[2] = D3 ? min_image((double)z - k.c[2], v.nz, true) : 0.0;
+  }
+  V[0] = k.vel[0] + (k.w[1] * r[2] - k.w[2] * r[1]);
+  V[1] = k.vel[1] + (k.w[2] * r[0] - k.w[0] * r[2]);
+  V[2] = k.vel[2] + (k.w[0] * r[1] - k.w[1] * r[0]);
+}
+
+// ---------------------------------------------------------------------------
+// Immersed-boundary update of one covered node: Eq. (1) with beta of Eq. (2)
+// and the solid term
+//   Omega^S_i = (f - f^eq)_{-i} - (f - f^eq)_i + f^eq_i(rho, V_S) - f^eq_i(rho, u),
+// written as a correction of the plain update,
+//   f*_i = f*_i(plain) + beta (omega (f_i - f^eq_i) + Omega^S_i),
+// and the Eq. (3) force/torque on each owner (-beta sum_i Omega^S_i c_i split
+// by covered fraction): the first owner's share is summed over the warp by
+// owner (warp_reduce_to_particles), the others go to their FP64
+// accumulators directly.  f: the node's pulled populations (stored form).
+// The whole warp calls it; lanes with mine = false do the arithmetic on a
+// valid node and write nothing.
+// ---------------------------------------------------------------------------
+template <class LAT, int STORE>
+__device__ __forceinline__ void imb_core(const View& v, const int xx, const int y, const int z, const int n,
+                                         const bool mine, typename Storage<STORE>::T (&f)[LAT::Q],
+                                         const Moments<typename Storage<STORE>::T>& m) {
+  using S = Storage<STORE>;
+  using T = typename S::T;
+  using E = typename S::E;
+  using Elem = typename S::Elem;
+  using PT = T;  // particle-side arithmetic: FP64 for FP64 storage, FP32 otherwise
+  constexpr int Q = LAT::Q;
+  constexpr int NP = (Q - 1) / 2;
+  constexpr bool D3 = LAT::DIM == 3;
+  constexpr int K = kMaxOwners;
+  const T om = S::DEV ? T(v.omega_f) : T(v.omega);
+  const T tau_t = S::DEV ? T(v.tau_f) : T(v.tau);
+
+  // owners, sorted by id with empty slots last, so that V_S sums in particle
+  // order.  Slots fill in order, so the taken ones are a prefix; all four
+  // are read at once (one memory round trip instead of a chain).
+  int own[K];
+  E eo[K];
+  int no = 0;
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    const int o = v.own[s][n];
+    const E e = static_cast<const E*>(v.eps[s])[n];
+    own[s] = o >= 0 ? o : 0x7fffffff;
+    eo[s] = o >= 0 ? e : E(0);
+    no += o >= 0 ? 1 : 0;
+  }
+  auto cswap = [&](int a, int b) {
+    if (own[a] > own[b]) {
+      const int t = own[a];
+      own[a] = own[b];
+      own[b] = t;
+      const E te = eo[a];
+      eo[a] = eo[b];
+      eo[b] = te;
+    }
+  };
+  static_assert(K == 4, "sorting network for four owner slots");
+  cswap(0, 1);
+  cswap(2, 3);
+  cswap(0, 2);
+  cswap(1, 3);
+  cswap(1, 2);
+
+  if constexpr (S::SCALED) {
+#pragma unroll
+    for (int q = 0; q < Q; q++) f[q] *= T(LAT::w(q));  // g = h w
+  }
+
+  // solid velocity at the node, position relative to each owner
+  PT esum = PT(0), vs0 = PT(0), vs1 = PT(0), vs2 = PT(0);
+  PT rk[K][3];
+  PT V1x = PT(0), V1y = PT(0), V1z = PT(0);
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    rk[k][0] = rk[k][1] = rk[k][2] = PT(0);
+    if (k < no) {
+      const int q = own[k];
+      const Kin<PT> kq = load_kin<STORE>(v, q);
+      PT V[3];
+      node_rel<D3>(v, kq, xx, y, z, rk[k], V);
+      const PT e = (PT)eo[k];
+      if (k == 0) {
+        V1x = V[0];
+        V1y = V[1];
+        V1z = V[2];
+      }
+      esum += e;
+      vs0 += e * V[0];
+      vs1 += e * V[1];
+      vs2 += e * V[2];
+    }
+  }
+  T beta = T(0), VSx = T(0), VSy = T(0), VSz = T(0);
+  PT inv_esum = PT(1);
+  if (no == 1) {
+    VSx = T(V1x);  // one owner: V_S is its velocity, the split factor 1
+    VSy = T(V1y);
+    VSz = T(V1z);
+  } else if (no > 1) {
+    inv_esum = PT(1) / esum;
+    VSx = T(vs0 * inv_esum);
+    VSy = T(vs1 * inv_esum);
+    VSz = T(vs2 * inv_esum);
+  }
+  if (no > 0 && esum > PT(0)) {
+    const T eps = esum < PT(1) ? T(esum) : T(1);
+    const T th = tau_t - T(0.5);
+    beta = eps * th / ((T(1) - eps) + th);  // Eq. (2)
+  }
+
+  // update, with f (deviation form for DEV storages, unscaled) and the
+  // pair parts of f^eq(rho, u) = A +- B, f^eq(rho, V_S) = AS +- BS:
+  //   g = f - f^eq,  D = g_{-q} - g_q,  dA = AS - A,  dB = BS - B,
+  //   Omega^S_q = D + dA + dB,  Omega^S_{-q} = dA - (D + dB),
+  //   f*_q = f_q + F_q + (beta - 1) omega g_q + beta Omega^S_q
+  // with A = W (k + (c.u_s)^2) (+ w drho), B = sqrt(2) W c.u_s, W = w rho.
+  const T rho = m.rho;
+  const T vx = T(kSqrt45) * VSx, vy = T(kSqrt45) * VSy, vz = T(kSqrt45) * VSz;
+  const T dk = k_of<LAT, STORE>(vx, vy, vz) - m.k;
+  const T cfac = (beta - T(1)) * om;
+  T mx = T(0), my = T(0), mz = T(0);
+  T res[Q];
+  {
+    const T W0 = T(LAT::w(0)) * rho;
+    const T A0 = S::DEV ? fma(W0, m.k, T(LAT::w(0)) * m.drho) : W0 * m.k;
+    res[0] = fma(beta, W0 * dk, fma(cfac, f[0] - A0, f[0]));  // Omega^S_0 = dA_0
+  }
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    const int q = 2 * k + 1;
+    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+    const T wq = T(LAT::w(q));
+    const T W = wq * rho, Wb = (T(kSqrt2) * wq) * rho;
+    const T cu = cdot<T>(cx, cy, cz, m.ux, m.uy, m.uz);
+    const T cv = cdot<T>(cx, cy, cz, vx, vy, vz);
+    const T t = fma(cu, cu, m.k);
+    const T A = S::DEV ? fma(W, t, wq * m.drho) : W * t;
+    const T B = Wb * cu;
+    const T gp = f[q] - (A + B), gm = f[q + 1] - (A - B);
+    const T dA = W * fma(cv, cv, fma(-cu, cu, dk));
+    const T E = (gm - gp) + Wb * (cv - cu);  // D + dB
+    const T Fq = fq_of<S::DEV, T>(v, q) * rho;
+    res[q] = fma(beta, E + dA, fma(cfac, gp, f[q] + Fq));
+    res[q + 1] = fma(beta, dA - E, fma(cfac, gm, f[q + 1] - Fq));
+    // Omega^S_q - Omega^S_{-q} = 2 E, and c_{q+1} = -c_q
+    if (cx) mx += cx > 0 ? E : -E;
+    if (cy) my += cy > 0 ? E : -E;
+    if (cz) mz += cz > 0 ? E : -E;
+  }
+  if (mine) {
+#pragma unroll
+    for (int q = 0; q < Q; q++)
+      S::store(static_cast<Elem*>(v.dst_q[q]), n, S::SCALED ? res[q] * T(1.0 / LAT::w(q)) : res[q]);
+  }
+
+  // momentum given to the fluid m = beta sum_i Omega_i^S c_i; the force on
+  // the particles is -m, split by covered fraction (Eq. 3 and reading)
+  const T b2 = T(2) * beta;
+  const PT m0 = PT(b2 * mx), m1 = PT(b2 * my), m2 = PT(b2 * mz);
+  const bool any = mine && esum > PT(0);
+  PT val[6] = {PT(0), PT(0), PT(0), PT(0), PT(0), PT(0)};
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    if (any && k < no) {
+      const PT a = no == 1 ? PT(1) : PT(eo[k]) * inv_esum;
+      const PT p0 = a * m0, p1 = a * m1, p2 = a * m2;
+      const PT F0 = -p0, F1 = -p1, F2 = -p2;
+      const PT T0 = -(rk[k][1] * p2 - rk[k][2] * p1);
+      const PT T1 = -(rk[k][2] * p0 - rk[k][0] * p2);
+      const PT T2 = -(rk[k][0] * p1 - rk[k][1] * p0);
+      if (k == 0) {
+        val[0] = F0; val[1] = F1; val[2] = F2;
+        val[3] = T0; val[4] = T1; val[5] = T2;
+      } else {
+        const int q = own[k];
+        atomicAdd(v.ff + 3 * q, (double)F0);
+        atomicAdd(v.ff + 3 * q + 1, (double)F1);
+        if (D3) atomicAdd(v.ff + 3 * q + 2, (double)F2);
+        if (D3) {
+          atomicAdd(v.tf + 3 * q, (double)T0);
+          atomicAdd(v.tf + 3 * q + 1, (double)T1);
+        }
+        atomicAdd(v.tf + 3 * q + 2, (double)T2);
+      }
+    }
+  }
+  warp_reduce_to_particles<PT>(any ? own[0] : -1, val, v.ff, v.tf);
+}
+
+// ---------------------------------------------------------------------------
+// Fused collision with a per-warp queue of covered nodes.  A warp takes row
+// segments of 32 nodes one after another: every node gets the plain BGK
+// update from its pulled populations (stored unless covered); the covered
+// nodes' populations and coordinates are appended to the warp's queue in
+// shared memory, and whenever 32 are queued the warp gives them the
+// immersed-boundary update with all lanes busy.  Only __syncwarp is used:
+// the warps of a CTA never wait for one another.
+// ---------------------------------------------------------------------------
+constexpr int kQueueCap = 64;  // 31 left over + 32 new at most
+
+template <int STORE>
+struct WarpQueue {
+  typename Storage<STORE>::T* f;  // [Q + 5][kQueueCap] populations (stored form), rho, drho, u_s
+  int* n;                          // [kQueueCap] node offset
+  int* xy;                         // [kQueueCap] x | y << 16
+  int* z;                          // [kQueueCap]
+};
+
+template <class LAT, int STORE>
+__host__ __device__ constexpr int queue_bytes_per_warp() {
+  return kQueueCap * ((LAT::Q + 5) * (int)sizeof(typename Storage<STORE>::T) + 3 * 4);
+}
+
+template <class LAT, int STORE>
+__device__ __forceinline__ WarpQueue<STORE> warp_queue(unsigned char* base, const int warp) {
+  using T = typename Storage<STORE>::T;
+  unsigned char* b = base + warp * queue_bytes_per_warp<LAT, STORE>();
+  WarpQueue<STORE> w;
+  w.f = reinterpret_cast<T*>(b);
+  w.n = reinterpret_cast<int*>(b + kQueueCap * (LAT::Q + 5) * sizeof(T));
+  w.xy = w.n + kQueueCap;
+  w.z = w.xy + kQueueCap;
+  return w;
+}
+
+// immersed-boundary update of the first count (<= 32) queued nodes
+template <class LAT, int STORE>
+__device__ __forceinline__ void queue_flush(const View& v, const WarpQueue<STORE>& wq, const int count,
+                                            const int lane) {
+  using T = typename Storage<STORE>::T;
+  const bool mine = lane < count;
+  const int s = mine ? lane : 0;
+  constexpr int Q = LAT::Q;
+  T f[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) f[q] = wq.f[q * kQueueCap + s];
+  Moments<T> m;
+  m.rho = wq.f[Q * kQueueCap + s];
+  m.drho = wq.f[(Q + 1) * kQueueCap + s];
+  m.ux = wq.f[(Q + 2) * kQueueCap + s];
+  m.uy = wq.f[(Q + 3) * kQueueCap + s];
+  m.uz = wq.f[(Q + 4) * kQueueCap + s];
+  m.k = k_of<LAT, STORE>(m.ux, m.uy, m.uz);
+  const int xy = wq.xy[s];
+  imb_core<LAT, STORE>(v, xy & 0xffff, xy >> 16, wq.z[s], wq.n[s], mine, f, m);
+}
+
+// One lane's node of the warp's row segment, populations f already pulled;
+// cnt is the warp's queue length (warp-uniform).
+template <class LAT, int STORE>
+__device__ __forceinline__ void fused_core(const View& v, const int xx, const int y, const int z, const int n,
+                                           const bool active, typename Storage<STORE>::T (&f)[LAT::Q],
+                                           const WarpQueue<STORE>& wq, int& cnt, const int lane) {
+  const unsigned FULL = 0xffffffffu;
+  constexpr int Q = LAT::Q;
+  const bool covered = active && v.own[0][n] >= 0;
+  const Moments<typename Storage<STORE>::T> m = plain_core<LAT, STORE>(v, n, active && !covered, f);
+  const unsigned b = __ballot_sync(FULL, covered);
+  if (b == 0u) return;
+  if (covered) {
+    const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+#pragma unroll
+    for (int q = 0; q < Q; q++) wq.f[q * kQueueCap + pos] = f[q];
+    wq.f[Q * kQueueCap + pos] = m.rho;
+    wq.f[(Q + 1) * kQueueCap + pos] = m.drho;
+    wq.f[(Q + 2) * kQueueCap + pos] = m.ux;
+    wq.f[(Q + 3) * kQueueCap + pos] = m.uy;
+    wq.f[(Q + 4) * kQueueCap + pos] = m.uz;
+    wq.n[pos] = n;
+    wq.xy[pos] = xx | (y << 16);  // x, y < 65536
+    wq.z[pos] = z;
+  }
+  cnt += __popc(b);
+  __syncwarp();
+  if (cnt >= 32) {
+    queue_flush<LAT, STORE>(v, wq, 32, lane);
+    __syncwarp();
+    if (lane < cnt - 32) {
+#pragma unroll
+      for (int q = 0; q < Q + 5; q++) wq.f[q * kQueueCap + lane] = wq.f[q * kQueueCap + 32 + lane];
+      wq.n[lane] = wq.n[32 + lane];
+      wq.xy[lane] = wq.xy[32 + lane];
+      wq.z[lane] = wq.z[32 + lane];
+    }
+    cnt -= 32;
+    __syncwarp();
+  }
+}
+
+// the same with the populations pulled from global memory
+template <class LAT, int STORE>
+__device__ __forceinline__ void fused_node(const View& v, const int xx, const int y, const int z, const bool active,
+                                           const WarpQueue<STORE>& wq, int& cnt, const int lane) {
+  using T = typename Storage<STORE>::T;
+  const int n = (z * v.ny + y) * v.pitch + xx;
+  T f[LAT::Q];
+  pull<LAT, STORE>(v, xx, y, z, n, active, f);
+  fused_core<LAT, STORE>(v, xx, y, z, n, active, f, wq, cnt, lane);
+}
+
+// CTA-packed form (non-persistent): every lane of a 128-node row tile gets
+// the plain update; the tile's covered nodes are packed into the first lanes
+// through shared memory (two CTA barriers) and updated by full warps.
+// smem: queue_bytes_per_warp * 2 bytes (128 packed entries).
+template <class LAT, int STORE>
+__device__ __forceinline__ void packed_node(const View& v, const int xx, const int y, const int z, const bool active,
+                                            unsigned char* smem) {
+  using T = typename Storage<STORE>::T;
+  constexpr int Q = LAT::Q;
+  constexpr int CAP = 128;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* sf = reinterpret_cast<T*>(smem);  // [Q + 5][CAP]
+  int* sn = reinterpret_cast<int*>(sf + (Q + 5) * CAP);
+  int* sxy = sn + CAP;
+  int* sz = sxy + CAP;
+  __shared__ int s_cnt[4];
+  const int n = (z * v.ny + y) * v.pitch + xx;
+  T f[Q];
+  pull<LAT, STORE>(v, xx, y, z, n, active, f);
+  const bool covered = active && v.own[0][n] >= 0;
+  const Moments<T> m = plain_core<LAT, STORE>(v, n, active && !covered, f);
+  const unsigned b = __ballot_sync(FULL, covered);
+  __syncthreads();  // the previous tile's packed state has been consumed
+  if (lane == 0) s_cnt[warp] = __popc(b);
+  __syncthreads();
+  int base = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < 4; w++) {
+    base += w < warp ? s_cnt[w] : 0;
+    total += s_cnt[w];
+  }
+  if (total == 0) return;
+  if (covered) {
+    const int pos = base + __popc(b & ((1u << lane) - 1u));
+#pragma unroll
+    for (int q = 0; q < Q; q++) sf[q * CAP + pos] = f[q];
+    sf[Q * CAP + pos] = m.rho;
+    sf[(Q + 1) * CAP + pos] = m.drho;
+    sf[(Q + 2) * CAP + pos] = m.ux;
+    sf[(Q + 3) * CAP + pos] = m.uy;
+    sf[(Q + 4) * CAP + pos] = m.uz;
+    sn[pos] = n;
+    sxy[pos] = xx | (y << 16);
+    sz[pos] = z;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x >= ((total + 31) & ~31)) return;  // whole warps beyond the packed nodes
+  const bool mine = (int)threadIdx.x < total;
+  const int s = mine ? (int)threadIdx.x : 0;
+  T g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) g[q] = sf[q * CAP + s];
+  Moments<T> mm;
+  mm.rho = sf[Q * CAP + s];
+  mm.drho = sf[(Q + 1) * CAP + s];
+  mm.ux = sf[(Q + 2) * CAP + s];
+  mm.uy = sf[(Q + 3) * CAP + s];
+  mm.uz = sf[(Q + 4) * CAP + s];
+  mm.k = k_of<LAT, STORE>(mm.ux, mm.uy, mm.uz);
+  imb_core<LAT, STORE>(v, sxy[s] & 0xffff, sxy[s] >> 16, sz[s], sn[s], mine, g, mm);
+}
+
+// drain a warp's queue (at the end of its segments)
+template <class LAT, int STORE>
+__device__ __forceinline__ void queue_drain(const View& v, const WarpQueue<STORE>& wq, int& cnt, const int lane) {
+  if (cnt > 0) queue_flush<LAT, STORE>(v, wq, cnt, lane);
+  cnt = 0;
+  __syncwarp();
 }
 
 }  // namespace lbm

@@ -5,7 +5,8 @@
 //   A  clear the previous eps footprints, zero the Eq. 3 sums and the bins
 //   B  rasterise eps (one CTA per particle); bin the particles
 //   C  pull-stream + Eq. 1 collision + Eq. 3 sums (tiles of tile_x x
-//      128/tile_x nodes); DEM contacts
+//      128/tile_x nodes, covered nodes through per-warp queues); DEM
+//      contacts
 //   D  particle update
 // The per-node, per-particle and per-cell work is the same device code as the
 // per-step kernels (dev_*.cuh), so each member evolves exactly as it would
@@ -111,13 +112,18 @@ __global__ void __launch_bounds__(128) batch_step_kernel(BatchArgs a) {
   if (!grid_barrier(a)) return;
 
   // C: collision tiles, contacts.  The member's view is staged in shared
-  // memory (the collision reads its per-direction plane pointers per access).
+  // memory (the collision reads its per-direction plane pointers per access);
+  // each warp's covered-node queue lives in the dynamic shared memory the
+  // raster tables used in phase B, and is drained before the member changes.
   __shared__ View sv;
   int cached = -1;
   const int ty = 128 / a.tile_x;
+  const WarpQueue<STORE> wq = warp_queue<LAT, STORE>(smem, threadIdx.x >> 5);
+  int cnt = 0;
   for (int t = blockIdx.x; t < NT; t += gridDim.x) {
     const int m = member_of(a.tile_off, a.nm, t);
     if (m != cached) {
+      if (cached >= 0) queue_drain<LAT, STORE>(sv, wq, cnt, lane);
       __syncthreads();
       const int* from = reinterpret_cast<const int*>(a.views + m);
       int* to = reinterpret_cast<int*>(&sv);
@@ -133,8 +139,9 @@ __global__ void __launch_bounds__(128) batch_step_kernel(BatchArgs a) {
     const int rows = v.ny * v.nz;
     const bool active = x < v.nx && r < rows;
     const int rr = r < rows ? r : rows - 1;
-    collide_node<LAT, STORE>(v, x < v.nx ? x : v.nx - 1, rr % v.ny, rr / v.ny, active);
+    fused_node<LAT, STORE>(v, x < v.nx ? x : v.nx - 1, rr % v.ny, rr / v.ny, active, wq, cnt, lane);
   }
+  if (cached >= 0) queue_drain<LAT, STORE>(sv, wq, cnt, lane);
   for (int i = gtid; i < P; i += nthreads) {
     const int m = member_of(a.part_off, a.nm, i);
     dem_contact_particle(a.views[m], i - a.part_off[m]);
@@ -169,6 +176,18 @@ static const void* batch_kernel(int dim, int storage) {
   if (storage == LBM_IMB_STORE_F64) return kernel_ptr<D3Q19, LBM_IMB_STORE_F64, double>();
   if (storage == LBM_IMB_STORE_F32DEV) return kernel_ptr<D3Q19, LBM_IMB_STORE_F32DEV, float>();
   return kernel_ptr<D3Q19, LBM_IMB_STORE_F16DEV, float>();
+}
+
+// dynamic shared memory the batch kernel needs besides the raster tables
+int batch_queue_smem(int dim, int storage) {
+  if (dim == 2) {
+    if (storage == LBM_IMB_STORE_F64) return 4 * queue_bytes_per_warp<D2Q9, LBM_IMB_STORE_F64>();
+    if (storage == LBM_IMB_STORE_F32DEV) return 4 * queue_bytes_per_warp<D2Q9, LBM_IMB_STORE_F32DEV>();
+    return 4 * queue_bytes_per_warp<D2Q9, LBM_IMB_STORE_F16DEV>();
+  }
+  if (storage == LBM_IMB_STORE_F64) return 4 * queue_bytes_per_warp<D3Q19, LBM_IMB_STORE_F64>();
+  if (storage == LBM_IMB_STORE_F32DEV) return 4 * queue_bytes_per_warp<D3Q19, LBM_IMB_STORE_F32DEV>();
+  return 4 * queue_bytes_per_warp<D3Q19, LBM_IMB_STORE_F16DEV>();
 }
 
 // co-resident CTAs of the batch kernel (0 on error)

@@ -20,11 +20,97 @@
 
 namespace lbm {
 
+// Row tiles t = (z * ny + y) * nxb + xt of 128 nodes, walked with a fixed
+// stride (the grid size) without divisions in the loop.
+struct TileWalk {
+  int xt, y, z, dxt, dy, dz, nxb, ny;
+  __device__ TileWalk(int t0, int stride, int nxb_, int ny_) : nxb(nxb_), ny(ny_) {
+    xt = t0 % nxb;
+    y = (t0 / nxb) % ny;
+    z = (t0 / nxb) / ny;
+    dxt = stride % nxb;
+    dy = (stride / nxb) % ny;
+    dz = (stride / nxb) / ny;
+  }
+  __device__ void next() {
+    xt += dxt;
+    const int c1 = xt >= nxb ? 1 : 0;
+    xt -= c1 * nxb;
+    y += dy + c1;  // < 2 ny
+    const int c2 = y >= ny ? 1 : 0;
+    y -= c2 * ny;
+    z += dz + c2;
+  }
+};
+
+// Persistent fused form: a CTA of 4 warps walks row tiles of 128 nodes
+// (grid-stride); each warp takes its 32-node segment of the tile, so the 19
+// pulled loads of a warp are 32 consecutive elements each (shifted by c_x)
+// and the stores are aligned.  Covered nodes go through the warp's queue
+// (dynamic shared memory, queue_bytes_per_warp per warp).
 template <class LAT, int STORE, int MINB>
-__global__ void __launch_bounds__(128, MINB) collide_kernel(View v) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128, MINB) collide_kernel(View v, int ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_q[];
+  const int nx = v.nx, nz = v.nz;
+  const int lane = threadIdx.x & 31;
+  const WarpQueue<STORE> wq = warp_queue<LAT, STORE>(smem_q, threadIdx.x >> 5);
+  int cnt = 0;
+  (void)ntiles;
+  for (TileWalk w(blockIdx.x, gridDim.x, (nx + 127) / 128, v.ny); w.z < nz; w.next()) {
+    const int x = w.xt * 128 + (int)threadIdx.x;
+    const bool active = x < nx;
+    fused_node<LAT, STORE>(v, active ? x : nx - 1, w.y, w.z, active, wq, cnt, lane);
+  }
+  queue_drain<LAT, STORE>(v, wq, cnt, lane);
+}
+
+// CTA-packed form: one CTA per 128-node row tile (no persistence).
+template <class LAT, int STORE, int MINB>
+__global__ void __launch_bounds__(128, MINB) collide_packed_kernel(View v) {
+  extern __shared__ __align__(16) unsigned char smem_p[];
+  const int x = blockIdx.x * 128 + threadIdx.x;
   const bool active = x < v.nx;
-  collide_node<LAT, STORE>(v, active ? x : v.nx - 1, blockIdx.y, blockIdx.z, active);
+  packed_node<LAT, STORE>(v, active ? x : v.nx - 1, blockIdx.y, blockIdx.z, active, smem_p);
+}
+
+// Software-pipelined persistent form: the populations (and owner word) of
+// the CTA's next tile are pulled into registers before the current tile is
+// collided, so every warp keeps one tile of loads in flight while it
+// computes.
+template <class LAT, int STORE, int MINB>
+__global__ void __launch_bounds__(128, MINB) collide_prefetch_kernel(View v, int ntiles) {
+  using T = typename Storage<STORE>::T;
+  extern __shared__ __align__(16) unsigned char smem_q[];
+  const int nx = v.nx, ny = v.ny, nz = v.nz, pitch = v.pitch;
+  const int lane = threadIdx.x & 31;
+  const WarpQueue<STORE> wq = warp_queue<LAT, STORE>(smem_q, threadIdx.x >> 5);
+  int cnt = 0;
+  (void)ntiles;
+  TileWalk w(blockIdx.x, gridDim.x, (nx + 127) / 128, ny);
+  if (w.z >= nz) return;
+  auto xof = [&](const TileWalk& t, bool& act) {
+    const int x = t.xt * 128 + (int)threadIdx.x;
+    act = x < nx;
+    return act ? x : nx - 1;
+  };
+  bool act;
+  int x = xof(w, act);
+  T fn[LAT::Q];
+  pull<LAT, STORE>(v, x, w.y, w.z, (w.z * ny + w.y) * pitch + x, act, fn);
+  while (w.z < nz) {
+    T f[LAT::Q];
+#pragma unroll
+    for (int q = 0; q < LAT::Q; q++) f[q] = fn[q];
+    const int cx = x, cy = w.y, cz = w.z;
+    const bool cact = act;
+    w.next();
+    if (w.z < nz) {
+      x = xof(w, act);
+      pull<LAT, STORE>(v, x, w.y, w.z, (w.z * ny + w.y) * pitch + x, act, fn);
+    }
+    fused_core<LAT, STORE>(v, cx, cy, cz, (cz * ny + cy) * pitch + cx, cact, f, wq, cnt, lane);
+  }
+  queue_drain<LAT, STORE>(v, wq, cnt, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -78,6 +164,8 @@ __global__ void __launch_bounds__(128) collide_tma_kernel(View v, int ntiles) {
   Elem* buf1 = buf0 + Q * RW::STRIDE;
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_bounce[2][Q];  // direction q of this buffer came from the node itself
+  const WarpQueue<STORE> wq = warp_queue<LAT, STORE>(smem_raw + 2 * Q * RW::STRIDE * RW::ES, threadIdx.x >> 5);
+  int cnt = 0;
 
   const int nx = v.nx, ny = v.ny, nz = v.nz, pitch = v.pitch;
   const int nxb = (nx + TX - 1) / TX;
@@ -202,18 +290,20 @@ __global__ void __launch_bounds__(128) collide_tma_kernel(View v, int ntiles) {
       const int cx = LAT::c(q, 0);
       const int off = s_bounce[b][q] ? lx : lx - cx;
       // shared memory: a plain load (the __ldg path is for global memory only)
-      f[q] = S::load_shared(cur + q * RW::STRIDE, off, LAT::w(q));
+      f[q] = S::load_shared(cur + q * RW::STRIDE, off);
     }
-    collide_core<LAT, STORE>(v, xx, y, z, active, (z * ny + y) * pitch + xx, f);
+    const int n = (z * ny + y) * pitch + xx;
+    fused_core<LAT, STORE>(v, xx, y, z, n, active, f, wq, cnt, tid & 31);
     __syncthreads();  // buffer b is free for the tile after next
     halo = halo_next;
   }
+  queue_drain<LAT, STORE>(v, wq, cnt, tid & 31);
 }
 
 template <class LAT, int STORE>
 static int tma_smem_bytes() {
   using RW = TmaRow<STORE>;
-  return 2 * LAT::Q * RW::STRIDE * RW::ES;
+  return 2 * LAT::Q * RW::STRIDE * RW::ES + 4 * queue_bytes_per_warp<LAT, STORE>();
 }
 
 template <class LAT, int STORE>
@@ -232,21 +322,62 @@ static void launch_tma(const View& v, cudaStream_t s) {
   collide_tma_kernel<LAT, STORE><<<grid < ntiles ? grid : ntiles, 128, smem, s>>>(v, ntiles);
 }
 
+template <class LAT, int STORE, int MINB, bool PREFETCH>
+static void launch_fused(const View& v, cudaStream_t s) {
+  static int grid = 0;
+  const int smem = 4 * queue_bytes_per_warp<LAT, STORE>();
+  const void* k;
+  if constexpr (PREFETCH) k = (const void*)collide_prefetch_kernel<LAT, STORE, MINB>;
+  else k = (const void*)collide_kernel<LAT, STORE, MINB>;
+  if (grid == 0) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  const int ntiles = ((v.nx + 127) / 128) * v.ny * v.nz;
+  const int g = grid < ntiles ? grid : ntiles;
+  if constexpr (PREFETCH) collide_prefetch_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);
+  else collide_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);
+}
+
 template <class LAT, int STORE, int MINB>
-static void launch_one(const View& v, cudaStream_t s) {
-  dim3 grid((v.nx + 127) / 128, v.ny, v.nz);
-  collide_kernel<LAT, STORE, MINB><<<grid, 128, 0, s>>>(v);
+static void launch_packed(const View& v, cudaStream_t s) {
+  const int smem = 2 * queue_bytes_per_warp<LAT, STORE>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(collide_packed_kernel<LAT, STORE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  collide_packed_kernel<LAT, STORE, MINB><<<dim3((v.nx + 127) / 128, v.ny, v.nz), 128, smem, s>>>(v);
 }
 
 // collide variants (chosen per simulation, see lbm_imb_set_collide_variant):
-//   0  one node per thread, 128-thread CTAs, occupancy left to the compiler
+//   0  persistent fused form, register budget for 4 CTAs per SM
 //   1  same, register budget for 8 CTAs per SM
 //   2  TMA-pipelined persistent form (reduced-precision storages; FP64 uses 0)
+//   3  persistent fused form, register budget for 6 CTAs per SM
+//   4  software-pipelined fused form (next tile pulled ahead), 4 CTAs per SM
+//   5  the same, 3 CTAs per SM
+//   6  CTA-packed form, one CTA per row tile, register budget for 8 CTAs/SM
+//   7  the same, 5 CTAs per SM
 template <class LAT, int STORE>
 static void dispatch(const View& v, cudaStream_t s) {
-  if (v.collide_variant == 1) launch_one<LAT, STORE, 8>(v, s);
-  else if (v.collide_variant == 2 && STORE != LBM_IMB_STORE_F64) launch_tma<LAT, STORE>(v, s);
-  else launch_one<LAT, STORE, 1>(v, s);
+  switch (v.collide_variant) {
+    case 1: launch_fused<LAT, STORE, 8, false>(v, s); break;
+    case 2:
+      if (STORE != LBM_IMB_STORE_F64) launch_tma<LAT, STORE>(v, s);
+      else launch_fused<LAT, STORE, 4, false>(v, s);
+      break;
+    case 3: launch_fused<LAT, STORE, 6, false>(v, s); break;
+    case 4: launch_fused<LAT, STORE, 4, true>(v, s); break;
+    case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
+    case 6: launch_packed<LAT, STORE, 8>(v, s); break;
+    case 7: launch_packed<LAT, STORE, 5>(v, s); break;
+    default: launch_fused<LAT, STORE, 4, false>(v, s);
+  }
 }
 
 void launch_collide(const View& v, cudaStream_t s) {

@@ -86,10 +86,12 @@ struct View {
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i
+  double cg3[19];  // 3 c_q . g_f
+  double omc;     // 1 - omega
   // FP32 copies for the reduced-precision kernels (a double -> float
   // conversion runs on the FP64 pipe, so none happens per node)
-  float tau_f, omega_f, rho0_f;
-  float fq_f[19];
+  float tau_f, omega_f, rho0_f, omc_f;
+  float fq_f[19], cg3_f[19];
   int substeps;
   int collide_variant;  // kernel form of the collision (0, 1, 2)
   // device error word

@@ -24,6 +24,8 @@ _dp = C.POINTER(C.c_double)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EOWNERS, EBIN = 0, -1, -2, -3, -4, -5, -6, -7, -8
 MAX_OWNERS = 4
+# kernel families of one step, in the order of lbm_imb_step_profiled's array
+KERNEL_FAMILIES = ("eps_clear", "eps_raster", "collide", "dem")
 
 
 class LbmImbError(RuntimeError):
@@ -247,10 +249,10 @@ class Simulation:
     def step_profiled(self, n: int):
         """Run n steps with CUDA events between kernel families; returns
         (per-family ms dict, total ms)."""
-        k = (C.c_double * 4)()
+        k = (C.c_double * len(KERNEL_FAMILIES))()
         t = C.c_double()
         _check(lib().lbm_imb_step_profiled(self.h, int(n), k, C.byref(t)), "lbm_imb_step_profiled")
-        names = ("eps_clear", "eps_raster", "collide", "dem")
+        names = KERNEL_FAMILIES
         return {nm: float(k[i]) for i, nm in enumerate(names)}, float(t.value)
 
     def set_collide_variant(self, variant: int):
@@ -403,7 +405,7 @@ class Batch:
         _check(lib().lbm_imb_sync(self.h), "lbm_imb_sync")
 
     def step_profiled(self, n: int):
-        k = (C.c_double * 4)()
+        k = (C.c_double * len(KERNEL_FAMILIES))()
         t = C.c_double()
         _check(lib().lbm_imb_step_profiled(self.h, int(n), k, C.byref(t)), "lbm_imb_step_profiled")
         return float(t.value)

@@ -207,3 +207,34 @@ def test_reduced_storage_error(storage, tol_u, tol_f):
     mlo = red.totals()[0]
     print(f"{storage}: velocity L2 rel {l2:.2e}, force rel {ferr:.2e}, mass drift {abs(mlo - m64) / m64:.2e}")
     assert l2 < tol_u and ferr < tol_f and abs(mlo - m64) / m64 < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# kernel forms of the plain collision: the same populations
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f64", "f32dev", "f16dev"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_collide_variants_agree(dim, storage):
+    """Every kernel form gives bitwise the populations of form 0 after one
+    step (nx = 300 spans ragged row tiles), and the FP64 forms stay within
+    the oracle tolerance after 12 steps."""
+    if dim == 3:
+        cfg = I.config3_scaled(nx=300, ny=20, nz=12).replace(storage=storage)
+    else:
+        cfg = I.channel_config(nx=300, ny=64, n_particles=12, radius=5.0, storage=storage)
+    L = lbm()
+    base = L.Simulation(cfg)
+    base.step(1)
+    f_base = base.populations()
+    for var in (1, 2, 3, 4, 5, 6, 7):
+        sim = L.Simulation(cfg)
+        sim.set_collide_variant(var)
+        sim.step(1)
+        assert np.array_equal(sim.populations(), f_base), f"variant {var}"
+        if storage == "f64":
+            ref = O.OracleSim(cfg)
+            ref.step(12)
+            sim.step(11)
+            assert rel_err(sim.populations(), ref.populations()) < POP_TOL, f"variant {var}"
+    with pytest.raises(L.LbmImbError):
+        base.set_collide_variant(8)
