@@ -66,6 +66,17 @@ WORKLOADS = {
 }
 
 
+# FP64 operations (DADD, DMUL, DFMA: one FP64-pipe slot each) the collision
+# executes per node, counted with ncu (smsp__sass_thread_inst_executed_op_
+# {dadd,dmul,dfma}) on the 192x384x192 D3Q19 channel: with no particles, and
+# with the config-3 solid fraction (covered fraction 0.218).
+FP64_OPS_PER_NODE = 148.0          # pull + moments + BGK of every node
+FP64_OPS_PER_COVERED_NODE = 225.0  # + immersed-boundary update of a covered node
+# FP64 pipe peak: the nominal 1.25 TFLOP/s of the GB300 FP64 units, i.e.
+# 625 G FP64-pipe operations per second (a DFMA counts two flops, one slot)
+FP64_PIPE_PEAK_GOPS = 625.0
+
+
 def algorithmic_bytes_per_lup(cfg, owned_fraction):
     """Read and write each population once (2 Q s), read the owner word of
     every node (4 B), read the covered fraction at owned nodes."""
@@ -459,6 +470,21 @@ def run_ours(args):
         cpu = cpu_oracle_sample()
 
     sim.close()
+    kname = f"collide_kernel<{'D3Q19' if cfg.dim == 3 else 'D2Q9'},{cfg.storage}>"
+    roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname, "bytes_per_lup": bpl,
+                "owned_fraction": fo, "peak_src": peaks["src"]}
+    if cfg.storage == "f64":
+        # the FP64 collision is bound by the FP64 pipe, not by HBM
+        ops = (FP64_OPS_PER_NODE + FP64_OPS_PER_COVERED_NODE * fo) * cfg.n_nodes
+        gops = ops / (t_coll * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
+                    "unit": "G FP64-pipe op/s", "frac": gops / FP64_PIPE_PEAK_GOPS, "traffic": None,
+                    "kernel": kname, "ops_per_node": FP64_OPS_PER_NODE,
+                    "ops_per_covered_node": FP64_OPS_PER_COVERED_NODE, "owned_fraction": fo,
+                    "peak_src": "nominal FP64 1.25 TFLOP/s of the profiling recipe / 2 flops per DFMA"}
+    else:
+        roofline = roof_hbm
     if rank == 0:
         clocks = clk.summary()
         line = {
@@ -469,11 +495,8 @@ def run_ours(args):
             "config": {"workload": wl["name"], "storage": cfg.storage, "nodes": cfg.n_nodes,
                        "particles": cfg.n_particles, "l2": "inputs larger than L2 (two lattices, "
                        f"{2 * (19 if cfg.dim == 3 else 9) * {'f64': 8, 'f32dev': 4, 'f16dev': 2}[cfg.storage] * cfg.n_nodes / 1e9:.1f} GB)", "graph": "CUDA graph per step"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": f"collide_kernel<{'D3Q19' if cfg.dim == 3 else 'D2Q9'},{cfg.storage}>",
-                         "bytes_per_lup": bpl,
-                         "owned_fraction": fo, "peak_src": peaks["src"]},
+            "roofline": roofline,
+            "roofline_hbm": roof_hbm,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "profiled_ms_per_step": tot / args.steps,
             "collide_variant": tune["variant"], "collide_tuning": tune.get("table"),

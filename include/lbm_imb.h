@@ -351,6 +351,13 @@ int lbm_imb_mlp_destroy(lbm_imb_mlp_t* m);
 int lbm_imb_mlp_probe_gemm(const uint16_t* a_host, const uint16_t* b_host, int N, int K,
                            float* d_host, void* dev_scratch, size_t scratch_bytes, void* stream);
 
+/* Test hook for the first-quadrant arctangent of the exact-volume formulas
+ * (FP64 rasterisation): for device arrays y, x [n] (y, x >= 0, not both
+ * zero) writes the library's atan2 to fast [n] and CUDA's atan2 to ref [n]
+ * (device arrays, caller-owned), then synchronises the stream.  n > 2^31
+ * elements is not supported.  EINVAL on null pointers or n < 0. */
+int lbm_imb_probe_atan2q1(const double* y, const double* x, double* fast, double* ref, int64_t n, void* stream);
+
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */
 int lbm_imb_destroy(lbm_imb_t* h);

@@ -8,6 +8,36 @@
 
 namespace lbm {
 
+// Division of small non-negative ints (t < 2^16) by a per-particle divisor
+// d < 2^16 by one high multiply: q = floor(t * (floor((2^32 - 1)/d) + 1) /
+// 2^32) is exact there (the error of the scaled reciprocal is below t/2^32
+// < 1/d).  One integer division per divisor instead of one per index.
+struct FastDiv {
+  unsigned d, m;
+  __device__ __forceinline__ explicit FastDiv(int dd) : d((unsigned)dd), m(dd > 1 ? 0xFFFFFFFFu / (unsigned)dd + 1u : 0u) {}
+  __device__ __forceinline__ int div(int t) const { return d > 1 ? (int)__umulhi((unsigned)t, m) : t; }
+};
+
+// t = i + ex (j + ey k) -> (i, j, k)
+struct FastDiv3 {
+  FastDiv a, b;
+  __device__ __forceinline__ FastDiv3(int ex, int ey) : a(ex), b(ex * ey) {}
+  __device__ __forceinline__ void split(int t, int& i, int& j, int& k) const {
+    k = b.div(t);
+    const int r = t - k * (int)b.d;
+    j = a.div(r);
+    i = r - j * (int)a.d;
+  }
+};
+
+// periodic index into [0, n) for boxes reaching at most one period outside
+__device__ __forceinline__ int wrap_idx(int i, const int n) {
+  if (i < 0) i += n;
+  else if (i >= n) i -= n;
+  if ((unsigned)i >= (unsigned)n) i = ((i % n) + n) % n;  // lattices smaller than a particle box
+  return i;
+}
+
 // --------------------------------------------------------------------------
 // clear the previous footprint (all owner slots) and zero the force sums
 // --------------------------------------------------------------------------
@@ -18,17 +48,18 @@ __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, c
   const int lx = box[0], ly = box[1], lz = box[2];
   const int ex = box[3], ey = box[4], ez = box[5];
   const int total = ex * ey * ez;
+  const FastDiv3 fd(ex, ey);
   for (int t = lane; t < total; t += 32) {
-    int i = lx + t % ex;
-    int j = ly + (t / ex) % ey;
-    int k = lz + t / (ex * ey);
+    int ci, cj, ck;
+    fd.split(t, ci, cj, ck);
+    int i = lx + ci, j = ly + cj, k = lz + ck;
     if (v.wall_y) {
       if (j < 0 || j >= v.ny) continue;
     } else {
-      j = ((j % v.ny) + v.ny) % v.ny;
+      j = wrap_idx(j, v.ny);
     }
-    i = ((i % v.nx) + v.nx) % v.nx;
-    k = ((k % v.nz) + v.nz) % v.nz;
+    i = wrap_idx(i, v.nx);
+    k = wrap_idx(k, v.nz);
     const long long n = ((long long)k * v.ny + j) * v.pitch + i;
 #pragma unroll
     for (int s = 0; s < kMaxOwners; s++) v.own[s][n] = -1;
@@ -120,6 +151,39 @@ __device__ __forceinline__ int split_axis(const T* b, int i, int zero, int (&lo_
   return 2;
 }
 
+// atan(k/16), k = 0..16 (round to nearest)
+__constant__ double kAtanTab[17] = {
+    0.0,                 0.06241880999595735, 0.12435499454676144, 0.18534794999569476,
+    0.24497866312686414, 0.3028848683749714,  0.35877067027057225, 0.4124104415973873,
+    0.4636476090008061,  0.5123894603107377,  0.5585993153435624,  0.6022873461349642,
+    0.6435011087932844,  0.6823165548747481,  0.7188299996216245,  0.7531512809621944,
+    0.7853981633974483};
+
+// atan2(y, x) for y, x >= 0, not both zero (all angles of the exact-volume
+// formulas lie in the first quadrant).  Method: with t = min/max <= 1 and
+// c = k/16 the nearest table point, the arctangent addition formula gives
+// atan(t) = atan(c) + atan(t'), t' = (t - c)/(1 + t c) = (n - c d)/(d + c n),
+// |t'| <= 1/32 (slightly more if k is off by one); atan(t') is its Taylor
+// series through t'^11 (truncation below 1e-17 relative).  y > x uses
+// pi/2 - atan(x/y).  One FP64 division instead of two plus range logic.
+__device__ __forceinline__ double atan2_q1(const double y, const double x) {
+  const bool sw = y > x;
+  const double num = sw ? x : y, den = sw ? y : x;
+  int k = __float2int_rn(16.f * __fdividef((float)num, (float)den));
+  k = k < 0 ? 0 : (k > 16 ? 16 : k);
+  const double c = (double)k * 0.0625;
+  const double tp = fma(-c, den, num) / fma(c, num, den);
+  const double s = tp * tp;
+  double p = fma(s, -1.0 / 11.0, 1.0 / 9.0);
+  p = fma(s, p, -1.0 / 7.0);
+  p = fma(s, p, 1.0 / 5.0);
+  p = fma(s, p, -1.0 / 3.0);
+  p = fma(s * tp, p, tp);
+  const double r = kAtanTab[k] + p;
+  return sw ? 1.57079632679489661923 - r : r;
+}
+__device__ __forceinline__ float atan2_q1(const float y, const float x) { return atan2f(y, x); }
+
 // one CTA per particle (block-uniform p); smem = dynamic shared memory of the
 // size raster_bytes gives
 template <int DIM, typename T>
@@ -182,10 +246,10 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     if (v.wall_y) {
       if (j < 0 || j >= v.ny) return;
     } else {
-      j = ((j % v.ny) + v.ny) % v.ny;
+      j = wrap_idx(j, v.ny);
     }
-    i = ((i % v.nx) + v.nx) % v.nx;
-    k = ((k % v.nz) + v.nz) % v.nz;
+    i = wrap_idx(i, v.nx);
+    k = wrap_idx(k, v.nz);
     const long long n = ((long long)k * v.ny + j) * v.pitch + i;
 #pragma unroll
     for (int s = 0; s < kMaxOwners; s++) {
@@ -196,15 +260,17 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     }
     atomicOr(v.err, ERR_OWNERS);
   };
+  const FastDiv3 cdiv(ne[0], ne[1]);
   for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-    const int idx[3] = {t % ne[0], (t / ne[0]) % ne[1], t / (ne[0] * ne[1])};
+    int idx[3];
+    cdiv.split(t, idx[0], idx[1], idx[2]);
     const int cls = classify_cell<T>(bnd, bndf, idx, DIM, R2, R2f);
     if (cls == 0) continue;
     if (cls == 1) {
       claim(idx[0], idx[1], idx[2], T(1));
       continue;
     }
-    cells[atomicAdd(&n_part, 1)] = t;
+    cells[atomicAdd(&n_part, 1)] = idx[0] | (idx[1] << 8) | (idx[2] << 16);  // ne <= 62
     int al[2], ah[2], bl[2], bh[2], cl[2] = {0, 0}, ch[2] = {0, 0};
     const int na = split_axis<T>(bnd[0], idx[0], ne[0] + 1, al, ah);
     const int nb = split_axis<T>(bnd[1], idx[1], ne[1] + 1, bl, bh);
@@ -225,25 +291,26 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
       const T u = val[d][i];
       const T su = u < R ? sqrt((R - u) * (R + u)) : T(0);
       ax_s[d][i] = su;
-      ax_psi[d][i] = atan2(su, u);
+      ax_psi[d][i] = atan2_q1(su, u);
     }
   } else {
-    const int dims[3][2] = {{tx, ty}, {tx, tz}, {ty, tz}};
     const int axes[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     const int n01 = tx * ty, n02 = tx * tz, n12 = ty * tz;
+    const FastDiv dx(tx), dy(ty);
     for (int t = threadIdx.x; t < n01 + n02 + n12; t += blockDim.x) {
       const int g = t < n01 ? 0 : (t < n01 + n02 ? 1 : 2);
       const int r = t - (g == 0 ? 0 : (g == 1 ? n01 : n01 + n02));
-      const int i = r % dims[g][0], j = r / dims[g][0];
+      const FastDiv& dv = g == 2 ? dy : dx;
+      const int j = dv.div(r), i = r - j * (int)dv.d;
       const T u = val[axes[g][0]][i], w = val[axes[g][1]][j];
       const T z2 = (R * R - u * u) - w * w;
       T* e = pr + 4 * (g * cap.pair_cap + r);
       if (z2 > T(0)) {
         const T z = sqrt(z2);
         e[0] = z;
-        e[1] = atan2(R * z, u * w);
-        e[2] = atan2(z, u);
-        e[3] = atan2(z, w);
+        e[1] = atan2_q1(R * z, u * w);
+        e[2] = atan2_q1(z, u);
+        e[3] = atan2_q1(z, w);
       } else {  // edge line outside the ball: the limit z -> 0 of the angles
         e[0] = e[1] = e[2] = e[3] = T(0);
       }
@@ -255,9 +322,12 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __syncthreads();
 
   // pass 2: the needed corner values
+  const T iR = T(1) / R;
+  const FastDiv3 tdiv(tx, ty);
   for (int q = threadIdx.x; q < n_need; q += blockDim.x) {
     const int t = clist[q];
-    const int i = t % tx, j = (t / tx) % ty, k = t / (tx * ty);
+    int i, j, k;
+    tdiv.split(t, i, j, k);
     const T a = val[0][i], b = val[1][j];
     T out = T(0);
     if (DIM == 2) {
@@ -274,12 +344,12 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
         const T tha = ab[3] + ac[3] - hpi;
         const T thb = ab[2] + bc[3] - hpi;
         const T thc = ac[2] + bc[2] - hpi;
-        const T om = ab[1] + ac[1] + bc[1] - T(2) * hpi - (a * tha + b * thb + cc * thc) / R;
+        const T om = ab[1] + ac[1] + bc[1] - T(2) * hpi - (a * tha + b * thb + cc * thc) * iR;
         const T R2t = R * R;
         const T Aa = T(0.5) * (R2t - a * a) * tha - T(0.5) * (b * zab + cc * zac) + b * cc;
         const T Ab = T(0.5) * (R2t - b * b) * thb - T(0.5) * (a * zab + cc * zbc) + a * cc;
         const T Ac = T(0.5) * (R2t - cc * cc) * thc - T(0.5) * (a * zac + b * zbc) + a * b;
-        out = (R2t * R * om - a * Aa - b * Ab - cc * Ac) / T(3);
+        out = (R2t * R * om - a * Aa - b * Ab - cc * Ac) * T(1.0 / 3.0);
       }
     }
     tab[t] = out;
@@ -289,7 +359,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   // pass 3: partially covered cells
   for (int q = threadIdx.x; q < n_part; q += blockDim.x) {
     const int t = cells[q];
-    const int idx[3] = {t % ne[0], (t / ne[0]) % ne[1], t / (ne[0] * ne[1])};
+    const int idx[3] = {t & 0xff, (t >> 8) & 0xff, t >> 16};
     int al[2], ah[2], bl[2], bh[2], cl[2] = {0, 0}, ch[2] = {0, 0};
     const int na = split_axis<T>(bnd[0], idx[0], ne[0] + 1, al, ah);
     const int nb = split_axis<T>(bnd[1], idx[1], ne[1] + 1, bl, bh);

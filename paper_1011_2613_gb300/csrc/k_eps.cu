@@ -72,4 +72,21 @@ int eps_raster_set_attrs(int bytes) {
   return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) ? 0 : -1;
 }
 
+__global__ void atan2_probe_kernel(const double* y, const double* x, double* fast, double* ref, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  fast[i] = atan2_q1(y[i], x[i]);
+  ref[i] = atan2(y[i], x[i]);
+}
+
 }  // namespace lbm
+
+extern "C" int lbm_imb_probe_atan2q1(const double* y, const double* x, double* fast, double* ref, int64_t n,
+                                     void* stream) {
+  if (!y || !x || !fast || !ref || n < 0) return LBM_IMB_EINVAL;
+  if (n == 0) return LBM_IMB_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lbm::atan2_probe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, fast, ref, (long long)n);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return LBM_IMB_ECUDA;
+  return LBM_IMB_OK;
+}

@@ -112,6 +112,9 @@ def lib():
             L.lbm_imb_batch_get_launch.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.lbm_imb_batch_set_barrier_test.restype = C.c_int
             L.lbm_imb_batch_set_barrier_test.argtypes = [C.c_void_p, C.c_int64, C.c_int]
+            L.lbm_imb_probe_atan2q1.restype = C.c_int
+            L.lbm_imb_probe_atan2q1.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                                C.c_void_p]
             L.lbm_imb_destroy.restype = C.c_int
             L.lbm_imb_destroy.argtypes = [C.c_void_p]
             L.lbm_imb_strerror.restype = C.c_char_p
@@ -422,3 +425,17 @@ class Batch:
     def set_barrier_test(self, spin_limit: int, phantom: int):
         _check(lib().lbm_imb_batch_set_barrier_test(self.h, int(spin_limit), int(phantom)),
                "lbm_imb_batch_set_barrier_test")
+
+
+def probe_atan2q1(y, x):
+    """The library's first-quadrant atan2 (FP64 rasterisation) and CUDA's
+    atan2 on device tensors y, x (float64, same shape); returns (fast, ref)."""
+    import torch
+    y = y.contiguous()
+    x = x.contiguous()
+    fast = torch.empty_like(y)
+    ref = torch.empty_like(y)
+    s = torch.cuda.current_stream(y.device)
+    _check(lib().lbm_imb_probe_atan2q1(y.data_ptr(), x.data_ptr(), fast.data_ptr(), ref.data_ptr(), y.numel(),
+                                        s.cuda_stream), "lbm_imb_probe_atan2q1")
+    return fast, ref
