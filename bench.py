@@ -67,11 +67,18 @@ WORKLOADS = {
 
 
 # FP64 operations (DADD, DMUL, DFMA: one FP64-pipe slot each) the collision
-# executes per node, counted with ncu (smsp__sass_thread_inst_executed_op_
-# {dadd,dmul,dfma}) on the 192x384x192 D3Q19 channel: with no particles, and
-# with the config-3 solid fraction (covered fraction 0.218).
-FP64_OPS_PER_NODE = 148.0          # pull + moments + BGK of every node
-FP64_OPS_PER_COVERED_NODE = 225.0  # + immersed-boundary update of a covered node
+# executes per node, by lattice dimension: (every node: pull, moments, BGK;
+# extra per covered node: the immersed-boundary update).  Counted with ncu
+# (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}) on the profiling
+# cases of paper_1011_2613_gb300.profile_case with and without particles:
+# D3Q19 192x384x192 (covered fraction 0.218), D2Q9 2048x4096 (0.067).
+FP64_OPS = {3: (148.0, 225.0), 2: (68.0, 151.0)}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node of
+# one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
+# case at the config-3 solid fraction (forms 5 / 6 / 6); a config-3 launch
+# moves this many bytes per node times its node count (same solid fraction).
+TRAFFIC_B_PER_NODE = {("f64", 3): 376.3, ("f32dev", 3): 186.6, ("f16dev", 3): 104.8}
+
 # FP64 pipe peak: the nominal 1.25 TFLOP/s of the GB300 FP64 units, i.e.
 # 625 G FP64-pipe operations per second (a DFMA counts two flops, one slot)
 FP64_PIPE_PEAK_GOPS = 625.0
@@ -250,6 +257,8 @@ def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=N
     res = {"mlups": cfg.n_nodes * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
            "collide_ms": t_coll, "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "bytes_per_lup": bpl, "collide_gbs": achieved, "hbm_frac": achieved / peaks["hbm_gbs"],
+           "traffic": (TRAFFIC_B_PER_NODE[(cfg.storage, cfg.dim)] * cfg.n_nodes
+                       if (cfg.storage, cfg.dim) in TRAFFIC_B_PER_NODE else None),
            "collide_variant": tune["variant"], "collide_tuning": tune.get("table")}
     if ref_sim is not None:
         done += args.warmup + 2 * args.steps
@@ -471,17 +480,21 @@ def run_ours(args):
 
     sim.close()
     kname = f"collide_kernel<{'D3Q19' if cfg.dim == 3 else 'D2Q9'},{cfg.storage}>"
+    tb = TRAFFIC_B_PER_NODE.get((cfg.storage, cfg.dim))
+    traffic = tb * cfg.n_nodes if tb is not None and args.workload in ("cfg3", "cfg3s") else None
     roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname, "bytes_per_lup": bpl,
-                "owned_fraction": fo, "peak_src": peaks["src"]}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname, "bytes_per_lup": bpl,
+                "owned_fraction": fo, "peak_src": peaks["src"],
+                "traffic_src": "ncu capture of the 192x384x192 case scaled by nodes" if traffic else None}
     if cfg.storage == "f64":
         # the FP64 collision is bound by the FP64 pipe, not by HBM
-        ops = (FP64_OPS_PER_NODE + FP64_OPS_PER_COVERED_NODE * fo) * cfg.n_nodes
+        per_node, per_cov = FP64_OPS[cfg.dim]
+        ops = (per_node + per_cov * fo) * cfg.n_nodes
         gops = ops / (t_coll * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
-                    "unit": "G FP64-pipe op/s", "frac": gops / FP64_PIPE_PEAK_GOPS, "traffic": None,
-                    "kernel": kname, "ops_per_node": FP64_OPS_PER_NODE,
-                    "ops_per_covered_node": FP64_OPS_PER_COVERED_NODE, "owned_fraction": fo,
+                    "unit": "G FP64-pipe op/s", "frac": gops / FP64_PIPE_PEAK_GOPS, "traffic": traffic,
+                    "kernel": kname, "ops_per_node": per_node,
+                    "ops_per_covered_node": per_cov, "owned_fraction": fo,
                     "peak_src": "nominal FP64 1.25 TFLOP/s of the profiling recipe / 2 flops per DFMA"}
     else:
         roofline = roof_hbm

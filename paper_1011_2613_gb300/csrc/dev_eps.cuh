@@ -39,7 +39,7 @@ __device__ __forceinline__ int wrap_idx(int i, const int n) {
 }
 
 // --------------------------------------------------------------------------
-// clear the previous footprint (all owner slots) and zero the force sums
+// clear the previous footprint (the taken owner slots) and zero the force sums
 // --------------------------------------------------------------------------
 // one warp per particle
 __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, const int lane,
@@ -61,8 +61,13 @@ __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, c
     i = wrap_idx(i, v.nx);
     k = wrap_idx(k, v.nz);
     const long long n = ((long long)k * v.ny + j) * v.pitch + i;
-#pragma unroll
-    for (int s = 0; s < kMaxOwners; s++) v.own[s][n] = -1;
+    // taken slots form a prefix: stop at the first free one (concurrent
+    // clears of overlapping boxes only ever write -1, so the order of their
+    // reads and writes does not matter)
+    for (int s = 0; s < kMaxOwners; s++) {
+      if (v.own[s][n] < 0) break;
+      v.own[s][n] = -1;
+    }
   }
   // FP32 kinematics record of the particle for the reduced-precision
   // collision: position split into the nearest node (int) and the offset
