@@ -455,10 +455,11 @@ def run_ours(args):
     variants = {}
     if not args.no_variants and rank == 0 and cfg.storage == "f64":
         steps_done = tuned_steps + args.warmup + 2 * args.steps + (args.steps if e2e else 0)
-        for st in ("f32dev", "f16dev"):
+        forms = [("f32dev", cfg.replace(storage="f32dev")), ("f16dev", cfg.replace(storage="f16dev")),
+                 ("f64_eps_table", cfg.replace(eps_method=1))]  # Eq. 6 covered fractions
+        for st, c in forms:
             try:
-                variants[st], steps_done = measure_variant(cfg.replace(storage=st), args, torch, peaks, st, sim,
-                                                           steps_done)
+                variants[st], steps_done = measure_variant(c, args, torch, peaks, st, sim, steps_done)
             except Exception as ex:  # report, keep the headline line
                 variants[st] = {"error": str(ex)}
 

@@ -103,7 +103,12 @@ typedef struct lbm_imb_config {
   double k_n;              /* DEM normal stiffness, >= 0 */
   double restitution;      /* DEM restitution coefficient e in (0, 1] */
   int32_t dem_substeps;    /* DEM sub-steps per lattice step, >= 1 */
-  int32_t reserved0;
+  int32_t eps_method;      /* covered fractions: 0 exact closed forms; 1 the table
+                            * lookup of Eq. 6: exact fractions on a grid over the
+                            * cell's offset from the centre (2D 256 radii x 128
+                            * slopes, 3D 96 x 64 x 48), FP32 interpolation;
+                            * needs all radii equal and > 1, else
+                            * LBM_IMB_EUNSUPPORTED */
   int64_t n_particles;     /* >= 0 */
   const double* pos;       /* host, [n][3], copied at init */
   const double* vel;       /* host, [n][3], copied at init */
@@ -124,7 +129,10 @@ size_t lbm_imb_required_bytes(const lbm_imb_config* cfg);
  * particles, set the populations to the rest equilibrium w_i rho0 and
  * rasterise eps.  cuda_stream (a cudaStream_t, may be NULL for the legacy
  * stream) is the stream every later call of this handle uses.  On success
- * *out receives the handle.  The device current at this call is used. */
+ * *out receives the handle.  The device current at this call is used.
+ * A rejected config returns its status (EINVAL, EUNSUPPORTED) before the
+ * buffer is looked at, so a call with dev_buf = NULL reports why
+ * lbm_imb_required_bytes returned 0. */
 int lbm_imb_init(const lbm_imb_config* cfg, void* dev_buf, size_t bytes,
                  void* cuda_stream, lbm_imb_t** out);
 

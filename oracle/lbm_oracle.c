@@ -427,10 +427,156 @@ typedef struct oracle_sim {
   int* own_p;          /* [N*OR_MAX_OWNERS] particle ids, ascending */
   double* own_e;       /* [N*OR_MAX_OWNERS] covered fraction per owner */
   long step;
+  int eps_method;      /* 0 exact covered fractions, 1 the table of Eq. (6) */
+  float* tab;          /* Eq. (6) table */
+  float tab_lo_r, tab_h_r, tab_h_s, tab_h_t;
 } oracle_sim;
 
 static long node_index(const oracle_sim* s, int x, int y, int z) {
   return ((long)z * s->n[1] + y) * s->n[0] + x;
+}
+
+int oracle_rasterize(oracle_sim* s);
+
+/* ------------------------------------------------------------------ */
+/* Eq. (6): covered fraction looked up in a table over the cell's      */
+/* position relative to the particle centre (one radius R).            */
+/* With the sorted offsets a >= b (>= c) >= 0 of the cell centre:       */
+/*   2D: r = |(a,b)| on [R - sqrt(2)/2, R + sqrt(2)/2], 256 points;     */
+/*       t = b/a on [0, 1], 128 points;                                 */
+/*   3D: r = |(a,b,c)| on [R - sqrt(3)/2, R + sqrt(3)/2], 96 points;    */
+/*       s = |(b,c)|/a on [0, sqrt(2)], 64 points; t = c/b on [0,1], 48. */
+/* Entries: the exact fraction at the grid point, stored in FP32;       */
+/* lookup: (bi/tri)linear interpolation in FP32, each operation rounded */
+/* on its own.  Cells entirely inside take 1, outside 0 (as R10).        */
+/* ------------------------------------------------------------------ */
+#define OT_R2 256
+#define OT_T2 128
+#define OT_R3 96
+#define OT_S3 64
+#define OT_T3 48
+
+static float ot_lerp(float x, float y, float w) {
+  float a = (1.0f - w) * x;
+  float b = w * y;
+  return a + b;
+}
+
+static float ot_coord(float x, float lo, float h, int n, int* i) {
+  float f = (x - lo) / h;
+  if (f < 0.0f) f = 0.0f;
+  if (f > (float)(n - 1)) f = (float)(n - 1);
+  int k = (int)f;
+  if (k > n - 2) k = n - 2;
+  *i = k;
+  return f - (float)k;
+}
+
+static float ot_lookup(const oracle_sim* s, const double off[3]) {
+  float a = fabsf((float)off[0]), b = fabsf((float)off[1]), c = s->dim == 3 ? fabsf((float)off[2]) : 0.0f;
+  float t0;
+  if (a < b) { t0 = a; a = b; b = t0; }
+  if (s->dim == 3) {
+    if (b < c) { t0 = b; b = c; c = t0; }
+    if (a < b) { t0 = a; a = b; b = t0; }
+  }
+  if (s->dim == 2) {
+    float r = sqrtf(a * a + b * b);
+    float t = a > 0.0f ? b / a : 0.0f;
+    int i, j;
+    float wr = ot_coord(r, s->tab_lo_r, s->tab_h_r, OT_R2, &i);
+    float wt = ot_coord(t, 0.0f, s->tab_h_t, OT_T2, &j);
+    const float* T = s->tab;
+    float lo_r = ot_lerp(T[i * OT_T2 + j], T[i * OT_T2 + j + 1], wt);
+    float hi_r = ot_lerp(T[(i + 1) * OT_T2 + j], T[(i + 1) * OT_T2 + j + 1], wt);
+    return ot_lerp(lo_r, hi_r, wr);
+  }
+  float aa = a * a, bb = b * b, cc = c * c;
+  float r = sqrtf((aa + bb) + cc);
+  float sv = a > 0.0f ? sqrtf(bb + cc) / a : 0.0f;
+  float t = b > 0.0f ? c / b : 0.0f;
+  int i, j, k;
+  float wr = ot_coord(r, s->tab_lo_r, s->tab_h_r, OT_R3, &i);
+  float ws = ot_coord(sv, 0.0f, s->tab_h_s, OT_S3, &j);
+  float wt = ot_coord(t, 0.0f, s->tab_h_t, OT_T3, &k);
+  float v[2];
+  for (int di = 0; di < 2; di++) {
+    const float* T = s->tab + ((i + di) * OT_S3 + j) * OT_T3 + k;
+    float lo_s = ot_lerp(T[0], T[1], wt);
+    float hi_s = ot_lerp(T[OT_T3], T[OT_T3 + 1], wt);
+    v[di] = ot_lerp(lo_s, hi_s, ws);
+  }
+  return ot_lerp(v[0], v[1], wr);
+}
+
+/* switch a simulation to the table (all radii equal and > 1); rebuilds the
+ * owners.  Returns 0, or -1 if the radii differ. */
+int oracle_set_eps_table(oracle_sim* s) {
+  if (s->np == 0) return 0;
+  double R = s->rad[0];
+  for (int p = 1; p < s->np; p++)
+    if (s->rad[p] != R) return -1;
+  if (!(R > 1.0)) return -1;
+  free(s->tab);
+  if (s->dim == 2) {
+    s->tab = (float*)malloc(sizeof(float) * OT_R2 * OT_T2);
+    for (int i = 0; i < OT_R2; i++)
+      for (int j = 0; j < OT_T2; j++) {
+        double r = (R - sqrt(2.0) / 2.0) + i * (sqrt(2.0) / (OT_R2 - 1));
+        double t = j * (1.0 / (OT_T2 - 1));
+        double a = r / sqrt(1.0 + t * t);
+        s->tab[i * OT_T2 + j] = (float)oracle_cell_fraction(2, 0.0, 0.0, 0.0, R, a, a * t, 0.0);
+      }
+    s->tab_lo_r = (float)(R - sqrt(2.0) / 2.0);
+    s->tab_h_r = (float)(sqrt(2.0) / (OT_R2 - 1));
+    s->tab_h_s = 0.0f;
+    s->tab_h_t = (float)(1.0 / (OT_T2 - 1));
+  } else {
+    s->tab = (float*)malloc(sizeof(float) * OT_R3 * OT_S3 * OT_T3);
+    for (int i = 0; i < OT_R3; i++)
+      for (int j = 0; j < OT_S3; j++)
+        for (int k = 0; k < OT_T3; k++) {
+          double r = (R - sqrt(3.0) / 2.0) + i * (sqrt(3.0) / (OT_R3 - 1));
+          double sv = j * (sqrt(2.0) / (OT_S3 - 1));
+          double t = k * (1.0 / (OT_T3 - 1));
+          double a = r / sqrt(1.0 + sv * sv);
+          double b = a * sv / sqrt(1.0 + t * t);
+          s->tab[(i * OT_S3 + j) * OT_T3 + k] = (float)oracle_cell_fraction(3, 0.0, 0.0, 0.0, R, a, b, b * t);
+        }
+    s->tab_lo_r = (float)(R - sqrt(3.0) / 2.0);
+    s->tab_h_r = (float)(sqrt(3.0) / (OT_R3 - 1));
+    s->tab_h_s = (float)(sqrt(2.0) / (OT_S3 - 1));
+    s->tab_h_t = (float)(1.0 / (OT_T3 - 1));
+  }
+  s->eps_method = 1;
+  return oracle_rasterize(s);
+}
+
+/* the table value at an arbitrary offset of the cell centre (test hook) */
+double oracle_eps_table_value(const oracle_sim* s, double ox, double oy, double oz) {
+  double off[3] = {ox, oy, oz};
+  return (double)ot_lookup(s, off);
+}
+
+/* Eq. (6) fraction of cell (i,j,k) for the ball (c, R): 1 inside, 0 outside,
+ * the table in between (clamped to [0, 1]) */
+static double table_cell_fraction(const oracle_sim* s, const double c[3], double R, int i, int j, int k) {
+  int idx[3] = {i, j, k};
+  double near2 = 0.0, far2 = 0.0, off[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < s->dim; d++) {
+    double bl = ((double)idx[d] - 0.5) - c[d], bh = ((double)idx[d] + 0.5) - c[d];
+    double nd = bl > 0.0 ? bl : (bh < 0.0 ? -bh : 0.0);
+    double fd = fabs(bl) > fabs(bh) ? fabs(bl) : fabs(bh);
+    near2 += nd * nd;
+    far2 += fd * fd;
+    off[d] = (double)idx[d] - c[d];
+  }
+  if (near2 >= R * R) return 0.0;
+  if (far2 <= R * R) return 1.0;
+  float e = ot_lookup(s, off);
+  if (e < 0.0f) e = 0.0f;
+  if (e > 1.0f) e = 1.0f;
+  return (double)e;
 }
 
 /* eps rasterisation: for each particle (ascending id) every node whose cell
@@ -460,7 +606,8 @@ int oracle_rasterize(oracle_sim* s) {
             }
           }
           if (skip) continue;
-          double ev = oracle_cell_fraction(s->dim, c[0], c[1], c[2], R, i, j, k);
+          double ev = s->eps_method == 1 ? table_cell_fraction(s, c, R, i, j, k)
+                                         : oracle_cell_fraction(s->dim, c[0], c[1], c[2], R, i, j, k);
           if (!(ev > 0.0)) continue;
           long n = node_index(s, idx[0], idx[1], idx[2]);
           int m = s->own_n[n];
@@ -547,7 +694,7 @@ oracle_sim* oracle_create(int dim, int nx, int ny, int nz, int wall_y,
 void oracle_destroy(oracle_sim* s) {
   if (!s) return;
   free(s->pos); free(s->vel); free(s->omg); free(s->ff); free(s->tf);
-  free(s->fc); free(s->rad); free(s->mass); free(s->inertia);
+  free(s->fc); free(s->rad); free(s->mass); free(s->inertia); free(s->tab);
   free(s->f); free(s->ft); free(s->fn);
   free(s->own_n); free(s->own_p); free(s->own_e);
   free(s);

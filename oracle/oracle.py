@@ -53,6 +53,10 @@ def _load():
             lib.oracle_volume_ball_box.argtypes = [C.c_double] * 10
             lib.oracle_cell_fraction.restype = C.c_double
             lib.oracle_cell_fraction.argtypes = [C.c_int] + [C.c_double] * 7
+            lib.oracle_set_eps_table.restype = C.c_int
+            lib.oracle_set_eps_table.argtypes = [C.c_void_p]
+            lib.oracle_eps_table_value.restype = C.c_double
+            lib.oracle_eps_table_value.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
             lib.oracle_collide_node.restype = C.c_double
             lib.oracle_collide_node.argtypes = [C.c_int, C.c_double, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
             lib.oracle_dem_advance.restype = None
@@ -191,7 +195,16 @@ class OracleSim:
         self.wall_y = int(cfg.wall_y)
         self.radius = np.asarray(cfg.radius, dtype=np.float64).copy()
         self.steps_done = 0
+        self.eps_method = int(getattr(cfg, "eps_method", 0))
+        if self.eps_method == 1 and lib.oracle_set_eps_table(self.h) != 0:
+            raise ValueError("the Eq. 6 table needs all radii equal and > 1")
         del npa
+
+    def eps_table_value(self, offset) -> float:
+        """Eq. 6 table value for a cell centred at ``offset`` from the particle
+        centre (before the inside/outside classification and the clamp)."""
+        o = [float(x) for x in offset] + [0.0] * (3 - len(offset))
+        return _load().oracle_eps_table_value(self.h, o[0], o[1], o[2])
 
     def close(self):
         if getattr(self, "h", None):

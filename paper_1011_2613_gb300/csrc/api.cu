@@ -40,6 +40,7 @@ struct Layout {
   size_t off_f[2], off_own[lbm::kMaxOwners], off_eps[lbm::kMaxOwners];
   size_t off_pos, off_vel, off_omg, off_rad, off_mass, off_inertia, off_ff, off_tf, off_fc;
   size_t off_lo, off_kin, off_binof, off_bincount, off_binslot, off_err, off_red, off_stage;
+  size_t off_tab;  // Eq. 6 table (eps_method 1), 0 bytes otherwise
   size_t stage_bytes;
   size_t total;
 };
@@ -56,6 +57,7 @@ int validate(const lbm_imb_config* c) {
   if (!(c->rho_fluid > 0.0)) return LBM_IMB_EINVAL;
   if (c->n_particles < 0 || c->n_particles > (1ll << 30)) return LBM_IMB_EINVAL;
   if (c->dem_substeps < 1) return LBM_IMB_EINVAL;
+  if (c->eps_method != 0 && c->eps_method != 1) return LBM_IMB_EINVAL;
   if (c->n_particles > 0) {
     if (!c->pos || !c->radius || !c->density) return LBM_IMB_EINVAL;
     if (!(c->k_n >= 0.0) || !(c->restitution > 0.0 && c->restitution <= 1.0)) return LBM_IMB_EINVAL;
@@ -88,6 +90,11 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->smem = 0;
   if (c->n_particles > 0) {
     if ((c->dim == 3 && rmax > 8.0) || (c->dim == 2 && rmax > 29.0)) return LBM_IMB_EUNSUPPORTED;
+    if (c->eps_method == 1) {  // one table: one radius, and a cell centre never at the table's r < 0
+      for (int64_t p = 0; p < c->n_particles; p++)
+        if (c->radius[p] != c->radius[0]) return LBM_IMB_EUNSUPPORTED;
+      if (!(c->radius[0] > 1.0)) return LBM_IMB_EUNSUPPORTED;
+    }
     L->smem = lbm::eps_raster_smem_bytes(c->dim, c->storage, rmax);
     if (L->smem < 0) return LBM_IMB_EUNSUPPORTED;
   }
@@ -118,6 +125,7 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->off_binslot = take((size_t)nbins * lbm::kBinCap * 4);
   L->off_err = take(16);
   L->off_red = take(8 * 8);
+  L->off_tab = take(c->eps_method == 1 && c->n_particles > 0 ? (size_t)lbm::eps_table_entries(c->dim) * 4 : 0);
   const size_t dense_row = (size_t)c->nx * 8 * (L->Q > 5 ? L->Q : 5);
   const size_t full = dense_row * (size_t)c->ny * nz;
   L->stage_bytes = full < kStageMax ? full : kStageMax;
@@ -317,6 +325,11 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   v.rho0_f = (float)v.rho0;
   v.err = reinterpret_cast<int*>(base + L.off_err);
   v.red = reinterpret_cast<double*>(base + L.off_red);
+  v.eps_method = np > 0 ? c->eps_method : 0;
+  v.eps_tab = reinterpret_cast<const float*>(base + L.off_tab);
+  v.tab_lo_r = v.tab_h_r = v.tab_h_s = v.tab_h_t = 0.f;
+  if (v.eps_method == 1)
+    lbm::eps_table_geometry(c->dim, c->radius[0], &v.tab_lo_r, &v.tab_h_r, &v.tab_h_s, &v.tab_h_t);
   h->f[0] = base + L.off_f[0];
   h->f[1] = base + L.off_f[1];
   h->cur = 0;
@@ -376,6 +389,8 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
     cudaError_t e = cudaMemsetAsync(v.err, 0, 16, h->stream);
     for (int s = 0; s < lbm::kMaxOwners && e == cudaSuccess; s++)
       e = cudaMemsetAsync(v.own[s], 0xff, (size_t)L.plane * 4, h->stream);
+    if (e == cudaSuccess && v.eps_method == 1)
+      e = lbm::launch_eps_table_build(c->dim, c->radius[0], const_cast<float*>(v.eps_tab), h->stream);
     if (e == cudaSuccess) {
       View v0 = view_of(h, 0);
       lbm::launch_init_equilibrium(v0, h->f[0], h->stream);
@@ -667,10 +682,11 @@ size_t lbm_imb_required_bytes(const lbm_imb_config* cfg) {
 
 int lbm_imb_init(const lbm_imb_config* c, void* dev_buf, size_t bytes, void* cuda_stream,
                  lbm_imb_t** out) {
-  if (!out || !dev_buf) return LBM_IMB_EINVAL;
+  if (!out) return LBM_IMB_EINVAL;
   Layout L;
-  int st = make_layout(c, &L);
+  int st = make_layout(c, &L);  // the configuration's own status first
   if (st) return st;
+  if (!dev_buf) return LBM_IMB_EINVAL;
   if (bytes < L.total) return LBM_IMB_ENOMEM;
   if (((uintptr_t)dev_buf) % kAlign) return LBM_IMB_EINVAL;
   lbm_imb* h = new (std::nothrow) lbm_imb();

@@ -189,9 +189,133 @@ __device__ __forceinline__ double atan2_q1(const double y, const double x) {
 }
 __device__ __forceinline__ float atan2_q1(const float y, const float x) { return atan2f(y, x); }
 
+// --------------------------------------------------------------------------
+// Exact fraction of one cell, without tables (builds the Eq. 6 table).
+// corner_area(R, u, v): area of the disk inside {X >= u, Y >= v}, u, v >= 0;
+// corner_volume(R, a, b, c): volume of the ball inside {X >= a, Y >= b,
+// Z >= c} (the closed forms of the rasteriser, evaluated directly).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double corner_area(const double R, const double u, const double v) {
+  if (u * u + v * v >= R * R) return 0.0;
+  const double su = sqrt((R - u) * (R + u)), sv = sqrt((R - v) * (R + v));
+  const double hpi = 1.57079632679489661923;
+  return 0.5 * R * R * (atan2_q1(su, u) + atan2_q1(sv, v) - hpi) - 0.5 * (u * su + v * sv) + u * v;
+}
+
+__device__ __forceinline__ double corner_volume(const double R, const double a, const double b, const double c) {
+  const double R2 = R * R;
+  if ((a * a + b * b) + c * c >= R2) return 0.0;
+  const double hpi = 1.57079632679489661923;
+  const double zab = sqrt((R2 - a * a) - b * b), zac = sqrt((R2 - a * a) - c * c);
+  const double zbc = sqrt((R2 - b * b) - c * c);
+  const double tha = atan2_q1(zab, b) + atan2_q1(zac, c) - hpi;
+  const double thb = atan2_q1(zab, a) + atan2_q1(zbc, c) - hpi;
+  const double thc = atan2_q1(zac, a) + atan2_q1(zbc, b) - hpi;
+  const double om = atan2_q1(R * zab, a * b) + atan2_q1(R * zac, a * c) + atan2_q1(R * zbc, b * c) -
+                    2.0 * hpi - (a * tha + b * thb + c * thc) / R;
+  const double Aa = 0.5 * (R2 - a * a) * tha - 0.5 * (b * zab + c * zac) + b * c;
+  const double Ab = 0.5 * (R2 - b * b) * thb - 0.5 * (a * zab + c * zbc) + a * c;
+  const double Ac = 0.5 * (R2 - c * c) * thc - 0.5 * (a * zac + b * zbc) + a * b;
+  return (R2 * R * om - a * Aa - b * Ab - c * Ac) / 3.0;
+}
+
+// covered fraction of the unit cell centred at offset off from the centre:
+// each axis interval is reflected onto the non-negative half-axis (split at
+// 0 when it straddles it) and the box volume is the alternating sum of the
+// corner functions over its 2^dim corners
+__device__ __forceinline__ double exact_cell_fraction(const int dim, const double R, const double* off) {
+  double lo[3][2], hi[3][2];
+  int np[3] = {1, 1, 1};
+  for (int d = 0; d < 3; d++) {
+    const double l = off[d] - 0.5, h = off[d] + 0.5;
+    if (d >= dim) { lo[d][0] = 0.0; hi[d][0] = 0.0; continue; }
+    if (l >= 0.0) { lo[d][0] = l; hi[d][0] = h; }
+    else if (h <= 0.0) { lo[d][0] = -h; hi[d][0] = -l; }
+    else { lo[d][0] = 0.0; hi[d][0] = -l; lo[d][1] = 0.0; hi[d][1] = h; np[d] = 2; }
+  }
+  double sum = 0.0;
+  for (int ia = 0; ia < np[0]; ia++)
+    for (int ib = 0; ib < np[1]; ib++)
+      for (int ic = 0; ic < (dim == 3 ? np[2] : 1); ic++)
+        for (int s = 0; s < (dim == 3 ? 8 : 4); s++) {
+          const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+          const double x = sx ? hi[0][ia] : lo[0][ia], y = sy ? hi[1][ib] : lo[1][ib];
+          const double vv = dim == 3 ? corner_volume(R, x, y, sz ? hi[2][ic] : lo[2][ic]) : corner_area(R, x, y);
+          sum += ((sx + sy + sz) & 1) ? -vv : vv;
+        }
+  return sum;
+}
+
+// --------------------------------------------------------------------------
+// Eq. 6: covered fraction from a table over the cell's offset from the
+// centre, for one particle radius R.  With the sorted offsets a >= b (>= c)
+// >= 0 the table runs over
+//   2D: r = |(a,b)| in [R - sqrt(2)/2, R + sqrt(2)/2] (kTabR2 points),
+//       t = b/a in [0, 1] (kTabT2 points);
+//   3D: r = |(a,b,c)| in [R - sqrt(3)/2, R + sqrt(3)/2] (kTabR3), s = |(b,c)|/a
+//       in [0, sqrt(2)] (kTabS3), t = c/b in [0, 1] (kTabT3),
+// entries = exact fractions at the grid points (FP32), and a cell takes the
+// (bi/tri)linear interpolation, every FP32 operation rounded on its own (no
+// contraction), so that any IEEE implementation of these steps gives the
+// same value.  Only cells that meet the surface use the table; cells inside
+// take 1 and cells outside 0 as in the exact rasteriser.
+// --------------------------------------------------------------------------
+constexpr int kTabR2 = 256, kTabT2 = 128;
+constexpr int kTabR3 = 96, kTabS3 = 64, kTabT3 = 48;
+
+__device__ __forceinline__ float tab_lerp(const float x, const float y, const float w) {
+  return __fadd_rn(__fmul_rn(__fsub_rn(1.f, w), x), __fmul_rn(w, y));
+}
+
+// index and weight of coordinate x on a grid lo + i h, i = 0..n-1
+__device__ __forceinline__ float tab_coord(const float x, const float lo, const float h, const int n, int& i) {
+  float f = __fdiv_rn(__fsub_rn(x, lo), h);
+  f = fminf(fmaxf(f, 0.f), (float)(n - 1));
+  int k = (int)f;
+  k = k > n - 2 ? n - 2 : k;
+  i = k;
+  return __fsub_rn(f, (float)k);
+}
+
+// off: the cell centre's offset from the particle centre, each component
+// computed in FP64 and rounded to FP32
+template <int DIM>
+__device__ __forceinline__ float eps_table_lookup(const View& v, const float* off) {
+  float a = fabsf(off[0]), b = fabsf(off[1]), c = DIM == 3 ? fabsf(off[2]) : 0.f;
+  float t0;
+  if (a < b) { t0 = a; a = b; b = t0; }
+  if (DIM == 3) {
+    if (b < c) { t0 = b; b = c; c = t0; }
+    if (a < b) { t0 = a; a = b; b = t0; }
+  }
+  const float* T = v.eps_tab;
+  if (DIM == 2) {
+    const float r = __fsqrt_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)));
+    const float t = a > 0.f ? __fdiv_rn(b, a) : 0.f;
+    int i, j;
+    const float wr = tab_coord(r, v.tab_lo_r, v.tab_h_r, kTabR2, i);
+    const float wt = tab_coord(t, 0.f, v.tab_h_t, kTabT2, j);
+    const float* q = T + i * kTabT2 + j;
+    return tab_lerp(tab_lerp(q[0], q[1], wt), tab_lerp(q[kTabT2], q[kTabT2 + 1], wt), wr);
+  }
+  const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
+  const float r = __fsqrt_rn(r2);
+  const float s = a > 0.f ? __fdiv_rn(__fsqrt_rn(__fadd_rn(__fmul_rn(b, b), __fmul_rn(c, c))), a) : 0.f;
+  const float t = b > 0.f ? __fdiv_rn(c, b) : 0.f;
+  int i, j, k;
+  const float wr = tab_coord(r, v.tab_lo_r, v.tab_h_r, kTabR3, i);
+  const float ws = tab_coord(s, 0.f, v.tab_h_s, kTabS3, j);
+  const float wt = tab_coord(t, 0.f, v.tab_h_t, kTabT3, k);
+  const float* q = T + (i * kTabS3 + j) * kTabT3 + k;
+  const int dj = kTabT3, di = kTabS3 * kTabT3;
+  const float c0 = tab_lerp(tab_lerp(q[0], q[1], wt), tab_lerp(q[dj], q[dj + 1], wt), ws);
+  const float c1 = tab_lerp(tab_lerp(q[di], q[di + 1], wt), tab_lerp(q[di + dj], q[di + dj + 1], wt), ws);
+  return tab_lerp(c0, c1, wr);
+}
+
 // one CTA per particle (block-uniform p); smem = dynamic shared memory of the
 // size raster_bytes gives
-template <int DIM, typename T>
+template <int DIM, typename T, bool TABLE = false>
 __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, const RasterSmem cap,
                                                     unsigned char* smem) {
   __syncthreads();  // the block may still be reading the previous particle's tables
@@ -222,6 +346,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ float bndf[3][64];
   __shared__ T val[3][64];  // value lists
   __shared__ T ax_s[2][64], ax_psi[2][64];  // 2D per-axis tables
+  __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
   __shared__ int n_part, n_need;
   const double R2 = R64 * R64;
   const float R2f = (float)R2;
@@ -239,9 +364,11 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     const T b = (d < DIM && i <= ne[d]) ? T(((double)(lo[d] + i) - 0.5) - c[d]) : T(0);
     bnd[d][i] = b;
     bndf[d][i] = (float)b;
+    if constexpr (TABLE) offc[d][i] = (d < DIM && i < ne[d]) ? (float)((double)(lo[d] + i) - c[d]) : 0.f;
     val[d][i] = (d < DIM && i <= ne[d]) ? fabs(b) : T(0);
   }
-  for (int t = threadIdx.x; t < tsize; t += blockDim.x) need[t] = 0;
+  if constexpr (!TABLE)
+    for (int t = threadIdx.x; t < tsize; t += blockDim.x) need[t] = 0;
   __syncthreads();
 
   // pass 1: full cells claim their node at once; partial cells are listed
@@ -275,6 +402,15 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
       claim(idx[0], idx[1], idx[2], T(1));
       continue;
     }
+    if constexpr (TABLE) {  // Eq. 6
+      float off[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int d = 0; d < DIM; d++) off[d] = offc[d][idx[d]];
+      const float e = eps_table_lookup<DIM>(v, off);
+      const float ec = e < 0.f ? 0.f : (e > 1.f ? 1.f : e);
+      if (ec > 0.f) claim(idx[0], idx[1], idx[2], T(ec));
+      continue;
+    }
     cells[atomicAdd(&n_part, 1)] = idx[0] | (idx[1] << 8) | (idx[2] << 16);  // ne <= 62
     int al[2], ah[2], bl[2], bh[2], cl[2] = {0, 0}, ch[2] = {0, 0};
     const int na = split_axis<T>(bnd[0], idx[0], ne[0] + 1, al, ah);
@@ -288,6 +424,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
             need[(zs[(s >> 2) & 1] * ty + ys[(s >> 1) & 1]) * tx + xs[s & 1]] = 1;
         }
   }
+  if constexpr (TABLE) return;
   // per-axis (2D) or per-pair (3D) angle tables
   const T hpi = T(1.57079632679489661923);
   if (DIM == 2) {

@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(128) batch_step_kernel(BatchArgs a) {
   // B: eps rasterisation, binning
   for (int i = blockIdx.x; i < P; i += gridDim.x) {
     const int m = member_of(a.part_off, a.nm, i);
-    eps_raster_particle<LAT::DIM, TE>(a.views[m], i - a.part_off[m], a.cap, smem);
+    if (a.views[m].eps_method == 1) eps_raster_particle<LAT::DIM, TE, true>(a.views[m], i - a.part_off[m], a.cap, smem);
+    else eps_raster_particle<LAT::DIM, TE, false>(a.views[m], i - a.part_off[m], a.cap, smem);
   }
   for (int i = gtid; i < P; i += nthreads) {
     const int m = member_of(a.part_off, a.nm, i);

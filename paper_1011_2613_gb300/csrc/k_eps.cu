@@ -29,10 +29,61 @@ __global__ void __launch_bounds__(128) eps_clear_kernel(View v, bool zero_forces
   if (p < v.np) eps_clear_particle(v, p, threadIdx.x & 31, zero_forces);
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool TABLE>
 __global__ void __launch_bounds__(128) eps_raster_kernel(View v, RasterSmem cap) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (blockIdx.x < v.np) eps_raster_particle<DIM, T>(v, blockIdx.x, cap, smem);
+  if (blockIdx.x < v.np) eps_raster_particle<DIM, T, TABLE>(v, blockIdx.x, cap, smem);
+}
+
+// Eq. 6 table: one thread per grid point (see dev_eps.cuh for the grid)
+template <int DIM>
+__global__ void eps_table_build_kernel(double R, float* tab) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  double off[3] = {0.0, 0.0, 0.0};
+  if (DIM == 2) {
+    if (id >= kTabR2 * kTabT2) return;
+    const int i = id / kTabT2, j = id % kTabT2;
+    const double r = (R - 0.70710678118654752440) + i * (1.41421356237309504880 / (kTabR2 - 1));
+    const double t = j * (1.0 / (kTabT2 - 1));
+    off[0] = r / sqrt(1.0 + t * t);
+    off[1] = off[0] * t;
+  } else {
+    if (id >= kTabR3 * kTabS3 * kTabT3) return;
+    const int i = id / (kTabS3 * kTabT3), j = (id / kTabT3) % kTabS3, k = id % kTabT3;
+    const double r = (R - 0.86602540378443864676) + i * (1.73205080756887729353 / (kTabR3 - 1));
+    const double sv = j * (1.41421356237309504880 / (kTabS3 - 1));
+    const double t = k * (1.0 / (kTabT3 - 1));
+    off[0] = r / sqrt(1.0 + sv * sv);
+    off[1] = off[0] * sv / sqrt(1.0 + t * t);
+    off[2] = off[1] * t;
+  }
+  tab[id] = (float)exact_cell_fraction(DIM, R, off);
+}
+
+long long eps_table_entries(int dim) {
+  return dim == 2 ? (long long)kTabR2 * kTabT2 : (long long)kTabR3 * kTabS3 * kTabT3;
+}
+
+void eps_table_geometry(int dim, double R, float* lo_r, float* h_r, float* h_s, float* h_t) {
+  if (dim == 2) {
+    *lo_r = (float)(R - sqrt(2.0) / 2.0);
+    *h_r = (float)(sqrt(2.0) / (kTabR2 - 1));
+    *h_s = 0.f;
+    *h_t = (float)(1.0 / (kTabT2 - 1));
+  } else {
+    *lo_r = (float)(R - sqrt(3.0) / 2.0);
+    *h_r = (float)(sqrt(3.0) / (kTabR3 - 1));
+    *h_s = (float)(sqrt(2.0) / (kTabS3 - 1));
+    *h_t = (float)(1.0 / (kTabT3 - 1));
+  }
+}
+
+cudaError_t launch_eps_table_build(int dim, double R, float* tab, cudaStream_t s) {
+  const long long n = eps_table_entries(dim);
+  const int grid = (int)((n + 255) / 256);
+  if (dim == 2) eps_table_build_kernel<2><<<grid, 256, 0, s>>>(R, tab);
+  else eps_table_build_kernel<3><<<grid, 256, 0, s>>>(R, tab);
+  return cudaGetLastError();
 }
 
 int eps_raster_smem_bytes(int dim, int storage, double rmax) {
@@ -47,30 +98,35 @@ void launch_eps_clear(const View& v, bool zero_forces, cudaStream_t s) {
   eps_clear_kernel<<<(v.np + 3) / 4, 128, 0, s>>>(v, zero_forces);
 }
 
+template <int DIM, typename T>
+static void raster_t(const View& v, const RasterSmem cap, int smem_bytes, cudaStream_t s) {
+  if (v.eps_method == 1) eps_raster_kernel<DIM, T, true><<<v.np, 128, 0, s>>>(v, cap);  // no tables
+  else eps_raster_kernel<DIM, T, false><<<v.np, 128, smem_bytes, s>>>(v, cap);
+}
+
 void launch_eps_raster(const View& v, int smem_bytes, cudaStream_t s) {
   if (v.np <= 0) return;
   const RasterSmem cap = raster_caps(v.dim, v.rmax_bins);
   if (v.dim == 2) {
-    if (v.storage == LBM_IMB_STORE_F64)
-      eps_raster_kernel<2, double><<<v.np, 128, smem_bytes, s>>>(v, cap);
-    else
-      eps_raster_kernel<2, float><<<v.np, 128, smem_bytes, s>>>(v, cap);
+    if (v.storage == LBM_IMB_STORE_F64) raster_t<2, double>(v, cap, smem_bytes, s);
+    else raster_t<2, float>(v, cap, smem_bytes, s);
   } else {
-    if (v.storage == LBM_IMB_STORE_F64)
-      eps_raster_kernel<3, double><<<v.np, 128, smem_bytes, s>>>(v, cap);
-    else
-      eps_raster_kernel<3, float><<<v.np, 128, smem_bytes, s>>>(v, cap);
+    if (v.storage == LBM_IMB_STORE_F64) raster_t<3, double>(v, cap, smem_bytes, s);
+    else raster_t<3, float>(v, cap, smem_bytes, s);
   }
 }
 
 // opt in to large dynamic shared memory (called at handle creation)
-int eps_raster_set_attrs(int bytes) {
-  cudaError_t e1 = cudaFuncSetAttribute(eps_raster_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaError_t e2 = cudaFuncSetAttribute(eps_raster_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaError_t e3 = cudaFuncSetAttribute(eps_raster_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaError_t e4 = cudaFuncSetAttribute(eps_raster_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) ? 0 : -1;
+template <bool TABLE>
+static bool set_attrs_t(int bytes) {
+  const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  return cudaFuncSetAttribute(eps_raster_kernel<2, double, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(eps_raster_kernel<2, float, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(eps_raster_kernel<3, double, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(eps_raster_kernel<3, float, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess;
 }
+
+int eps_raster_set_attrs(int bytes) { return (set_attrs_t<false>(bytes) && set_attrs_t<true>(bytes)) ? 0 : -1; }
 
 __global__ void atan2_probe_kernel(const double* y, const double* x, double* fast, double* ref, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;

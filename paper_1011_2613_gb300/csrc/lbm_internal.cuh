@@ -93,7 +93,11 @@ struct View {
   float tau_f, omega_f, rho0_f, omc_f;
   float fq_f[19], cg3_f[19];
   int substeps;
-  int collide_variant;  // kernel form of the collision (0, 1, 2)
+  int collide_variant;  // kernel form of the collision
+  // covered fractions: 0 exact closed forms, 1 the Eq. 6 table (one radius)
+  int eps_method;
+  const float* eps_tab;  // table of exact fractions (see dev_eps.cuh)
+  float tab_lo_r, tab_h_r, tab_h_s, tab_h_t;
   // device error word
   int* err;
   // scratch for reductions (totals)
@@ -109,6 +113,9 @@ void launch_init_equilibrium(const View& v, void* f, cudaStream_t s);
 void launch_eps_clear(const View& v, bool zero_forces, cudaStream_t s);
 void launch_eps_raster(const View& v, int smem_bytes, cudaStream_t s);
 int eps_raster_smem_bytes(int dim, int storage, double rmax);
+long long eps_table_entries(int dim);
+void eps_table_geometry(int dim, double R, float* lo_r, float* h_r, float* h_s, float* h_t);
+cudaError_t launch_eps_table_build(int dim, double R, float* tab, cudaStream_t s);
 int eps_raster_set_attrs(int bytes);
 void launch_collide(const View& v, cudaStream_t s);
 void launch_dem(const View& v, cudaStream_t s);

@@ -49,6 +49,7 @@ class SuspensionConfig:
     density: np.ndarray  # (np,) solid density in lattice units
     storage: str = "f64"
     name: str = ""
+    eps_method: int = 0  # 0 exact covered fractions, 1 the table lookup of Eq. 6
 
     @property
     def n_nodes(self) -> int:

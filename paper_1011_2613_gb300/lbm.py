@@ -43,7 +43,7 @@ class Config(C.Structure):
         ("nz", C.c_int32), ("wall_y", C.c_int32), ("storage", C.c_int32), ("tau", C.c_double),
         ("body_force", C.c_double * 3), ("gravity", C.c_double * 3), ("rho_fluid", C.c_double),
         ("k_n", C.c_double), ("restitution", C.c_double), ("dem_substeps", C.c_int32),
-        ("reserved0", C.c_int32), ("n_particles", C.c_int64), ("pos", _dp), ("vel", _dp),
+        ("eps_method", C.c_int32), ("n_particles", C.c_int64), ("pos", _dp), ("vel", _dp),
         ("omega", _dp), ("radius", _dp), ("density", _dp),
     ]
 
@@ -162,6 +162,7 @@ def make_config(cfg) -> tuple[Config, list]:
     c.k_n = float(cfg.k_n)
     c.restitution = float(cfg.restitution)
     c.dem_substeps = int(cfg.dem_substeps)
+    c.eps_method = int(getattr(cfg, "eps_method", 0))
     c.n_particles = np_
     if np_:
         c.pos = ptr(cfg.pos)
@@ -198,7 +199,9 @@ class Simulation:
         self.device = torch.device(device if device is not None else "cuda")
         c, keep = make_config(cfg)
         nbytes = int(L.lbm_imb_required_bytes(C.byref(c)))
-        if nbytes == 0:
+        if nbytes == 0:  # the configuration is rejected: report why
+            h0 = C.c_void_p()
+            _check(L.lbm_imb_init(C.byref(c), None, 0, None, C.byref(h0)), "lbm_imb_init")
             raise LbmImbError(EINVAL, "lbm_imb_required_bytes")
         self.nbytes = nbytes
         with torch.cuda.device(self.device):
