@@ -365,6 +365,19 @@ def measure_closure(args, torch, n=96, snapshots=6):
                         f"1000 steps, every 100 steps x {snapshots}; seeds 1-8 train, 9-10 test"}
 
 
+def measure_validation():
+    """Fixed sphere in a simple cubic array (phi ~ 0.008, Re_p ~ 0.1, FP64,
+    exact covered fractions): steady drag factor against Hasimoto's result
+    for sphere radii 3 to 8 lattice units."""
+    from paper_1011_2613_gb300 import validation as V
+    t0 = time.perf_counter()
+    rows = [V.fixed_sphere_drag(R) for R in (3.0, 4.5, 6.0, 8.0)]
+    keep = ("R", "L", "phi", "steps", "K", "K_hasimoto", "rel_error", "re_p", "force_balance")
+    return {"rows": [{k: r[k] for k in keep} for r in rows], "seconds": time.perf_counter() - t0,
+            "workload": "one fixed sphere per periodic cube (simple cubic array), body force on the gas, "
+                        "tau 1, run from rest for 10 drag relaxation times"}
+
+
 def compare_to(ref, sim, torch):
     """Velocity-field L2, particle trajectory and mass drift vs FP64."""
     u64 = torch.empty(ref.dim * ref.N, dtype=torch.float64, device=ref.device)
@@ -474,6 +487,12 @@ def run_ours(args):
             variants["closure_d3q19"] = measure_closure(args, torch)
         except Exception as ex:
             variants["closure_d3q19"] = {"error": str(ex)}
+
+    if not args.no_variants and rank == 0 and cfg.storage == "f64":
+        try:
+            variants["validation_fixed_sphere"] = measure_validation()
+        except Exception as ex:
+            variants["validation_fixed_sphere"] = {"error": str(ex)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -317,3 +317,23 @@ def closure_config(phi: float, seed: int, n: int = 128, radius: float = 3.75, de
     vel = v0 * random_directions(rng, k, 3)
     return _finish(3, n, n, n, 0, tau, (0.0, -gs, 0.0), 1.0, e, radii, np.full(k, density_ratio), pos, vel,
                    f"closure D3Q19 {n}^3 periodic, phi={phi}, {k} spheres, seed {seed}", storage=storage)
+
+
+def fixed_sphere_config(R: float, phi: float, tau: float = 1.0, re_p: float = 0.2, storage: str = "f64",
+                        offset=(0.1, 0.2, 0.3)) -> SuspensionConfig:
+    """Gravity-driven flow through a simple cubic array of fixed spheres: one
+    sphere of radius R in a periodic cube of side L = round(R (4 pi/(3 phi))^(1/3)),
+    held in place by a solid/gas density ratio of 1e12 and no gravity of its
+    own; the gas is driven by a body force along x sized for the particle
+    Reynolds number re_p (Stokes estimate).  The centre sits near the cube
+    centre, shifted by ``offset`` so that it is not node-aligned."""
+    L = int(round(R * (4.0 * math.pi / (3.0 * phi)) ** (1.0 / 3.0)))
+    nu = (tau - 0.5) / 3.0
+    u_target = re_p * nu / (2.0 * R)
+    g = 6.0 * math.pi * nu * R * u_target / L ** 3  # Stokes drag of one sphere per cube volume
+    pos = np.array([[L / 2 + offset[0], L / 2 + offset[1], L / 2 + offset[2]]])
+    return SuspensionConfig(
+        dim=3, nx=L, ny=L, nz=L, wall_y=0, tau=tau, body_force=np.array([g, 0.0, 0.0]), gravity=np.zeros(3),
+        rho_fluid=1.0, k_n=0.0, restitution=1.0, dem_substeps=1, pos=pos, vel=np.zeros((1, 3)),
+        omega=np.zeros((1, 3)), radius=np.array([float(R)]), density=np.array([1e12]), storage=storage,
+        name=f"fixed sphere R={R} in a periodic {L}^3 cube, phi={4 / 3 * math.pi * R ** 3 / L ** 3:.4f}")
