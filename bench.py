@@ -75,9 +75,9 @@ WORKLOADS = {
 FP64_OPS = {3: (148.0, 225.0), 2: (68.0, 151.0)}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node of
 # one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
-# case at the config-3 solid fraction (forms 5 / 6 / 6); a config-3 launch
+# case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
 # moves this many bytes per node times its node count (same solid fraction).
-TRAFFIC_B_PER_NODE = {("f64", 3): 376.3, ("f32dev", 3): 186.6, ("f16dev", 3): 104.8}
+TRAFFIC_B_PER_NODE = {("f64", 3): 376.3, ("f32dev", 3): 189.6, ("f16dev", 3): 116.4}
 
 # FP64 pipe peak: the nominal 1.25 TFLOP/s of the GB300 FP64 units, i.e.
 # 625 G FP64-pipe operations per second (a DFMA counts two flops, one slot)

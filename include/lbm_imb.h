@@ -174,8 +174,11 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
  *   before the current one is collided, 5 the same with a budget for 3
  *   CTAs per SM, 6 one CTA per row tile that packs its covered nodes into
  *   full warps through shared memory (register budget for 8 CTAs per SM),
- *   7 the same with a budget for 5 CTAs per SM.
- * Returns EINVAL outside 0..7.  Not for batch members or batches. */
+ *   7 the same with a budget for 5 CTAs per SM, 8 two adjacent nodes per
+ *   thread with paired FP32 arithmetic and aligned pair loads/stores
+ *   (reduced-precision storages only; FP64 falls back to 0; 6 CTAs per SM),
+ *   9 the same with 4 CTAs per SM.
+ * Returns EINVAL outside 0..9.  Not for batch members or batches. */
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
 
 /* Wait for the handle's stream and report device-side errors. */

@@ -99,7 +99,7 @@ def tuned_batch(cfgs, device=None, path: str | None = None, steps: int = 3):
     return batch, rec, False
 
 
-COLLIDE_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7)
+COLLIDE_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9)
 
 
 def collide_signature(cfg, device_name: str) -> str:

@@ -958,7 +958,7 @@ int lbm_imb_drag_samples(lbm_imb_t* h, const double* u_dev, const double* eps_de
 }
 
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant) {
-  if (!h || h->is_member || variant < 0 || variant > 7) return LBM_IMB_EINVAL;
+  if (!h || h->is_member || variant < 0 || variant > 9) return LBM_IMB_EINVAL;
   if (h->is_batch) return LBM_IMB_EUNSUPPORTED;
   if (h->graphs_ok) {
     cudaGraphExecDestroy(h->graph[0]);

@@ -108,6 +108,39 @@ __device__ __forceinline__ void warp_reduce_to_particles(int key, PT (&val)[6], 
   }
 }
 
+// Two FP32 values processed together by the paired instructions of this
+// GPU (FADD2 / FMUL2 / FFMA2): the arithmetic type of the two-node forms.
+struct F2 {
+  float2 v;
+  __device__ __forceinline__ F2() {}
+  __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ F2(double s) : v(make_float2((float)s, (float)s)) {}
+  __device__ __forceinline__ F2(int s) : v(make_float2((float)s, (float)s)) {}
+  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+  // found by argument-dependent lookup only (does not hide ::fma)
+  friend __device__ __forceinline__ F2 fma(const F2 a, const F2 b, const F2 c) {
+    F2 r;
+    r.v = __ffma2_rn(a.v, b.v, c.v);
+    return r;
+  }
+};
+__device__ __forceinline__ F2 operator+(const F2 a, const F2 b) {
+  F2 r;
+  r.v = __fadd2_rn(a.v, b.v);
+  return r;
+}
+__device__ __forceinline__ F2 operator*(const F2 a, const F2 b) {
+  F2 r;
+  r.v = __fmul2_rn(a.v, b.v);
+  return r;
+}
+__device__ __forceinline__ F2 operator-(const F2 a) { return a * F2(-1.f); }  // exact
+__device__ __forceinline__ F2 operator-(const F2 a, const F2 b) { return fma(b, F2(-1.f), a); }  // one rounding
+
+__device__ __forceinline__ float rcp(const float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(const double x) { return 1.0 / x; }
+__device__ __forceinline__ F2 rcp(const F2 x) { return F2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
+
 // c . u built from the non-zero components only (after unrolling the
 // direction loop the branches fold, and no 0*u term survives)
 template <typename T>
@@ -222,20 +255,15 @@ struct Moments {
   T drho, rho, ux, uy, uz, k;
 };
 
-template <class LAT, int STORE>
-__device__ __forceinline__ typename Storage<STORE>::T k_of(const typename Storage<STORE>::T ux,
-                                                           const typename Storage<STORE>::T uy,
-                                                           const typename Storage<STORE>::T uz) {
-  using T = typename Storage<STORE>::T;
+template <class LAT, int STORE, class T = typename Storage<STORE>::T>
+__device__ __forceinline__ T k_of(const T ux, const T uy, const T uz) {
   const T usq = LAT::DIM == 3 ? fma(ux, ux, fma(uy, uy, uz * uz)) : fma(ux, ux, uy * uy);
   return Storage<STORE>::DEV ? usq * T(-1.0 / 3.0) : fma(usq, T(-1.0 / 3.0), T(1));
 }
 
-template <class LAT, int STORE>
-__device__ __forceinline__ Moments<typename Storage<STORE>::T> moments(
-    const View& v, const typename Storage<STORE>::T (&f)[LAT::Q]) {
+template <class LAT, int STORE, class T = typename Storage<STORE>::T>
+__device__ __forceinline__ Moments<T> moments(const View& v, const T (&f)[LAT::Q]) {
   using S = Storage<STORE>;
-  using T = typename S::T;
   constexpr int NP = (LAT::Q - 1) / 2;
   constexpr bool D3 = LAT::DIM == 3;
   T s0 = S::SCALED ? T(LAT::w(0)) * f[0] : f[0];
@@ -254,14 +282,11 @@ __device__ __forceinline__ Moments<typename Storage<STORE>::T> moments(
   Moments<T> r;
   r.drho = S::DEV ? s0 : T(0);
   r.rho = S::DEV ? T(v.rho0_f) + s0 : s0;
-  T irho;
-  if constexpr (sizeof(T) == 4) irho = __frcp_rn(r.rho);
-  else irho = T(1) / r.rho;
-  const T is = T(kSqrt45) * irho;
+  const T is = T(kSqrt45) * rcp(r.rho);
   r.ux = jx * is;
   r.uy = jy * is;
   r.uz = D3 ? jz * is : T(0);
-  r.k = k_of<LAT, STORE>(r.ux, r.uy, r.uz);
+  r.k = k_of<LAT, STORE, T>(r.ux, r.uy, r.uz);
   return r;
 }
 
@@ -270,12 +295,9 @@ __device__ __forceinline__ Moments<typename Storage<STORE>::T> moments(
 //   A = omega W (k + (c.u_s)^2)            (+ omega w drho in deviation form)
 //   B = W (sqrt(2) omega c.u_s + 3 c.g_f),  W = w rho
 // (w = 1 in the scaled form).  The weight products fold per weight class.
-template <class LAT, int STORE>
-__device__ __forceinline__ void bgk(const View& v, const Moments<typename Storage<STORE>::T>& m,
-                                    const typename Storage<STORE>::T (&f)[LAT::Q],
-                                    typename Storage<STORE>::T (&out)[LAT::Q]) {
+template <class LAT, int STORE, class T = typename Storage<STORE>::T>
+__device__ __forceinline__ void bgk(const View& v, const Moments<T>& m, const T (&f)[LAT::Q], T (&out)[LAT::Q]) {
   using S = Storage<STORE>;
-  using T = typename S::T;
   constexpr int NP = (LAT::Q - 1) / 2;
   const T om = S::DEV ? T(v.omega_f) : T(v.omega);
   const T omc = S::DEV ? T(v.omc_f) : T(v.omc);
@@ -731,6 +753,169 @@ __device__ __forceinline__ void packed_node(const View& v, const int xx, const i
   mm.uz = sf[(Q + 4) * CAP + s];
   mm.k = k_of<LAT, STORE>(mm.ux, mm.uy, mm.uz);
   imb_core<LAT, STORE>(v, sxy[s] & 0xffff, sxy[s] >> 16, sz[s], sn[s], mine, g, mm);
+}
+
+// ---------------------------------------------------------------------------
+// Two-node form (reduced-precision storages).  A thread takes the adjacent
+// nodes x, x+1 (x even) of a row: directions with c_x = 0 come as one
+// aligned two-element load, the others as two element loads; the moments and
+// the BGK update of both nodes run as paired FP32 arithmetic (F2); stores
+// are aligned pairs.  A CTA covers 128 nodes of two rows; its covered nodes
+// are packed into the first lanes through shared memory and get the
+// immersed-boundary update one node per thread (their plain values, stored
+// first, are overwritten after the CTA barrier).
+// smem: pair_pack_bytes<LAT, STORE>() bytes.
+// ---------------------------------------------------------------------------
+template <int STORE>
+struct PairIO;
+template <>
+struct PairIO<LBM_IMB_STORE_F32DEV> {
+  __device__ static __forceinline__ float2 load2(const float* p, int i) {
+    return __ldg(reinterpret_cast<const float2*>(p + i));
+  }
+  __device__ static __forceinline__ float load1(const float* p, int i) { return __ldg(p + i); }
+  __device__ static __forceinline__ void store2(float* p, int i, float2 v) {
+    *reinterpret_cast<float2*>(p + i) = v;
+  }
+  __device__ static __forceinline__ void store1(float* p, int i, float a) { p[i] = a; }
+};
+template <>
+struct PairIO<LBM_IMB_STORE_F16DEV> {
+  __device__ static __forceinline__ float2 load2(const __half* p, int i) {
+    return __half22float2(__ldg(reinterpret_cast<const __half2*>(p + i)));
+  }
+  __device__ static __forceinline__ float load1(const __half* p, int i) { return __half2float(__ldg(p + i)); }
+  __device__ static __forceinline__ void store2(__half* p, int i, float2 v) {
+    *reinterpret_cast<__half2*>(p + i) = __floats2half2_rn(v.x, v.y);
+  }
+  __device__ static __forceinline__ void store1(__half* p, int i, float a) { p[i] = __float2half_rn(a); }
+};
+
+template <class LAT, int STORE>
+__host__ __device__ constexpr int pair_pack_bytes() {
+  return 256 * ((LAT::Q + 5) * 4 + 3 * 4);
+}
+
+// pull of the node pair (x, x+1) of row (y, z); n = offset of node x (even)
+template <class LAT, int STORE>
+__device__ __forceinline__ void pull_pair(const View& v, const int x, const int y, const int z, const int n,
+                                          F2 (&f)[LAT::Q]) {
+  using IO = PairIO<STORE>;
+  using Elem = typename Storage<STORE>::Elem;
+  constexpr int Q = LAT::Q;
+  const int nx = v.nx, ny = v.ny, nz = v.nz, pitch = v.pitch;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+  const int ry[3] = {y * pitch, ym * pitch, yp * pitch};
+  const int rz[3] = {z * ny * pitch, zm * ny * pitch, zp * ny * pitch};
+  // x sources of the two nodes for c_x = +1 (left) and c_x = -1 (right)
+  const int l0 = x == 0 ? nx - 1 : x - 1, l1 = x;
+  const int r0 = x + 1 < nx ? x + 1 : 0, r1 = x + 2 < nx ? x + 2 : (x + 2 == nx ? 0 : 1);
+  const bool wall_row = v.wall_y && (y == 0 || y == ny - 1);
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+    const int row = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)];
+    const bool bounce = wall_row && ((cy == 1 && y == 0) || (cy == -1 && y == ny - 1));
+    if (bounce) {  // halfway bounce-back: the opposite populations of the pair itself
+      const float2 w = IO::load2(static_cast<const Elem*>(v.src_q[opp(q)]), n);
+      f[q] = F2(w.x, w.y);
+    } else {
+      const Elem* src = static_cast<const Elem*>(v.src_q[q]);
+      if (cx == 0) {
+        const float2 w = IO::load2(src, row + x);
+        f[q] = F2(w.x, w.y);
+      } else {
+        const int s0 = cx == 1 ? l0 : r0, s1 = cx == 1 ? l1 : r1;
+        f[q] = F2(IO::load1(src, row + s0), IO::load1(src, row + s1));
+      }
+    }
+  }
+}
+
+template <class LAT, int STORE>
+__device__ __forceinline__ void pair_node(const View& v, const int x, const int y, const int z, const bool row_ok,
+                                          unsigned char* smem) {
+  using S = Storage<STORE>;
+  using IO = PairIO<STORE>;
+  using Elem = typename S::Elem;
+  constexpr int Q = LAT::Q;
+  constexpr int NP = (Q - 1) / 2;
+  constexpr int CAP = 256;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* sf = reinterpret_cast<float*>(smem);  // [Q + 5][CAP]
+  int* sn = reinterpret_cast<int*>(sf + (Q + 5) * CAP);
+  int* sxy = sn + CAP;
+  int* sz = sxy + CAP;
+  __shared__ int s_cnt[4];
+  const int nx = v.nx;
+  const bool a0 = row_ok && x < nx, a1 = row_ok && x + 1 < nx;
+  const int xc = a0 ? x : ((nx - 1) & ~1);  // a valid even node for idle lanes
+  const int n = (z * v.ny + y) * v.pitch + xc;
+  const int2 o = *reinterpret_cast<const int2*>(v.own[0] + n);
+  const bool c0 = a0 && o.x >= 0, c1 = a1 && o.y >= 0;
+  F2 f[Q];
+  pull_pair<LAT, STORE>(v, xc, y, z, n, f);
+  const Moments<F2> m = moments<LAT, STORE, F2>(v, f);
+  F2 out[Q];
+  bgk<LAT, STORE, F2>(v, m, f, out);
+  if (a1) {
+#pragma unroll
+    for (int q = 0; q < Q; q++) IO::store2(static_cast<Elem*>(v.dst_q[q]), n, out[q].v);
+  } else if (a0) {
+#pragma unroll
+    for (int q = 0; q < Q; q++) IO::store1(static_cast<Elem*>(v.dst_q[q]), n, out[q].v.x);
+  }
+  // pack the covered nodes of the CTA
+  const unsigned b0 = __ballot_sync(FULL, c0), b1 = __ballot_sync(FULL, c1);
+  if (lane == 0) s_cnt[warp] = __popc(b0) + __popc(b1);
+  __syncthreads();
+  int base = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < 4; w++) {
+    base += w < warp ? s_cnt[w] : 0;
+    total += s_cnt[w];
+  }
+  if (total == 0) return;
+  const unsigned lt = (1u << lane) - 1u;
+  int pos = base + __popc(b0 & lt) + __popc(b1 & lt);
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const bool ch = h == 0 ? c0 : c1;
+    if (ch) {
+#pragma unroll
+      for (int q = 0; q < Q; q++) sf[q * CAP + pos] = h == 0 ? f[q].v.x : f[q].v.y;
+      sf[Q * CAP + pos] = h == 0 ? m.rho.v.x : m.rho.v.y;
+      sf[(Q + 1) * CAP + pos] = h == 0 ? m.drho.v.x : m.drho.v.y;
+      sf[(Q + 2) * CAP + pos] = h == 0 ? m.ux.v.x : m.ux.v.y;
+      sf[(Q + 3) * CAP + pos] = h == 0 ? m.uy.v.x : m.uy.v.y;
+      sf[(Q + 4) * CAP + pos] = h == 0 ? m.uz.v.x : m.uz.v.y;
+      sn[pos] = n + h;
+      sxy[pos] = (xc + h) | (y << 16);  // x, y < 65536
+      sz[pos] = z;
+      pos++;
+    }
+  }
+  __syncthreads();
+  for (int b = 0; b < total; b += 128) {
+    if (b + warp * 32 >= total) break;  // whole warps beyond the packed nodes
+    const int i = b + (int)threadIdx.x;
+    const bool mine = i < total;
+    const int s = mine ? i : b;
+    float g[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) g[q] = sf[q * CAP + s];
+    Moments<float> mm;
+    mm.rho = sf[Q * CAP + s];
+    mm.drho = sf[(Q + 1) * CAP + s];
+    mm.ux = sf[(Q + 2) * CAP + s];
+    mm.uy = sf[(Q + 3) * CAP + s];
+    mm.uz = sf[(Q + 4) * CAP + s];
+    mm.k = k_of<LAT, STORE, float>(mm.ux, mm.uy, mm.uz);
+    imb_core<LAT, STORE>(v, sxy[s] & 0xffff, sxy[s] >> 16, sz[s], sn[s], mine, g, mm);
+  }
+  (void)NP;
 }
 
 // drain a warp's queue (at the end of its segments)

@@ -73,6 +73,20 @@ __global__ void __launch_bounds__(128, MINB) collide_packed_kernel(View v) {
   packed_node<LAT, STORE>(v, active ? x : v.nx - 1, blockIdx.y, blockIdx.z, active, smem_p);
 }
 
+// Two-node form: CTA = 128 nodes (64 pairs) of two consecutive rows; grid x
+// over row pairs, grid y over 128-node x tiles (reduced-precision storages).
+template <class LAT, int STORE, int MINB>
+__global__ void __launch_bounds__(128, MINB) collide_pair_kernel(View v) {
+  extern __shared__ __align__(16) unsigned char smem_pp[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = v.ny * v.nz;
+  const int r = blockIdx.x * 2 + (warp >> 1);
+  const bool row_ok = r < rows;
+  const int rr = row_ok ? r : rows - 1;
+  const int x = blockIdx.y * 128 + ((warp & 1) * 32 + lane) * 2;
+  pair_node<LAT, STORE>(v, x, rr % v.ny, rr / v.ny, row_ok, smem_pp);
+}
+
 // Software-pipelined persistent form: the populations (and owner word) of
 // the CTA's next tile are pulled into registers before the current tile is
 // collided, so every warp keeps one tile of loads in flight while it
@@ -354,6 +368,23 @@ static void launch_packed(const View& v, cudaStream_t s) {
   collide_packed_kernel<LAT, STORE, MINB><<<dim3((v.nx + 127) / 128, v.ny, v.nz), 128, smem, s>>>(v);
 }
 
+template <class LAT, int STORE, int MINB>
+static void launch_pair(const View& v, cudaStream_t s) {
+  if constexpr (STORE == LBM_IMB_STORE_F64) {
+    launch_fused<LAT, STORE, 4, false>(v, s);  // two-node form: reduced-precision storages only
+  } else {
+    const int smem = pair_pack_bytes<LAT, STORE>();
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(collide_pair_kernel<LAT, STORE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+      attr = true;
+    }
+    const dim3 grid((v.ny * v.nz + 1) / 2, (v.nx + 127) / 128);
+    collide_pair_kernel<LAT, STORE, MINB><<<grid, 128, smem, s>>>(v);
+  }
+}
+
 // collide variants (chosen per simulation, see lbm_imb_set_collide_variant):
 //   0  persistent fused form, register budget for 4 CTAs per SM
 //   1  same, register budget for 8 CTAs per SM
@@ -363,6 +394,9 @@ static void launch_packed(const View& v, cudaStream_t s) {
 //   5  the same, 3 CTAs per SM
 //   6  CTA-packed form, one CTA per row tile, register budget for 8 CTAs/SM
 //   7  the same, 5 CTAs per SM
+//   8  two-node form (paired FP32 arithmetic), 6 CTAs per SM (reduced-
+//      precision storages; FP64 uses 0)
+//   9  the same, 4 CTAs per SM
 template <class LAT, int STORE>
 static void dispatch(const View& v, cudaStream_t s) {
   switch (v.collide_variant) {
@@ -376,6 +410,8 @@ static void dispatch(const View& v, cudaStream_t s) {
     case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
     case 6: launch_packed<LAT, STORE, 8>(v, s); break;
     case 7: launch_packed<LAT, STORE, 5>(v, s); break;
+    case 8: launch_pair<LAT, STORE, 6>(v, s); break;
+    case 9: launch_pair<LAT, STORE, 4>(v, s); break;
     default: launch_fused<LAT, STORE, 4, false>(v, s);
   }
 }
