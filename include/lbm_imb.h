@@ -115,6 +115,13 @@ typedef struct lbm_imb_config {
   const double* omega;     /* host, [n][3], copied at init */
   const double* radius;    /* host, [n], copied at init; > 0 */
   const double* density;   /* host, [n], solid density in lattice units */
+  double dem_skin;         /* 0: DEM contacts from a cell list rebuilt every
+                            * (sub)step; > 0: from Verlet neighbour lists of the
+                            * pairs closer than R_i + R_j + dem_skin, rebuilt on
+                            * the device when a particle has moved more than
+                            * dem_skin/2 since the last build (the same contact
+                            * forces, summed in the same order); not for batch
+                            * members (LBM_IMB_EUNSUPPORTED) */
 } lbm_imb_config;
 
 typedef struct lbm_imb lbm_imb_t; /* opaque, library-owned host state */
@@ -157,6 +164,9 @@ enum {
  * family over the n steps, *total_ms the device time from the first launch
  * to the end of the last step.  Same results as lbm_imb_step. */
 int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* total_ms);
+
+/* Number of Verlet-list builds so far (0 with dem_skin = 0); synchronises. */
+int lbm_imb_dem_rebuilds(lbm_imb_t* h, int64_t* builds);
 
 /* Number of kernel launches one time step issues (for launch accounting). */
 int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
@@ -240,7 +250,9 @@ size_t lbm_imb_batch_required_bytes(const lbm_imb_config* cfgs, int n);
  * tile_x: 32, 64 or 128 (0 = 128); blocks_per_sm: CTAs per SM of the
  * persistent grid (0 = as many as fit).  The batch handle steps with
  * lbm_imb_step / lbm_imb_step_profiled (whose time goes to the
- * LBM_IMB_K_COLLIDE slot) and is released with lbm_imb_destroy. */
+ * LBM_IMB_K_COLLIDE slot) and is released with lbm_imb_destroy.  Members
+ * need dem_substeps = 1 and dem_skin = 0 (LBM_IMB_EUNSUPPORTED otherwise);
+ * a rejected config set returns its status before the buffer is looked at. */
 int lbm_imb_batch_init(const lbm_imb_config* cfgs, int n, int tile_x, int blocks_per_sm,
                        void* dev_buf, size_t bytes, void* cuda_stream, lbm_imb_t** out);
 

@@ -41,6 +41,7 @@ struct Layout {
   size_t off_pos, off_vel, off_omg, off_rad, off_mass, off_inertia, off_ff, off_tf, off_fc;
   size_t off_lo, off_kin, off_binof, off_bincount, off_binslot, off_err, off_red, off_stage;
   size_t off_tab;  // Eq. 6 table (eps_method 1), 0 bytes otherwise
+  size_t off_vl_nbr, off_vl_count, off_vl_ref, off_vl_flag;  // Verlet lists (dem_skin > 0)
   size_t stage_bytes;
   size_t total;
 };
@@ -58,6 +59,7 @@ int validate(const lbm_imb_config* c) {
   if (c->n_particles < 0 || c->n_particles > (1ll << 30)) return LBM_IMB_EINVAL;
   if (c->dem_substeps < 1) return LBM_IMB_EINVAL;
   if (c->eps_method != 0 && c->eps_method != 1) return LBM_IMB_EINVAL;
+  if (!(c->dem_skin >= 0.0) || !isfinite(c->dem_skin)) return LBM_IMB_EINVAL;
   if (c->n_particles > 0) {
     if (!c->pos || !c->radius || !c->density) return LBM_IMB_EINVAL;
     if (!(c->k_n >= 0.0) || !(c->restitution > 0.0 && c->restitution <= 1.0)) return LBM_IMB_EINVAL;
@@ -84,7 +86,8 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   for (int64_t p = 0; p < c->n_particles; p++) rmax = c->radius[p] > rmax ? c->radius[p] : rmax;
   L->rmax = rmax;
   const int ext[3] = {c->nx, c->ny, nz};
-  st = lbm::dem_bin_geometry(c->dim, ext, c->wall_y, rmax, L->nb, L->bsz);
+  // Verlet lists need every pair within R_i + R_j + skin in neighbouring bins
+  st = lbm::dem_bin_geometry(c->dim, ext, c->wall_y, rmax + 0.5 * c->dem_skin, L->nb, L->bsz);
   if (st) return st;
   L->rmax = rmax;
   L->smem = 0;
@@ -126,6 +129,11 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->off_err = take(16);
   L->off_red = take(8 * 8);
   L->off_tab = take(c->eps_method == 1 && c->n_particles > 0 ? (size_t)lbm::eps_table_entries(c->dim) * 4 : 0);
+  const bool vl = c->dem_skin > 0.0 && c->n_particles > 0;
+  L->off_vl_nbr = take(vl ? np * lbm::kVerletCap * 4 : 0);
+  L->off_vl_count = take(vl ? np * 4 : 0);
+  L->off_vl_ref = take(vl ? np * 24 : 0);
+  L->off_vl_flag = take(16);
   const size_t dense_row = (size_t)c->nx * 8 * (L->Q > 5 ? L->Q : 5);
   const size_t full = dense_row * (size_t)c->ny * nz;
   L->stage_bytes = full < kStageMax ? full : kStageMax;
@@ -326,6 +334,12 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   v.err = reinterpret_cast<int*>(base + L.off_err);
   v.red = reinterpret_cast<double*>(base + L.off_red);
   v.eps_method = np > 0 ? c->eps_method : 0;
+  v.dem_skin = np > 0 ? c->dem_skin : 0.0;
+  v.vl_nbr = reinterpret_cast<int*>(base + L.off_vl_nbr);
+  v.vl_count = reinterpret_cast<int*>(base + L.off_vl_count);
+  v.vl_ref = reinterpret_cast<double*>(base + L.off_vl_ref);
+  v.vl_flag = reinterpret_cast<int*>(base + L.off_vl_flag);
+  v.vl_builds = reinterpret_cast<long long*>(base + L.off_vl_flag + 8);
   v.eps_tab = reinterpret_cast<const float*>(base + L.off_tab);
   v.tab_lo_r = v.tab_h_r = v.tab_h_s = v.tab_h_t = 0.f;
   if (v.eps_method == 1)
@@ -391,6 +405,10 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
       e = cudaMemsetAsync(v.own[s], 0xff, (size_t)L.plane * 4, h->stream);
     if (e == cudaSuccess && v.eps_method == 1)
       e = lbm::launch_eps_table_build(c->dim, c->radius[0], const_cast<float*>(v.eps_tab), h->stream);
+    if (e == cudaSuccess) {  // Verlet: first pass builds; no builds yet
+      const long long flag_builds[2] = {1, 0};
+      e = cudaMemcpyAsync(v.vl_flag, flag_builds, 16, cudaMemcpyHostToDevice, h->stream);
+    }
     if (e == cudaSuccess) {
       View v0 = view_of(h, 0);
       lbm::launch_init_equilibrium(v0, h->f[0], h->stream);
@@ -444,6 +462,7 @@ static int batch_layout(const lbm_imb_config* cfgs, int n, BatchLayout* B) {
     if (st) return st;
     if (c->dim != cfgs[0].dim || c->storage != cfgs[0].storage) return LBM_IMB_EINVAL;
     if (c->dem_substeps != 1) return LBM_IMB_EUNSUPPORTED;
+    if (c->dem_skin != 0.0) return LBM_IMB_EUNSUPPORTED;
     B->member_off[i] = take(B->member[i].total);
   }
   B->total = o;
@@ -576,10 +595,11 @@ size_t lbm_imb_batch_required_bytes(const lbm_imb_config* cfgs, int n) {
 
 int lbm_imb_batch_init(const lbm_imb_config* cfgs, int n, int tile_x, int blocks_per_sm, void* dev_buf,
                        size_t bytes, void* cuda_stream, lbm_imb_t** out) {
-  if (!out || !dev_buf || ((uintptr_t)dev_buf) % kAlign) return LBM_IMB_EINVAL;
+  if (!out) return LBM_IMB_EINVAL;
   BatchLayout* B = (BatchLayout*)malloc(sizeof(BatchLayout));
   if (!B) return LBM_IMB_ENOMEM;
-  int st = batch_layout(cfgs, n, B);
+  int st = batch_layout(cfgs, n, B);  // the configurations' own status first
+  if (!st && (!dev_buf || ((uintptr_t)dev_buf) % kAlign)) st = LBM_IMB_EINVAL;
   if (!st && bytes < B->total) st = LBM_IMB_ENOMEM;
   lbm_imb* h = nullptr;
   if (!st) {
@@ -805,7 +825,17 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches) {
     *launches = 1;
     return LBM_IMB_OK;
   }
-  *launches = h->np > 0 ? 3 + 4 * h->v.substeps : 1;
+  *launches = h->np > 0 ? 3 + (h->v.dem_skin > 0.0 ? 6 : 4) * h->v.substeps : 1;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_dem_rebuilds(lbm_imb_t* h, int64_t* builds) {
+  if (!h || !builds || h->is_batch) return LBM_IMB_EINVAL;
+  long long b = 0;
+  if (cudaMemcpyAsync(&b, h->v.vl_builds, 8, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LBM_IMB_ECUDA;
+  *builds = b;
   return LBM_IMB_OK;
 }
 

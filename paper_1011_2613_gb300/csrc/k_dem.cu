@@ -1,5 +1,6 @@
 // K3: DEM particle update (Xiong et al., Eqs. 4-5: frictionless linear
-// spring-dashpot contacts) with a per-step cell list, and the symplectic
+// spring-dashpot contacts) with a per-step cell list (or Verlet lists
+// rebuilt on demand, dem_skin > 0), and the symplectic
 // Euler integration of the particles under the hydrodynamic force/torque of
 // Eq. (3), the contact force and gravity.
 //
@@ -29,13 +30,55 @@ __global__ void dem_contact_kernel(View v) {
 
 __global__ void dem_integrate_kernel(View v, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < v.np) dem_integrate_particle(v, i, dt);
+  if (i >= v.np) return;
+  dem_integrate_particle(v, i, dt);
+  if (v.dem_skin > 0.0) dem_verlet_check_particle(v, i);
+}
+
+// Verlet path: the bins and lists are rebuilt only while the device flag is
+// set (the launches stay in the captured graph and return at once otherwise)
+__global__ void dem_vl_zero_bins_kernel(View v, int nbins) {
+  if (*(volatile int*)v.vl_flag == 0) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nbins) v.bin_count[i] = 0;
+}
+
+__global__ void dem_vl_bin_kernel(View v) {
+  if (*(volatile int*)v.vl_flag == 0) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < v.np) dem_bin_particle(v, p);
+}
+
+__global__ void dem_vl_build_kernel(View v) {
+  if (*(volatile int*)v.vl_flag == 0) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < v.np) dem_verlet_build_particle(v, p);
+}
+
+__global__ void dem_vl_done_kernel(View v) {
+  if (*v.vl_flag != 0) {
+    *v.vl_flag = 0;
+    *v.vl_builds += 1;
+  }
+}
+
+__global__ void dem_vl_contact_kernel(View v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < v.np) dem_verlet_contact_particle(v, i);
 }
 
 void launch_dem_contacts(const View& v, cudaStream_t s) {
   if (v.np <= 0) return;
   const int nbins = v.nb[0] * v.nb[1] * v.nb[2];
   const int T = 128;
+  if (v.dem_skin > 0.0) {
+    dem_vl_zero_bins_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(v, nbins);
+    dem_vl_bin_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
+    dem_vl_build_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
+    dem_vl_done_kernel<<<1, 1, 0, s>>>(v);
+    dem_vl_contact_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
+    return;
+  }
   dem_zero_bins_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(v.bin_count, nbins);
   dem_bin_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);
   dem_contact_kernel<<<(v.np + T - 1) / T, T, 0, s>>>(v);

@@ -10,6 +10,7 @@ namespace lbm {
 
 constexpr int kMaxOwners = LBM_IMB_MAX_OWNERS;
 constexpr int kBinCap = 16;  // particles per DEM cell-list bin
+constexpr int kVerletCap = 48;  // partners per Verlet list
 
 // device error word bits
 enum : int { ERR_OWNERS = 1, ERR_BIN = 2, ERR_NONFINITE = 4, ERR_TIMEOUT = 8 };
@@ -83,6 +84,15 @@ struct View {
   int* bin_count;  // [nbins]
   int* bin_slot;   // [nbins * kBinCap]
   double rmax_bins;  // largest radius the bins were sized for
+  // Verlet neighbour lists (dem_skin > 0): [np][kVerletCap] partner ids in
+  // ascending order, their counts, the positions at the last build, and
+  // flag[0] = rebuild needed, *builds = number of builds
+  double dem_skin;
+  int* vl_nbr;
+  int* vl_count;
+  double* vl_ref;
+  int* vl_flag;
+  long long* vl_builds;
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i

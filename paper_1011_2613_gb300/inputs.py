@@ -50,6 +50,7 @@ class SuspensionConfig:
     storage: str = "f64"
     name: str = ""
     eps_method: int = 0  # 0 exact covered fractions, 1 the table lookup of Eq. 6
+    dem_skin: float = 0.0  # 0 cell list every step, > 0 Verlet lists with this skin
 
     @property
     def n_nodes(self) -> int:

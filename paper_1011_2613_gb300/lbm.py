@@ -44,7 +44,7 @@ class Config(C.Structure):
         ("body_force", C.c_double * 3), ("gravity", C.c_double * 3), ("rho_fluid", C.c_double),
         ("k_n", C.c_double), ("restitution", C.c_double), ("dem_substeps", C.c_int32),
         ("eps_method", C.c_int32), ("n_particles", C.c_int64), ("pos", _dp), ("vel", _dp),
-        ("omega", _dp), ("radius", _dp), ("density", _dp),
+        ("omega", _dp), ("radius", _dp), ("density", _dp), ("dem_skin", C.c_double),
     ]
 
 
@@ -65,6 +65,8 @@ def lib():
             L.lbm_imb_step.argtypes = [C.c_void_p, C.c_int64]
             L.lbm_imb_step_profiled.restype = C.c_int
             L.lbm_imb_step_profiled.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
+            L.lbm_imb_dem_rebuilds.restype = C.c_int
+            L.lbm_imb_dem_rebuilds.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
             L.lbm_imb_launches_per_step.restype = C.c_int
             L.lbm_imb_launches_per_step.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
             L.lbm_imb_set_collide_variant.restype = C.c_int
@@ -163,6 +165,7 @@ def make_config(cfg) -> tuple[Config, list]:
     c.restitution = float(cfg.restitution)
     c.dem_substeps = int(cfg.dem_substeps)
     c.eps_method = int(getattr(cfg, "eps_method", 0))
+    c.dem_skin = float(getattr(cfg, "dem_skin", 0.0))
     c.n_particles = np_
     if np_:
         c.pos = ptr(cfg.pos)
@@ -263,6 +266,12 @@ class Simulation:
 
     def set_collide_variant(self, variant: int):
         _check(lib().lbm_imb_set_collide_variant(self.h, int(variant)), "lbm_imb_set_collide_variant")
+
+    def dem_rebuilds(self) -> int:
+        """Verlet-list builds so far (dem_skin > 0)."""
+        b = C.c_int64()
+        _check(lib().lbm_imb_dem_rebuilds(self.h, C.byref(b)), "lbm_imb_dem_rebuilds")
+        return int(b.value)
 
     def launches_per_step(self) -> int:
         x = C.c_int()
@@ -374,7 +383,9 @@ class Batch:
             arr[i] = c
             keeps.append(keep)
         nbytes = int(L.lbm_imb_batch_required_bytes(arr, n))
-        if nbytes == 0:
+        if nbytes == 0:  # a configuration is rejected: report why
+            h0 = C.c_void_p()
+            _check(L.lbm_imb_batch_init(arr, n, 0, 0, None, 0, None, C.byref(h0)), "lbm_imb_batch_init")
             raise LbmImbError(EINVAL, "lbm_imb_batch_required_bytes")
         self.nbytes = nbytes
         self.device = torch.device(device if device is not None else "cuda")
