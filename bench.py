@@ -320,7 +320,7 @@ def measure_batch(args, torch, peaks, n=32, seed=4):
                         "10-2000 disks R 4-8, density ratio log-uniform [2.5,1500]"}
 
 
-def measure_closure(args, torch, n=96, snapshots=6):
+def measure_closure(args, torch, n=128, snapshots=20):
     """Config-5 closure: drag samples from resolved D3Q19 periodic runs at
     phi 0.05-0.4 (seeds 1-10, FP32-deviation storage), network trained on
     seeds 1-8 with the library's tcgen05 kernels, evaluated on seeds 9-10
