@@ -277,6 +277,42 @@ def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=N
     return res, steps_target
 
 
+def measure_slabs(cfg, args, torch, nslabs, ref_sim, steps_target):
+    """The same workload decomposed into ``nslabs`` y slabs with a halo
+    exchange after every collision (the paper's multi-GPU subdomains, on one
+    device): throughput, halo bytes per step, and the particle state against
+    the whole-lattice FP64 run at the same step count."""
+    from paper_1011_2613_gb300 import lbm as L
+    sl = L.Slabs(cfg, nslabs)
+    sl.step(args.warmup)
+    sl.sync()
+    ms = time_graph_steps(sl, torch, args.steps)
+    done = args.warmup + args.steps
+    if steps_target > done:
+        sl.step(steps_target - done)
+    elif done > steps_target:
+        ref_sim.step(done - steps_target)
+        steps_target = done
+    sl.sync()
+    ref_sim.sync()
+    pw, ps = ref_sim.particles(), sl.particles()
+    diff = {k: float(np.max(np.abs(ps[k] - pw[k])) / max(float(np.max(np.abs(pw[k]))), 1e-300))
+            for k in ("pos", "vel", "force")}
+    q_cross = 5 if cfg.dim == 3 else 3
+    esz = {"f64": 8, "f32dev": 4, "f16dev": 2}[cfg.storage]
+    pitch = (cfg.nx + 31) // 32 * 32
+    nz = cfg.nz if cfg.dim == 3 else 1
+    bounds = nslabs - (1 if cfg.wall_y else 0)
+    halo = 2 * bounds * q_cross * nz * pitch * esz * 2  # read + write
+    sl.close()
+    del sl
+    torch.cuda.empty_cache()
+    return {"slabs": nslabs, "rows": [n for _, n in L.slab_rows(cfg.ny, nslabs)],
+            "mlups": cfg.n_nodes * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+            "halo_bytes_per_step": halo, "particles_vs_whole_rel": diff, "after_steps": steps_target,
+            "exchange": "device halo kernel, populations crossing each face only"}, steps_target
+
+
 def measure_batch(args, torch, peaks, n=32, seed=4):
     """Config-4 batch: n independent D2Q9 FP64 suspensions of uneven sizes in
     one persistent graph-replayed launch per step (launch shape from the
@@ -475,6 +511,10 @@ def run_ours(args):
                 variants[st], steps_done = measure_variant(c, args, torch, peaks, st, sim, steps_done)
             except Exception as ex:  # report, keep the headline line
                 variants[st] = {"error": str(ex)}
+        try:
+            variants["slabs4_f64"], steps_done = measure_slabs(cfg, args, torch, 4, sim, steps_done)
+        except Exception as ex:
+            variants["slabs4_f64"] = {"error": str(ex)}
 
     if not args.no_variants and rank == 0 and cfg.storage == "f64":
         try:

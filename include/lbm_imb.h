@@ -381,6 +381,28 @@ int lbm_imb_mlp_probe_gemm(const uint16_t* a_host, const uint16_t* b_host, int N
  * elements is not supported.  EINVAL on null pointers or n < 0. */
 int lbm_imb_probe_atan2q1(const double* y, const double* x, double* fast, double* ref, int64_t n, void* stream);
 
+/* One lattice decomposed along y into nslabs (2..16) slabs on this device,
+ * exchanging halo rows after every collision: the multi-GPU design of the
+ * paper (a subdomain per GPU, boundary populations passed to the
+ * neighbours; "Numerical scheme", Fig. 2) emulated in one block.
+ * Slab s computes ny_s rows (ny split as evenly as possible, the first
+ * ny % nslabs slabs one row more; ny_s >= 2), stored between two halo rows.
+ * Particles are shared by the slabs (each rasterises them into its rows and
+ * adds its Eq. 3 sums), and the DEM runs once per step.  The handle steps
+ * with lbm_imb_step and answers lbm_imb_particles / set_particles /
+ * sync / steps_done; per-slab populations and fields come from the member
+ * handles (lbm_imb_slab_member; local lattice of ny_s + 2 rows, row 0 and
+ * row ny_s + 1 the halos; a halo row is current only in the directions that
+ * cross into the slab, c_y = +1 below and c_y = -1 above).  2 <= nslabs
+ * <= 16.  The collision uses form 0 for every slab.
+ * dem_skin must be 0 (LBM_IMB_EUNSUPPORTED).  Device bytes from
+ * lbm_imb_slabs_required_bytes (0 if the config is rejected; lbm_imb_slabs_init
+ * with dev_buf = NULL then reports why). */
+size_t lbm_imb_slabs_required_bytes(const lbm_imb_config* cfg, int nslabs);
+int lbm_imb_slabs_init(const lbm_imb_config* cfg, int nslabs, void* dev_buf, size_t bytes,
+                       void* cuda_stream, lbm_imb_t** out);
+int lbm_imb_slab_member(lbm_imb_t* h, int i, lbm_imb_t** member);
+
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */
 int lbm_imb_destroy(lbm_imb_t* h);

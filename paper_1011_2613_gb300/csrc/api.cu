@@ -155,8 +155,10 @@ int map_err(int bits) {
 
 struct lbm_imb {
   View v;  // fsrc/fdst filled per use
-  // batch state (is_batch) or membership of a batch (is_member)
-  bool is_batch, is_member;
+  // batch state (is_batch), y-slab decomposition (is_slab), or membership
+  // of either (is_member)
+  bool is_batch, is_member, is_slab;
+  lbm::SlabHalo halo;  // is_slab: halo rows to exchange after every collision
   int nm;
   lbm_imb* members;
   lbm_imb* parent;
@@ -197,7 +199,26 @@ View view_of(const lbm_imb* h, int src) {
   return v;
 }
 
+// one step of a y-slab decomposition (lbm_imb_slabs_init)
+void enqueue_slab_step(lbm_imb* h, int src) {
+  for (int k = 0; k < h->nm; k++) {
+    lbm_imb* m = h->members + k;
+    lbm::launch_eps_clear(view_of(m, src), k == 0, h->stream);  // slab 0 zeroes the force sums
+  }
+  for (int k = 0; k < h->nm; k++) {
+    lbm_imb* m = h->members + k;
+    lbm::launch_eps_raster(view_of(m, src), m->smem, h->stream);
+  }
+  for (int k = 0; k < h->nm; k++) lbm::launch_collide(view_of(h->members + k, src), h->stream);
+  lbm::launch_halo_exchange(h->halo, src ^ 1, h->stream);
+  lbm::launch_dem(h->v, h->stream);
+}
+
 void enqueue_step(lbm_imb* h, int src) {
+  if (h->is_slab) {
+    enqueue_slab_step(h, src);
+    return;
+  }
   View v = view_of(h, src);
   lbm::launch_eps_clear(v, true, h->stream);
   lbm::launch_eps_raster(v, h->smem, h->stream);
@@ -257,8 +278,13 @@ long long rows_per_chunk(const lbm_imb* h, int comps) {
 }  // namespace
 
 // lay out one simulation in its device block and initialise it
+// a y slab of a decomposed lattice (see View::y0); null for a whole lattice
+struct SlabGeom {
+  int y0, ny_c, ygo, ny_glob, wall_lo, wall_hi, wall_y;
+};
+
 static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, const Layout& L,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, const SlabGeom* sg = nullptr) {
   h->stream = stream;
   unsigned char* base = static_cast<unsigned char*>(dev_buf);
   const int nz = c->dim == 3 ? c->nz : 1;
@@ -274,6 +300,20 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   v.plane = L.plane;
   v.wall_y = c->wall_y;
   v.storage = c->storage;
+  v.y0 = 0;
+  v.ny_c = c->ny;
+  v.ygo = 0;
+  v.ny_glob = c->ny;
+  v.wall_lo = v.wall_hi = c->wall_y;
+  if (sg) {
+    v.y0 = sg->y0;
+    v.ny_c = sg->ny_c;
+    v.ygo = sg->ygo;
+    v.ny_glob = sg->ny_glob;
+    v.wall_lo = sg->wall_lo;
+    v.wall_hi = sg->wall_hi;
+    v.wall_y = sg->wall_y;
+  }
   for (int s = 0; s < lbm::kMaxOwners; s++) {
     v.own[s] = reinterpret_cast<int*>(base + L.off_own[s]);
     v.eps[s] = base + L.off_eps[s];
@@ -658,6 +698,186 @@ int lbm_imb_batch_init(const lbm_imb_config* cfgs, int n, int tile_x, int blocks
   return LBM_IMB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// y slabs: one lattice decomposed along y on one device.  Slab s holds
+// ny_s computed rows (ny split as evenly as possible, the first ny % ns
+// slabs one row more) between two halo rows; after every collision a halo
+// kernel copies the boundary rows of the post-collision populations into
+// the neighbours' halos (across the ends too when y is periodic), the
+// exchange a multi-GPU run makes over NVLink.  The particles, their force
+// sums and the DEM are shared: every slab rasterises the particles into its
+// own rows and adds its Eq. 3 sums to the same FP64 accumulators; the DEM
+// runs once per step on the whole domain.
+// ---------------------------------------------------------------------------
+struct SlabLayout {
+  int ns, ny_s[16];
+  Layout L[16];
+  size_t off[16];
+  size_t off_bincount, off_binslot;
+  int nb[3];
+  double bsz[3];
+  size_t total;
+};
+
+static void slab_config(const lbm_imb_config* c, int ny_s, lbm_imb_config* out) {
+  *out = *c;
+  out->ny = ny_s + 2;
+  out->wall_y = 1;  // layout only: the slab's walls and halos come from its SlabGeom
+}
+
+static int slab_layout(const lbm_imb_config* c, int ns, SlabLayout* S) {
+  if (!c || ns < 2 || ns > 16) return LBM_IMB_EINVAL;
+  Layout G;
+  int st = make_layout(c, &G);
+  if (st) return st;
+  if (c->dem_skin != 0.0) return LBM_IMB_EUNSUPPORTED;
+  S->ns = ns;
+  const int base = c->ny / ns, rem = c->ny % ns;
+  size_t o = 0;
+  for (int k = 0; k < ns; k++) {
+    S->ny_s[k] = base + (k < rem ? 1 : 0);
+    if (S->ny_s[k] < 2) return LBM_IMB_EUNSUPPORTED;
+    lbm_imb_config cs;
+    slab_config(c, S->ny_s[k], &cs);
+    st = make_layout(&cs, &S->L[k]);
+    if (st) return st;
+    S->off[k] = o;
+    o = align_up(o + S->L[k].total);
+  }
+  for (int d = 0; d < 3; d++) {
+    S->nb[d] = G.nb[d];
+    S->bsz[d] = G.bsz[d];
+  }
+  const size_t nbins = (size_t)G.nb[0] * G.nb[1] * G.nb[2];
+  S->off_bincount = o;
+  o = align_up(o + nbins * 4);
+  S->off_binslot = o;
+  o = align_up(o + nbins * lbm::kBinCap * 4);
+  S->total = o;
+  return LBM_IMB_OK;
+}
+
+size_t lbm_imb_slabs_required_bytes(const lbm_imb_config* cfg, int nslabs) {
+  SlabLayout* S = (SlabLayout*)malloc(sizeof(SlabLayout));
+  if (!S) return 0;
+  const size_t t = slab_layout(cfg, nslabs, S) == LBM_IMB_OK ? S->total : 0;
+  free(S);
+  return t;
+}
+
+int lbm_imb_slabs_init(const lbm_imb_config* c, int nslabs, void* dev_buf, size_t bytes, void* cuda_stream,
+                       lbm_imb_t** out) {
+  if (!out) return LBM_IMB_EINVAL;
+  SlabLayout* S = (SlabLayout*)malloc(sizeof(SlabLayout));
+  if (!S) return LBM_IMB_ENOMEM;
+  int st = slab_layout(c, nslabs, S);  // the configuration's own status first
+  if (!st && (!dev_buf || ((uintptr_t)dev_buf) % kAlign)) st = LBM_IMB_EINVAL;
+  if (!st && bytes < S->total) st = LBM_IMB_ENOMEM;
+  lbm_imb* h = nullptr;
+  if (!st) {
+    h = new (std::nothrow) lbm_imb();
+    if (!h) st = LBM_IMB_ENOMEM;
+  }
+  if (!st) {
+    h->members = new (std::nothrow) lbm_imb[nslabs]();
+    if (!h->members) st = LBM_IMB_ENOMEM;
+  }
+  unsigned char* base = static_cast<unsigned char*>(dev_buf);
+  if (!st) {
+    h->is_slab = true;
+    h->nm = nslabs;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    int y_start = 0;
+    for (int k = 0; k < nslabs && !st; k++) {
+      lbm_imb* m = h->members + k;
+      lbm_imb_config cs;
+      slab_config(c, S->ny_s[k], &cs);
+      SlabGeom g;
+      g.y0 = 1;
+      g.ny_c = S->ny_s[k];
+      g.ygo = y_start - 1;
+      g.ny_glob = c->ny;
+      g.wall_lo = c->wall_y && k == 0;
+      g.wall_hi = c->wall_y && k == nslabs - 1;
+      g.wall_y = c->wall_y;
+      st = setup_handle(m, &cs, base + S->off[k], S->L[k], h->stream, &g);
+      m->is_member = true;
+      m->parent = h;
+      y_start += S->ny_s[k];
+    }
+  }
+  if (!st) {
+    // one particle state for every slab (slab 0's arrays), one error word
+    const View& p0 = h->members[0].v;
+    for (int k = 1; k < nslabs; k++) {
+      View& vk = h->members[k].v;
+      vk.pos = p0.pos; vk.vel = p0.vel; vk.omg = p0.omg; vk.rad = p0.rad;
+      vk.mass = p0.mass; vk.inertia = p0.inertia; vk.ff = p0.ff; vk.tf = p0.tf; vk.fc = p0.fc;
+      vk.lo = p0.lo; vk.kin = p0.kin; vk.bin_of = p0.bin_of; vk.err = p0.err; vk.red = p0.red;
+    }
+    // the handle's own view: the whole domain, for the DEM and the particle calls
+    View& v = h->v;
+    v = p0;
+    v.ny = c->ny;
+    v.y0 = 0;
+    v.ny_c = c->ny;
+    v.ygo = 0;
+    v.ny_glob = c->ny;
+    v.wall_y = v.wall_lo = v.wall_hi = c->wall_y;
+    for (int d = 0; d < 3; d++) {
+      v.nb[d] = S->nb[d];
+      v.bsz[d] = S->bsz[d];
+    }
+    v.bin_count = reinterpret_cast<int*>(base + S->off_bincount);
+    v.bin_slot = reinterpret_cast<int*>(base + S->off_binslot);
+    h->dim = c->dim;
+    h->Q = h->members[0].Q;
+    h->np = h->members[0].np;
+    h->N = (long long)c->nx * c->ny * (c->dim == 3 ? c->nz : 1);
+    h->smem = h->members[0].smem;
+    lbm::SlabHalo& hb = h->halo;
+    memset(&hb, 0, sizeof(hb));
+    const size_t esz = c->storage == LBM_IMB_STORE_F64 ? 8 : (c->storage == LBM_IMB_STORE_F32DEV ? 4 : 2);
+    for (int k = 0; k < nslabs; k++) {
+      hb.f[0][k] = static_cast<unsigned char*>(h->members[k].f[0]);
+      hb.f[1][k] = static_cast<unsigned char*>(h->members[k].f[1]);
+      hb.ny[k] = S->ny_s[k] + 2;
+      hb.plane_bytes[k] = (long long)S->L[k].plane * (long long)esz;
+    }
+    hb.ns = nslabs;
+    hb.periodic = !c->wall_y;
+    hb.row_bytes = (int)(S->L[0].pitch * esz);
+    hb.nz = c->dim == 3 ? c->nz : 1;
+    int nup = 0, ndn = 0;
+    for (int q = 0; q < h->members[0].Q; q++) {
+      const int cy = c->dim == 2 ? lbm::D2Q9::c(q, 1) : lbm::D3Q19::c(q, 1);
+      if (cy == 1) hb.qdir[0][nup++] = q;
+      if (cy == -1) hb.qdir[1][ndn++] = q;
+    }
+    hb.nq = nup;  // == ndn: the directions come in opposite pairs
+    // the halos of the initial state
+    if (lbm::launch_halo_exchange(hb, 0, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      st = LBM_IMB_ECUDA;
+  }
+  free(S);
+  if (st) {
+    if (h) {
+      delete[] h->members;
+      delete h;
+    }
+    return st;
+  }
+  *out = h;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_slab_member(lbm_imb_t* h, int i, lbm_imb_t** member) {
+  if (!h || !member || !h->is_slab || i < 0 || i >= h->nm) return LBM_IMB_EINVAL;
+  *member = h->members + i;
+  return LBM_IMB_OK;
+}
+
 int lbm_imb_batch_member(lbm_imb_t* h, int i, lbm_imb_t** member) {
   if (!h || !member || !h->is_batch || i < 0 || i >= h->nm) return LBM_IMB_EINVAL;
   *member = h->members + i;
@@ -746,11 +966,16 @@ int lbm_imb_step(lbm_imb_t* h, int64_t n) {
     }
     h->cur ^= 1;
     h->steps++;
+    for (int k = 0; h->is_slab && k < h->nm; k++) {
+      h->members[k].cur = h->cur;
+      h->members[k].steps = h->steps;
+    }
   }
   return check_cuda(cudaGetLastError());
 }
 
 int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* total_ms) {
+  if (h && h->is_slab) return LBM_IMB_EUNSUPPORTED;
   if (!h || n < 1 || n > 4096 || !kernel_ms || !total_ms || h->is_member) return LBM_IMB_EINVAL;
   if (h->is_batch) {
     // one persistent launch per step: its time goes to the collide slot
@@ -825,6 +1050,10 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches) {
     *launches = 1;
     return LBM_IMB_OK;
   }
+  if (h->is_slab) {  // per slab: clear, raster, collide; then the halo copy and the DEM
+    *launches = (h->np > 0 ? 3 : 1) * h->nm + 1 + (h->np > 0 ? 4 * h->v.substeps : 0);
+    return LBM_IMB_OK;
+  }
   *launches = h->np > 0 ? 3 + (h->v.dem_skin > 0.0 ? 6 : 4) * h->v.substeps : 1;
   return LBM_IMB_OK;
 }
@@ -876,6 +1105,7 @@ int lbm_imb_set_particles(lbm_imb_t* h, const double* pos, const double* vel, co
 }
 
 int lbm_imb_fields(lbm_imb_t* h, double* rho, double* u, double* eps, int64_t cap, int on_device) {
+  if (h && h->is_slab) return LBM_IMB_EUNSUPPORTED;  // per slab: the member handles
   if (!h || cap < h->N) return LBM_IMB_EINVAL;
   View v = view_of(h, h->cur);
   if (eps) {
@@ -913,6 +1143,7 @@ int lbm_imb_fields(lbm_imb_t* h, double* rho, double* u, double* eps, int64_t ca
 }
 
 int lbm_imb_get_populations(lbm_imb_t* h, double* f, int64_t cap, int on_device) {
+  if (h && h->is_slab) return LBM_IMB_EUNSUPPORTED;  // per slab: the member handles
   if (!h || !f || cap < (int64_t)h->Q * h->N) return LBM_IMB_EINVAL;
   View v = view_of(h, h->cur);
   const long long rows = (long long)v.ny * v.nz;
@@ -936,6 +1167,7 @@ int lbm_imb_get_populations(lbm_imb_t* h, double* f, int64_t cap, int on_device)
 }
 
 int lbm_imb_set_populations(lbm_imb_t* h, const double* f, int64_t cap, int on_device) {
+  if (h && h->is_slab) return LBM_IMB_EUNSUPPORTED;  // per slab: the member handles
   if (!h || !f || cap < (int64_t)h->Q * h->N) return LBM_IMB_EINVAL;
   View v = view_of(h, h->cur);
   const long long rows = (long long)v.ny * v.nz;
@@ -961,6 +1193,7 @@ int lbm_imb_set_populations(lbm_imb_t* h, const double* f, int64_t cap, int on_d
 }
 
 int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum, double* particle_momentum) {
+  if (h && h->is_slab) return LBM_IMB_EUNSUPPORTED;  // per slab: the member handles
   if (!h) return LBM_IMB_EINVAL;
   View v = view_of(h, h->cur);
   lbm::launch_totals(v, h->f[h->cur], h->stream);
@@ -980,7 +1213,7 @@ int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum, dou
 
 int lbm_imb_drag_samples(lbm_imb_t* h, const double* u_dev, const double* eps_dev, double shell, float* feats,
                          float* target, int64_t cap) {
-  if (!h || h->is_batch || !u_dev || !eps_dev || !feats || !target || cap < h->np || !(shell > 0.0))
+  if (!h || h->is_batch || h->is_slab || !u_dev || !eps_dev || !feats || !target || cap < h->np || !(shell > 0.0))
     return LBM_IMB_EINVAL;
   View v = view_of(h, h->cur);
   lbm::launch_drag_samples(v, u_dev, eps_dev, shell, feats, target, h->stream);
@@ -988,6 +1221,7 @@ int lbm_imb_drag_samples(lbm_imb_t* h, const double* u_dev, const double* eps_de
 }
 
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant) {
+  if (h && h->is_slab) return LBM_IMB_EUNSUPPORTED;  // per slab: the member handles
   if (!h || h->is_member || variant < 0 || variant > 9) return LBM_IMB_EINVAL;
   if (h->is_batch) return LBM_IMB_EUNSUPPORTED;
   if (h->graphs_ok) {
@@ -1011,6 +1245,15 @@ int lbm_imb_destroy(lbm_imb_t* h) {
   if (h->is_batch) {
     batch_drop_graphs(h);
     for (int i = 0; i < h->nm; i++) lbm_imb_destroy_member_graphs(h->members + i);
+    delete[] h->members;
+    delete h;
+    return LBM_IMB_OK;
+  }
+  if (h->is_slab) {
+    if (h->graphs_ok) {
+      cudaGraphExecDestroy(h->graph[0]);
+      cudaGraphExecDestroy(h->graph[1]);
+    }
     delete[] h->members;
     delete h;
     return LBM_IMB_OK;

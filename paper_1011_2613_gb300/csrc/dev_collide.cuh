@@ -215,8 +215,8 @@ __device__ __forceinline__ void pull(const View& v, const int xx, const int y, c
   const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
   const int ry[3] = {y * pitch, ym * pitch, yp * pitch};
   const int rz[3] = {z * ny * pitch, zm * ny * pitch, zp * ny * pitch};
-  const bool wall_row = v.wall_y && (y == 0 || y == ny - 1);
-  if (!wall_row) {  // rows are whole warps: the test is warp-uniform in the row kernel
+  const bool wlo = v.wall_lo && y == v.y0, whi = v.wall_hi && y == v.y0 + v.ny_c - 1;
+  if (!(wlo || whi)) {  // rows are whole warps: the test is warp-uniform in the row kernel
 #pragma unroll
     for (int q = 0; q < Q; q++) {
       const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
@@ -230,7 +230,7 @@ __device__ __forceinline__ void pull(const View& v, const int xx, const int y, c
       const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
       const int sx = cx == 1 ? xm : (cx == -1 ? xp : xx);
       const int idx = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)] + sx;
-      const bool bounce = (cy == 1 && y == 0) || (cy == -1 && y == ny - 1);
+      const bool bounce = (cy == 1 && wlo) || (cy == -1 && whi);
       if (bounce)  // halfway bounce-back: the opposite population of this node
         f[q] = load ? S::load(static_cast<const Elem*>(v.src_q[opp(q)]), n) : T(0);
       else
@@ -376,18 +376,18 @@ __device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& 
   return k;
 }
 
-// node position relative to the particle (minimum image) and the rigid-body
-// velocity V = v + w x r there
+// node position relative to the particle (minimum image; y is the local row,
+// global row y + ygo) and the rigid-body velocity V = v + w x r there
 template <bool D3, typename PT>
 __device__ __forceinline__ void node_rel(const View& v, const Kin<PT>& k, const int x, const int y, const int z,
                                          PT (&r)[3], PT (&V)[3]) {
   if constexpr (sizeof(PT) == 4) {
     r[0] = min_image_f(float(x - k.ic[0]) - k.c[0], v.nx, true);
-    r[1] = min_image_f(float(y - k.ic[1]) - k.c[1], v.ny, !v.wall_y);
+    r[1] = min_image_f(float(y + v.ygo - k.ic[1]) - k.c[1], v.ny_glob, !v.wall_y);
     r[2] = D3 ? min_image_f(float(z - k.ic[2]) - k.c[2], v.nz, true) : 0.f;
   } else {
     r[0] = min_image((double)x - k.c[0], v.nx, true);
-    r[1] = min_image((double)y - k.c[1], v.ny, !v.wall_y);
+    r[1] = min_image((double)(y + v.ygo) - k.c[1], v.ny_glob, !v.wall_y);
     r[2] = D3 ? min_image((double)z - k.c[2], v.nz, true) : 0.0;
   }
   V[0] = k.vel[0] + (k.w[1] * r[2] - k.w[2] * r[1]);
@@ -811,12 +811,12 @@ __device__ __forceinline__ void pull_pair(const View& v, const int x, const int 
   // x sources of the two nodes for c_x = +1 (left) and c_x = -1 (right)
   const int l0 = x == 0 ? nx - 1 : x - 1, l1 = x;
   const int r0 = x + 1 < nx ? x + 1 : 0, r1 = x + 2 < nx ? x + 2 : (x + 2 == nx ? 0 : 1);
-  const bool wall_row = v.wall_y && (y == 0 || y == ny - 1);
+  const bool wlo = v.wall_lo && y == v.y0, whi = v.wall_hi && y == v.y0 + v.ny_c - 1;
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
     const int row = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)];
-    const bool bounce = wall_row && ((cy == 1 && y == 0) || (cy == -1 && y == ny - 1));
+    const bool bounce = (cy == 1 && wlo) || (cy == -1 && whi);
     if (bounce) {  // halfway bounce-back: the opposite populations of the pair itself
       const float2 w = IO::load2(static_cast<const Elem*>(v.src_q[opp(q)]), n);
       f[q] = F2(w.x, w.y);

@@ -42,22 +42,41 @@ __device__ __forceinline__ int wrap_idx(int i, const int n) {
 // clear the previous footprint (the taken owner slots) and zero the force sums
 // --------------------------------------------------------------------------
 // one warp per particle
+// whether rows ly .. ly + ey - 1 of the whole lattice include one of this
+// slab's computed rows (always, for a whole lattice)
+__device__ __forceinline__ bool rows_meet_slab(const View& v, const int ly, const int ey) {
+  if (v.ny_c == v.ny_glob) return true;
+  for (int r = 0; r < ey; r++) {
+    int j = ly + r;
+    if (v.wall_y) {
+      if (j < 0 || j >= v.ny_glob) continue;
+    } else {
+      j = wrap_idx(j, v.ny_glob);
+    }
+    j -= v.ygo;
+    if (j >= v.y0 && j < v.y0 + v.ny_c) return true;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, const int lane,
                                                    const bool zero_forces) {
   const int* box = v.lo + 6 * p;
   const int lx = box[0], ly = box[1], lz = box[2];
   const int ex = box[3], ey = box[4], ez = box[5];
-  const int total = ex * ey * ez;
+  const int total = rows_meet_slab(v, ly, ey) ? ex * ey * ez : 0;
   const FastDiv3 fd(ex, ey);
   for (int t = lane; t < total; t += 32) {
     int ci, cj, ck;
     fd.split(t, ci, cj, ck);
     int i = lx + ci, j = ly + cj, k = lz + ck;
     if (v.wall_y) {
-      if (j < 0 || j >= v.ny) continue;
+      if (j < 0 || j >= v.ny_glob) continue;
     } else {
-      j = wrap_idx(j, v.ny);
+      j = wrap_idx(j, v.ny_glob);
     }
+    j -= v.ygo;  // local row; only this slab's computed rows
+    if (j < v.y0 || j >= v.y0 + v.ny_c) continue;
     i = wrap_idx(i, v.nx);
     k = wrap_idx(k, v.nz);
     const long long n = ((long long)k * v.ny + j) * v.pitch + i;
@@ -359,6 +378,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     n_part = 0;
     n_need = 0;
   }
+  if (!rows_meet_slab(v, lo[1], ne[1])) return;  // another slab's particle (block-uniform)
   for (int t = threadIdx.x; t < 3 * 64; t += blockDim.x) {
     const int d = t / 64, i = t % 64;
     const T b = (d < DIM && i <= ne[d]) ? T(((double)(lo[d] + i) - 0.5) - c[d]) : T(0);
@@ -376,10 +396,12 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   auto claim = [&](int ci, int cj, int ck, T e) {
     int i = lo[0] + ci, j = lo[1] + cj, k = lo[2] + ck;
     if (v.wall_y) {
-      if (j < 0 || j >= v.ny) return;
+      if (j < 0 || j >= v.ny_glob) return;
     } else {
-      j = wrap_idx(j, v.ny);
+      j = wrap_idx(j, v.ny_glob);
     }
+    j -= v.ygo;  // local row; only this slab's computed rows
+    if (j < v.y0 || j >= v.y0 + v.ny_c) return;
     i = wrap_idx(i, v.nx);
     k = wrap_idx(k, v.nz);
     const long long n = ((long long)k * v.ny + j) * v.pitch + i;

@@ -56,10 +56,10 @@ __global__ void __launch_bounds__(128, MINB) collide_kernel(View v, int ntiles) 
   const WarpQueue<STORE> wq = warp_queue<LAT, STORE>(smem_q, threadIdx.x >> 5);
   int cnt = 0;
   (void)ntiles;
-  for (TileWalk w(blockIdx.x, gridDim.x, (nx + 127) / 128, v.ny); w.z < nz; w.next()) {
+  for (TileWalk w(blockIdx.x, gridDim.x, (nx + 127) / 128, v.ny_c); w.z < nz; w.next()) {
     const int x = w.xt * 128 + (int)threadIdx.x;
     const bool active = x < nx;
-    fused_node<LAT, STORE>(v, active ? x : nx - 1, w.y, w.z, active, wq, cnt, lane);
+    fused_node<LAT, STORE>(v, active ? x : nx - 1, v.y0 + w.y, w.z, active, wq, cnt, lane);
   }
   queue_drain<LAT, STORE>(v, wq, cnt, lane);
 }
@@ -351,7 +351,7 @@ static void launch_fused(const View& v, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
-  const int ntiles = ((v.nx + 127) / 128) * v.ny * v.nz;
+  const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
   const int g = grid < ntiles ? grid : ntiles;
   if constexpr (PREFETCH) collide_prefetch_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);
   else collide_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);

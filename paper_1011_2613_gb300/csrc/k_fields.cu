@@ -180,3 +180,51 @@ void launch_totals(const View& v, const void* f, cudaStream_t s) {
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+// Halo rows of y slabs (lbm_imb_slabs_init).  Work item = one 16-byte piece
+// of one row of one direction plane at one z, for one side of one slab
+// boundary: side 0 copies the lower slab's last computed row into the upper
+// slab's lower halo, side 1 the upper slab's first computed row into the
+// lower slab's upper halo.  Only the directions the pull reads from a halo
+// row move: c_y = +1 on side 0, c_y = -1 on side 1 (5 of 19 in D3Q19, 3 of
+// 9 in D2Q9).  Rows are whole multiples of 64 bytes (pitch is a multiple of
+// 32 elements) and planes start on 256-byte boundaries.
+__global__ void halo_exchange_kernel(SlabHalo h, int parity) {
+  const int pieces = h.row_bytes / 16;
+  const int nbound = h.periodic ? h.ns : h.ns - 1;
+  const long long per_side = (long long)h.nq * h.nz * pieces;
+  const long long total = 2LL * nbound * per_side;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long bs = w / per_side;
+    long long r = w - bs * per_side;
+    const int b = (int)(bs >> 1), side = (int)(bs & 1);
+    const int iq = (int)(r / ((long long)h.nz * pieces));
+    r -= (long long)iq * h.nz * pieces;
+    const int z = (int)(r / pieces), c = (int)(r - (long long)z * pieces);
+    const int q = h.qdir[side][iq];
+    const int lo = b, hi = b + 1 == h.ns ? 0 : b + 1;
+    const int from = side == 0 ? lo : hi, to = side == 0 ? hi : lo;
+    const int yf = side == 0 ? h.ny[lo] - 2 : 1;   // computed row
+    const int yt = side == 0 ? 0 : h.ny[lo] - 1;   // halo row
+    const unsigned char* src = h.f[parity][from] + q * h.plane_bytes[from] +
+                               ((long long)z * h.ny[from] + yf) * h.row_bytes + 16LL * c;
+    unsigned char* dst = h.f[parity][to] + q * h.plane_bytes[to] +
+                         ((long long)z * h.ny[to] + yt) * h.row_bytes + 16LL * c;
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+  }
+}
+
+cudaError_t launch_halo_exchange(const SlabHalo& h, int parity, cudaStream_t s) {
+  const int nbound = h.periodic ? h.ns : h.ns - 1;
+  const long long total = 2LL * nbound * h.nq * h.nz * (h.row_bytes / 16);
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  halo_exchange_kernel<<<(unsigned)blocks, 256, 0, s>>>(h, parity);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

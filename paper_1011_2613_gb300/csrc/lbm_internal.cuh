@@ -60,6 +60,13 @@ __host__ __device__ constexpr int opp(int q) {
 struct View {
   // lattice geometry
   int dim, Q, nx, ny, nz, pitch, wall_y, storage;
+  // y slab of a decomposed lattice: local rows y0 .. y0 + ny_c - 1 are
+  // computed (the rows around them are halos the exchange fills); local row
+  // y is row y + ygo of the whole lattice, ny_glob rows tall; a wall lies
+  // below the first / above the last computed row when wall_lo / wall_hi.
+  // A whole lattice: y0 = 0, ny_c = ny, ygo = 0, ny_glob = ny,
+  // wall_lo = wall_hi = wall_y.
+  int y0, ny_c, ygo, ny_glob, wall_lo, wall_hi;
   long long plane;  // elements per population plane = pitch * ny * nz
   // populations: src is read (pull), dst written; per-direction plane
   // bases (fsrc + q * plane elements), filled by the host with fsrc/fdst
@@ -128,6 +135,21 @@ void eps_table_geometry(int dim, double R, float* lo_r, float* h_r, float* h_s, 
 cudaError_t launch_eps_table_build(int dim, double R, float* tab, cudaStream_t s);
 int eps_raster_set_attrs(int bytes);
 void launch_collide(const View& v, cudaStream_t s);
+// halo rows of y slabs: for every boundary, the last computed row of the
+// lower slab and the first of the upper one are copied (all directions, all
+// z) into the other slab's halo row of the populations `parity`
+struct SlabHalo {
+  unsigned char* f[2][16];  // per slab: the two population lattices
+  int ny[16];               // per slab: local rows (computed + 2 halos)
+  int ns;                   // slabs
+  int periodic;             // exchange across the ends too (no walls)
+  long long plane_bytes[16];
+  int row_bytes, nz;
+  // the directions a halo row feeds: qdir[0] those with c_y = +1 (pulled
+  // from the row below the first computed row), qdir[1] those with c_y = -1
+  int nq, qdir[2][8];
+};
+cudaError_t launch_halo_exchange(const SlabHalo& h, int parity, cudaStream_t s);
 void launch_dem(const View& v, cudaStream_t s);
 void launch_dem_contacts(const View& v, cudaStream_t s);
 int dem_bin_geometry(int dim, const int* ext, int wall_y, double rmax, int nb[3], double bsz[3]);

@@ -65,6 +65,13 @@ def lib():
             L.lbm_imb_step.argtypes = [C.c_void_p, C.c_int64]
             L.lbm_imb_step_profiled.restype = C.c_int
             L.lbm_imb_step_profiled.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
+            L.lbm_imb_slabs_required_bytes.restype = C.c_size_t
+            L.lbm_imb_slabs_required_bytes.argtypes = [C.POINTER(Config), C.c_int]
+            L.lbm_imb_slabs_init.restype = C.c_int
+            L.lbm_imb_slabs_init.argtypes = [C.POINTER(Config), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                             C.POINTER(C.c_void_p)]
+            L.lbm_imb_slab_member.restype = C.c_int
+            L.lbm_imb_slab_member.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
             L.lbm_imb_dem_rebuilds.restype = C.c_int
             L.lbm_imb_dem_rebuilds.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
             L.lbm_imb_launches_per_step.restype = C.c_int
@@ -221,7 +228,7 @@ class Simulation:
 
     # ------------------------------------------------------------------
     @classmethod
-    def _member(cls, batch, i, cfg):
+    def _member(cls, batch, i, cfg, accessor="lbm_imb_batch_member"):
         self = cls.__new__(cls)
         self.cfg = cfg
         self.dim = int(cfg.dim)
@@ -233,7 +240,7 @@ class Simulation:
         self.stream = batch.stream
         self.batch = batch  # keeps the batch (and its memory) alive
         h = C.c_void_p()
-        _check(lib().lbm_imb_batch_member(batch.h, i, C.byref(h)), "lbm_imb_batch_member")
+        _check(getattr(lib(), accessor)(batch.h, i, C.byref(h)), accessor)
         self.h = h
         self._member_of = batch
         return self
@@ -453,3 +460,82 @@ def probe_atan2q1(y, x):
     _check(lib().lbm_imb_probe_atan2q1(y.data_ptr(), x.data_ptr(), fast.data_ptr(), ref.data_ptr(), y.numel(),
                                         s.cuda_stream), "lbm_imb_probe_atan2q1")
     return fast, ref
+
+
+def slab_rows(ny: int, nslabs: int):
+    """(first global row, computed rows) of each y slab: ny split as evenly as
+    possible, the first ny % nslabs slabs one row more."""
+    base, rem = divmod(int(ny), int(nslabs))
+    out, y = [], 0
+    for k in range(nslabs):
+        n = base + (1 if k < rem else 0)
+        out.append((y, n))
+        y += n
+    return out
+
+
+class Slabs:
+    """One suspension decomposed along y into ``nslabs`` slabs with halo
+    exchange after every collision (lbm_imb_slabs_* in the C ABI).  The
+    particles are shared; ``members[k]`` gives slab k's local lattice (its
+    computed rows between two halo rows)."""
+
+    def __init__(self, cfg, nslabs: int, device=None, stream=None):
+        import torch
+
+        L = lib()
+        self.cfg = cfg
+        self.nslabs = int(nslabs)
+        c, keep = make_config(cfg)
+        nbytes = int(L.lbm_imb_slabs_required_bytes(C.byref(c), self.nslabs))
+        if nbytes == 0:  # the configuration is rejected: report why
+            h0 = C.c_void_p()
+            _check(L.lbm_imb_slabs_init(C.byref(c), self.nslabs, None, 0, None, C.byref(h0)), "lbm_imb_slabs_init")
+            raise LbmImbError(EINVAL, "lbm_imb_slabs_required_bytes")
+        self.nbytes = nbytes
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            ptr = (self.buf.data_ptr() + 255) // 256 * 256
+            h = C.c_void_p()
+            st = L.lbm_imb_slabs_init(C.byref(c), self.nslabs, C.c_void_p(ptr), nbytes,
+                                      C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        del keep
+        _check(st, "lbm_imb_slabs_init")
+        self.h = h
+        self.dim = int(cfg.dim)
+        self.np = int(len(cfg.radius))
+        self.Q = 9 if self.dim == 2 else 19
+        self.shape = (int(cfg.nx), int(cfg.ny), int(cfg.nz) if self.dim == 3 else 1)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        self.rows = slab_rows(cfg.ny, self.nslabs)
+        self.members = [Simulation._member(self, k, cfg.replace(ny=n + 2), "lbm_imb_slab_member")
+                        for k, (_, n) in enumerate(self.rows)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            lib().lbm_imb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _check(lib().lbm_imb_step(self.h, int(n)), "lbm_imb_step")
+
+    def sync(self):
+        _check(lib().lbm_imb_sync(self.h), "lbm_imb_sync")
+
+    particles = Simulation.particles
+
+    def populations(self) -> np.ndarray:
+        """The whole lattice's populations (Q, nz, ny, nx), assembled from the
+        slabs' computed rows."""
+        parts = [m.populations()[:, :, 1:n + 1, :] for m, (_, n) in zip(self.members, self.rows)]
+        return np.concatenate(parts, axis=2)

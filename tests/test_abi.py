@@ -79,3 +79,17 @@ def test_required_bytes_and_validation(built):
     n16 = lbm.required_bytes(cfg.replace(storage="f16dev"))
     assert n16 < n32 < n
     assert built.lbm_imb_strerror(-7).decode().startswith("a lattice cell")
+
+
+def test_slab_rows_partition():
+    """The y-slab split of the decomposed lattice (host logic): every row once,
+    sizes differing by at most one, larger slabs first."""
+    from paper_1011_2613_gb300 import lbm as L
+
+    for ny in (7, 64, 1512):
+        for ns in (2, 3, 5, 16):
+            rows = L.slab_rows(ny, ns)
+            assert rows[0][0] == 0 and sum(n for _, n in rows) == ny
+            assert all(rows[k][0] + rows[k][1] == rows[k + 1][0] for k in range(ns - 1))
+            sizes = [n for _, n in rows]
+            assert max(sizes) - min(sizes) <= 1 and sizes == sorted(sizes, reverse=True)
