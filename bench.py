@@ -78,6 +78,8 @@ FP64_OPS = {3: (148.0, 225.0), 2: (68.0, 151.0)}
 # case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
 # moves this many bytes per node times its node count (same solid fraction).
 TRAFFIC_B_PER_NODE = {("f64", 3): 376.3, ("f32dev", 3): 189.6, ("f16dev", 3): 116.4}
+ESZ = {"f64": 8, "f32dev": 4, "f16dev": 2, "f64dev": 8}  # bytes per stored population
+DTYPE = {"f64": "f64", "f32dev": "f32", "f16dev": "f32", "f64dev": "f32x2"}  # arithmetic type
 
 # FP64 pipe peak: the nominal 1.25 TFLOP/s of the GB300 FP64 units, i.e.
 # 625 G FP64-pipe operations per second (a DFMA counts two flops, one slot)
@@ -88,8 +90,8 @@ def algorithmic_bytes_per_lup(cfg, owned_fraction):
     """Read and write each population once (2 Q s), read the owner word of
     every node (4 B), read the covered fraction at owned nodes."""
     Q = 9 if cfg.dim == 2 else 19
-    s = {"f64": 8, "f32dev": 4, "f16dev": 2}[cfg.storage]
-    se = 8 if cfg.storage == "f64" else 4
+    s = ESZ[cfg.storage]
+    se = 8 if cfg.storage in ("f64", "f64dev") else 4
     return 2 * Q * s + 4 + se * owned_fraction
 
 
@@ -235,7 +237,7 @@ def pick_collide(sim, args):
         sim.set_collide_variant(args.collide_variant)
         return {"variant": args.collide_variant, "table": None}, 0
     tune, cached = autotune.tuned_collide(sim)
-    return tune, 0 if cached else 3 * len(autotune.COLLIDE_VARIANTS)
+    return tune, 0 if cached else 3 * len(autotune.collide_variants(sim.cfg.storage))
 
 
 def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=None):
@@ -299,7 +301,7 @@ def measure_slabs(cfg, args, torch, nslabs, ref_sim, steps_target):
     diff = {k: float(np.max(np.abs(ps[k] - pw[k])) / max(float(np.max(np.abs(pw[k]))), 1e-300))
             for k in ("pos", "vel", "force")}
     q_cross = 5 if cfg.dim == 3 else 3
-    esz = {"f64": 8, "f32dev": 4, "f16dev": 2}[cfg.storage]
+    esz = ESZ[cfg.storage]
     pitch = (cfg.nx + 31) // 32 * 32
     nz = cfg.nz if cfg.dim == 3 else 1
     bounds = nslabs - (1 if cfg.wall_y else 0)
@@ -505,6 +507,7 @@ def run_ours(args):
     if not args.no_variants and rank == 0 and cfg.storage == "f64":
         steps_done = tuned_steps + args.warmup + 2 * args.steps + (args.steps if e2e else 0)
         forms = [("f32dev", cfg.replace(storage="f32dev")), ("f16dev", cfg.replace(storage="f16dev")),
+                 ("f64dev", cfg.replace(storage="f64dev")),  # FP64 deviation, double-FP32 arithmetic
                  ("f64_eps_table", cfg.replace(eps_method=1))]  # Eq. 6 covered fractions
         for st, c in forms:
             try:
@@ -563,11 +566,11 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"f64": "f64", "f32dev": "f32", "f16dev": "f32"}[cfg.storage],
+            "vs_baseline": None, "dtype": DTYPE[cfg.storage],
             "data": "synthetic",
             "config": {"workload": wl["name"], "storage": cfg.storage, "nodes": cfg.n_nodes,
                        "particles": cfg.n_particles, "l2": "inputs larger than L2 (two lattices, "
-                       f"{2 * (19 if cfg.dim == 3 else 9) * {'f64': 8, 'f32dev': 4, 'f16dev': 2}[cfg.storage] * cfg.n_nodes / 1e9:.1f} GB)", "graph": "CUDA graph per step"},
+                       f"{2 * (19 if cfg.dim == 3 else 9) * ESZ[cfg.storage] * cfg.n_nodes / 1e9:.1f} GB)", "graph": "CUDA graph per step"},
             "roofline": roofline,
             "roofline_hbm": roof_hbm,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
@@ -591,7 +594,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS))
-    ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev"])
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev", "f64dev"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--collide-variant", type=int, default=None,
                     help="fix the collide kernel form instead of autotuning it")

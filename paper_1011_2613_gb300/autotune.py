@@ -100,6 +100,12 @@ def tuned_batch(cfgs, device=None, path: str | None = None, steps: int = 3):
 
 
 COLLIDE_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9)
+# the double-FP32 storage has the persistent fused and TMA forms only
+COLLIDE_VARIANTS_BY_STORAGE = {"f64dev": (0, 1, 2, 3, 4, 5)}
+
+
+def collide_variants(storage) -> tuple:
+    return COLLIDE_VARIANTS_BY_STORAGE.get(storage, COLLIDE_VARIANTS)
 
 
 def collide_signature(cfg, device_name: str) -> str:
@@ -107,9 +113,11 @@ def collide_signature(cfg, device_name: str) -> str:
                      f"n{int(math.log2(max(cfg.n_nodes, 1)))}", f"p{int(math.log2(max(cfg.n_particles, 1)))}"])
 
 
-def tune_collide(sim, steps: int = 2, variants=COLLIDE_VARIANTS) -> dict:
+def tune_collide(sim, steps: int = 2, variants=None) -> dict:
     """Time every collide kernel form on ``sim`` (real steps: the simulation
     advances) and leave it on the fastest.  Returns {"variant", "table"}."""
+    if variants is None:
+        variants = collide_variants(sim.cfg.storage)
     table = []
     for var in variants:
         try:

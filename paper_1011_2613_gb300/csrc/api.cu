@@ -53,7 +53,7 @@ int validate(const lbm_imb_config* c) {
   if (c->dim == 2 && c->nz != 1) return LBM_IMB_EINVAL;
   if (c->ny > 65535 || c->nz > 65535) return LBM_IMB_EUNSUPPORTED;
   if (!(c->tau > 0.5) || !isfinite(c->tau)) return LBM_IMB_EINVAL;
-  if (c->storage < 0 || c->storage > 2) return LBM_IMB_EINVAL;
+  if (c->storage < 0 || c->storage > 3) return LBM_IMB_EINVAL;
   if (c->wall_y != 0 && c->wall_y != 1) return LBM_IMB_EINVAL;
   if (!(c->rho_fluid > 0.0)) return LBM_IMB_EINVAL;
   if (c->n_particles < 0 || c->n_particles > (1ll << 30)) return LBM_IMB_EINVAL;
@@ -80,8 +80,8 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->pitch = (c->nx + 31) / 32 * 32;
   L->plane = (long long)L->pitch * c->ny * nz;
   if (L->plane >= (1ll << 31)) return LBM_IMB_EUNSUPPORTED;  // 32-bit node offsets
-  L->esz_f = c->storage == LBM_IMB_STORE_F64 ? 8 : (c->storage == LBM_IMB_STORE_F32DEV ? 4 : 2);
-  L->esz_eps = c->storage == LBM_IMB_STORE_F64 ? 8 : 4;
+  L->esz_f = lbm::pop_bytes(c->storage);
+  L->esz_eps = lbm::fp64_eps(c->storage) ? 8 : 4;
   double rmax = 0.0;
   for (int64_t p = 0; p < c->n_particles; p++) rmax = c->radius[p] > rmax ? c->radius[p] : rmax;
   L->rmax = rmax;
@@ -122,7 +122,7 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->off_tf = take(np * 24);
   L->off_fc = take(np * 24);
   L->off_lo = take(np * 24);
-  L->off_kin = take(np * 64);
+  L->off_kin = take(np * 128);
   L->off_binof = take(np * 4);
   L->off_bincount = take((size_t)nbins * 4);
   L->off_binslot = take((size_t)nbins * lbm::kBinCap * 4);
@@ -190,7 +190,7 @@ View view_of(const lbm_imb* h, int src) {
   View v = h->v;
   v.fsrc = h->f[src];
   v.fdst = h->f[src ^ 1];
-  const size_t esz = v.storage == LBM_IMB_STORE_F64 ? 8 : (v.storage == LBM_IMB_STORE_F32DEV ? 4 : 2);
+  const size_t esz = lbm::pop_bytes(v.storage);
   for (int q = 0; q < 19; q++) {
     const size_t off = q < v.Q ? (size_t)q * (size_t)v.plane * esz : 0;
     v.src_q[q] = static_cast<const unsigned char*>(v.fsrc) + off;
@@ -371,6 +371,18 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   v.tau_f = (float)v.tau;
   v.omega_f = (float)v.omega;
   v.rho0_f = (float)v.rho0;
+  auto split = [](double d, float* p) {  // high and low FP32 parts
+    p[0] = (float)d;
+    p[1] = (float)(d - (double)p[0]);
+  };
+  split(v.omc, v.omc_df);
+  split(v.tau, v.tau_df);
+  split(v.omega, v.omega_df);
+  split(v.rho0, v.rho0_df);
+  for (int q = 0; q < 19; q++) {
+    split(v.fq[q], v.fq_df[q]);
+    split(v.cg3[q], v.cg3_df[q]);
+  }
   v.err = reinterpret_cast<int*>(base + L.off_err);
   v.red = reinterpret_cast<double*>(base + L.off_red);
   v.eps_method = np > 0 ? c->eps_method : 0;
@@ -503,6 +515,7 @@ static int batch_layout(const lbm_imb_config* cfgs, int n, BatchLayout* B) {
     if (c->dim != cfgs[0].dim || c->storage != cfgs[0].storage) return LBM_IMB_EINVAL;
     if (c->dem_substeps != 1) return LBM_IMB_EUNSUPPORTED;
     if (c->dem_skin != 0.0) return LBM_IMB_EUNSUPPORTED;
+    if (c->storage == LBM_IMB_STORE_F64DEV) return LBM_IMB_EUNSUPPORTED;
     B->member_off[i] = take(B->member[i].total);
   }
   B->total = o;
@@ -837,7 +850,7 @@ int lbm_imb_slabs_init(const lbm_imb_config* c, int nslabs, void* dev_buf, size_
     h->smem = h->members[0].smem;
     lbm::SlabHalo& hb = h->halo;
     memset(&hb, 0, sizeof(hb));
-    const size_t esz = c->storage == LBM_IMB_STORE_F64 ? 8 : (c->storage == LBM_IMB_STORE_F32DEV ? 4 : 2);
+    const size_t esz = lbm::pop_bytes(c->storage);
     for (int k = 0; k < nslabs; k++) {
       hb.f[0][k] = static_cast<unsigned char*>(h->members[k].f[0]);
       hb.f[1][k] = static_cast<unsigned char*>(h->members[k].f[1]);

@@ -2,6 +2,9 @@
 // Noble-Torczynski immersed moving boundary term, shared by the per-step
 // kernel (k_collide.cu) and the batched persistent kernel (k_batch.cu).
 #pragma once
+#include <type_traits>
+
+#include "dev_df.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -60,6 +63,52 @@ struct Storage<LBM_IMB_STORE_F16DEV> {
   }
 };
 
+// FP64 deviation g = f - w rho0, collided in double-FP32 arithmetic
+// (dev_df.cuh): FP64 accuracy with the arithmetic on the FP32 pipe
+template <>
+struct Storage<LBM_IMB_STORE_F64DEV> {
+  using Elem = double;
+  using T = DF;
+  using E = double;
+  static constexpr bool DEV = true;
+  static constexpr bool SCALED = false;
+  __device__ static __forceinline__ T load(const Elem* p, int i) { return df_from_bits(__ldg(p + i)); }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return df_from_bits(p[i]); }
+  __device__ static __forceinline__ void store(Elem* p, int i, T v) { p[i] = df_to_bits(v); }
+  __device__ static __forceinline__ void store2(Elem* p, Elem* r, int i, T a, T b) {
+    p[i] = df_to_bits(a);
+    r[i] = df_to_bits(b);
+  }
+};
+
+// a per-simulation constant in the arithmetic type of the storage
+template <int STORE>
+__device__ __forceinline__ typename Storage<STORE>::T pick(const double d, const float f, const float (&p)[2]) {
+  if constexpr (STORE == LBM_IMB_STORE_F64) return d;
+  else if constexpr (STORE == LBM_IMB_STORE_F64DEV) return DF(p[0], p[1]);
+  else return f;
+}
+
+// warp shuffles and the FP64 value of each arithmetic type
+__device__ __forceinline__ float shfl_xor(const float a, const int d) { return __shfl_xor_sync(0xffffffffu, a, d); }
+__device__ __forceinline__ double shfl_xor(const double a, const int d) { return __shfl_xor_sync(0xffffffffu, a, d); }
+__device__ __forceinline__ float shfl_down(const float a, const int d) { return __shfl_down_sync(0xffffffffu, a, d); }
+__device__ __forceinline__ double shfl_down(const double a, const int d) {
+  return __shfl_down_sync(0xffffffffu, a, d);
+}
+__device__ __forceinline__ double to_double(const float a) { return (double)a; }
+__device__ __forceinline__ double to_double(const double a) { return a; }
+__device__ __forceinline__ double to_double(const DF a) { return df_to_bits(a); }
+// a stored covered fraction in the particle-side arithmetic type
+template <typename PT, typename E>
+__device__ __forceinline__ PT to_pt(const E a) {
+  return (PT)a;
+}
+template <>
+__device__ __forceinline__ DF to_pt<DF, double>(const double a) {
+  return df_from_bits(a);
+}
+
 // Sum the per-node force/torque contributions of a warp by particle (key)
 // and add them to the FP64 per-particle accumulators.
 template <typename PT>
@@ -74,13 +123,13 @@ __device__ __forceinline__ void warp_reduce_to_particles(int key, PT (&val)[6], 
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
 #pragma unroll
-      for (int k = 0; k < 6; k++) val[k] += __shfl_xor_sync(FULL, val[k], d);
+      for (int k = 0; k < 6; k++) val[k] += shfl_xor(val[k], d);
     }
     if (lane < 6) {
       PT x = val[0];
 #pragma unroll
       for (int k = 1; k < 6; k++) x = lane == k ? val[k] : x;
-      if (x != PT(0)) atomicAdd((lane < 3 ? ff + 3 * k0 + lane : tf + 3 * k0 + lane - 3), (double)x);
+      if (x != PT(0)) atomicAdd((lane < 3 ? ff + 3 * k0 + lane : tf + 3 * k0 + lane - 3), to_double(x));
     }
     return;
   }
@@ -94,7 +143,7 @@ __device__ __forceinline__ void warp_reduce_to_particles(int key, PT (&val)[6], 
   for (int d = 1; d < 32; d <<= 1) {
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-      const PT t = __shfl_down_sync(FULL, val[k], d);
+      const PT t = shfl_down(val[k], d);
       if (lane + d <= run_end) val[k] += t;
     }
   }
@@ -102,8 +151,8 @@ __device__ __forceinline__ void warp_reduce_to_particles(int key, PT (&val)[6], 
   if (head && key >= 0) {
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      if (val[k] != PT(0)) atomicAdd(ff + 3 * key + k, (double)val[k]);
-      if (val[3 + k] != PT(0)) atomicAdd(tf + 3 * key + k, (double)val[3 + k]);
+      if (val[k] != PT(0)) atomicAdd(ff + 3 * key + k, to_double(val[k]));
+      if (val[3 + k] != PT(0)) atomicAdd(tf + 3 * key + k, to_double(val[3 + k]));
     }
   }
 }
@@ -153,16 +202,14 @@ __device__ __forceinline__ T cdot(int cx, int cy, int cz, T ux, T uy, T uz) {
   return r;
 }
 
-template <bool DEV, typename T>
-__device__ __forceinline__ T fq_of(const View& v, int q) {
-  if constexpr (DEV) return v.fq_f[q];
-  else return v.fq[q];
+template <int STORE>
+__device__ __forceinline__ typename Storage<STORE>::T fq_of(const View& v, int q) {
+  return pick<STORE>(v.fq[q], v.fq_f[q], v.fq_df[q]);
 }
 
-template <bool DEV, typename T>
-__device__ __forceinline__ T cg3_of(const View& v, int q) {
-  if constexpr (DEV) return v.cg3_f[q];
-  else return v.cg3[q];
+template <int STORE>
+__device__ __forceinline__ typename Storage<STORE>::T cg3_of(const View& v, int q) {
+  return pick<STORE>(v.cg3[q], v.cg3_f[q], v.cg3_df[q]);
 }
 
 // j_a += c_a (w) m for one opposite pair; the first non-zero term assigns
@@ -184,6 +231,14 @@ __device__ __forceinline__ float min_image_f(float d, int n, bool periodic) {
   const float L = (float)n;
   if (d > 0.5f * L) d -= L;
   else if (d < -0.5f * L) d += L;
+  return d;
+}
+
+__device__ __forceinline__ DF min_image_df(DF d, int n, bool periodic) {
+  if (!periodic) return d;
+  const float L = (float)n;
+  if (d.h > 0.5f * L) d = d - DF(L);
+  else if (d.h < -0.5f * L) d = d + DF(L);
   return d;
 }
 
@@ -281,7 +336,7 @@ __device__ __forceinline__ Moments<T> moments(const View& v, const T (&f)[LAT::Q
   }
   Moments<T> r;
   r.drho = S::DEV ? s0 : T(0);
-  r.rho = S::DEV ? T(v.rho0_f) + s0 : s0;
+  r.rho = S::DEV ? pick<STORE>(v.rho0, v.rho0_f, v.rho0_df) + s0 : s0;
   const T is = T(kSqrt45) * rcp(r.rho);
   r.ux = jx * is;
   r.uy = jy * is;
@@ -299,8 +354,8 @@ template <class LAT, int STORE, class T = typename Storage<STORE>::T>
 __device__ __forceinline__ void bgk(const View& v, const Moments<T>& m, const T (&f)[LAT::Q], T (&out)[LAT::Q]) {
   using S = Storage<STORE>;
   constexpr int NP = (LAT::Q - 1) / 2;
-  const T om = S::DEV ? T(v.omega_f) : T(v.omega);
-  const T omc = S::DEV ? T(v.omc_f) : T(v.omc);
+  const T om = pick<STORE>(v.omega, v.omega_f, v.omega_df);
+  const T omc = pick<STORE>(v.omc, v.omc_f, v.omc_df);
   const T omb = T(kSqrt2) * om;
   auto A_of = [&](T wq, T t) -> T {
     const T ow = om * (S::SCALED ? T(1) : wq);
@@ -314,7 +369,7 @@ __device__ __forceinline__ void bgk(const View& v, const Moments<T>& m, const T 
     const T wq = T(LAT::w(q));
     const T cu = cdot<T>(LAT::c(q, 0), LAT::c(q, 1), LAT::c(q, 2), m.ux, m.uy, m.uz);
     const T A = A_of(wq, fma(cu, cu, m.k));
-    const T B = ((S::SCALED ? T(1) : wq) * m.rho) * fma(omb, cu, cg3_of<S::DEV, T>(v, q));
+    const T B = ((S::SCALED ? T(1) : wq) * m.rho) * fma(omb, cu, cg3_of<STORE>(v, q));
     out[q] = fma(omc, f[q], A + B);
     out[q + 1] = fma(omc, f[q + 1], A - B);
   }
@@ -354,7 +409,17 @@ struct Kin {
 template <int STORE>
 __device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& v, const int q) {
   Kin<typename Storage<STORE>::T> k;
-  if constexpr (Storage<STORE>::DEV) {
+  if constexpr (STORE == LBM_IMB_STORE_F64DEV) {
+    // 32-float record: high parts, nearest node, then the low parts
+    const float4* kp = reinterpret_cast<const float4*>(v.kin) + 8 * q;
+    const float4 fr = __ldg(kp), vp = __ldg(kp + 2), wp = __ldg(kp + 3);
+    const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
+    const float4 frl = __ldg(kp + 4), vpl = __ldg(kp + 6), wpl = __ldg(kp + 7);
+    k.c[0] = DF(fr.x, frl.x); k.c[1] = DF(fr.y, frl.y); k.c[2] = DF(fr.z, frl.z);
+    k.ic[0] = ir.x; k.ic[1] = ir.y; k.ic[2] = ir.z;
+    k.vel[0] = DF(vp.x, vpl.x); k.vel[1] = DF(vp.y, vpl.y); k.vel[2] = DF(vp.z, vpl.z);
+    k.w[0] = DF(wp.x, wpl.x); k.w[1] = DF(wp.y, wpl.y); k.w[2] = DF(wp.z, wpl.z);
+  } else if constexpr (Storage<STORE>::DEV) {
     const float4* kp = reinterpret_cast<const float4*>(v.kin) + 4 * q;
     const float4 fr = __ldg(kp);
     const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
@@ -381,7 +446,11 @@ __device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& 
 template <bool D3, typename PT>
 __device__ __forceinline__ void node_rel(const View& v, const Kin<PT>& k, const int x, const int y, const int z,
                                          PT (&r)[3], PT (&V)[3]) {
-  if constexpr (sizeof(PT) == 4) {
+  if constexpr (std::is_same<PT, DF>::value) {
+    r[0] = min_image_df(DF(float(x - k.ic[0])) - k.c[0], v.nx, true);
+    r[1] = min_image_df(DF(float(y + v.ygo - k.ic[1])) - k.c[1], v.ny_glob, !v.wall_y);
+    r[2] = D3 ? min_image_df(DF(float(z - k.ic[2])) - k.c[2], v.nz, true) : DF(0.f);
+  } else if constexpr (sizeof(PT) == 4) {
     r[0] = min_image_f(float(x - k.ic[0]) - k.c[0], v.nx, true);
     r[1] = min_image_f(float(y + v.ygo - k.ic[1]) - k.c[1], v.ny_glob, !v.wall_y);
     r[2] = D3 ? min_image_f(float(z - k.ic[2]) - k.c[2], v.nz, true) : 0.f;
@@ -421,8 +490,8 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   constexpr int NP = (Q - 1) / 2;
   constexpr bool D3 = LAT::DIM == 3;
   constexpr int K = kMaxOwners;
-  const T om = S::DEV ? T(v.omega_f) : T(v.omega);
-  const T tau_t = S::DEV ? T(v.tau_f) : T(v.tau);
+  const T om = pick<STORE>(v.omega, v.omega_f, v.omega_df);
+  const T tau_t = pick<STORE>(v.tau, v.tau_f, v.tau_df);
 
   // owners, sorted by id with empty slots last, so that V_S sums in particle
   // order.  Slots fill in order, so the taken ones are a prefix; all four
@@ -472,7 +541,7 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
       const Kin<PT> kq = load_kin<STORE>(v, q);
       PT V[3];
       node_rel<D3>(v, kq, xx, y, z, rk[k], V);
-      const PT e = (PT)eo[k];
+      const PT e = to_pt<PT>(eo[k]);
       if (k == 0) {
         V1x = V[0];
         V1y = V[1];
@@ -533,7 +602,7 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
     const T gp = f[q] - (A + B), gm = f[q + 1] - (A - B);
     const T dA = W * fma(cv, cv, fma(-cu, cu, dk));
     const T E = (gm - gp) + Wb * (cv - cu);  // D + dB
-    const T Fq = fq_of<S::DEV, T>(v, q) * rho;
+    const T Fq = fq_of<STORE>(v, q) * rho;
     res[q] = fma(beta, E + dA, fma(cfac, gp, f[q] + Fq));
     res[q + 1] = fma(beta, dA - E, fma(cfac, gm, f[q + 1] - Fq));
     // Omega^S_q - Omega^S_{-q} = 2 E, and c_{q+1} = -c_q
@@ -556,7 +625,7 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
 #pragma unroll
   for (int k = 0; k < K; k++) {
     if (any && k < no) {
-      const PT a = no == 1 ? PT(1) : PT(eo[k]) * inv_esum;
+      const PT a = no == 1 ? PT(1) : to_pt<PT>(eo[k]) * inv_esum;
       const PT p0 = a * m0, p1 = a * m1, p2 = a * m2;
       const PT F0 = -p0, F1 = -p1, F2 = -p2;
       const PT T0 = -(rk[k][1] * p2 - rk[k][2] * p1);
@@ -567,14 +636,14 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
         val[3] = T0; val[4] = T1; val[5] = T2;
       } else {
         const int q = own[k];
-        atomicAdd(v.ff + 3 * q, (double)F0);
-        atomicAdd(v.ff + 3 * q + 1, (double)F1);
-        if (D3) atomicAdd(v.ff + 3 * q + 2, (double)F2);
+        atomicAdd(v.ff + 3 * q, to_double(F0));
+        atomicAdd(v.ff + 3 * q + 1, to_double(F1));
+        if (D3) atomicAdd(v.ff + 3 * q + 2, to_double(F2));
         if (D3) {
-          atomicAdd(v.tf + 3 * q, (double)T0);
-          atomicAdd(v.tf + 3 * q + 1, (double)T1);
+          atomicAdd(v.tf + 3 * q, to_double(T0));
+          atomicAdd(v.tf + 3 * q + 1, to_double(T1));
         }
-        atomicAdd(v.tf + 3 * q + 2, (double)T2);
+        atomicAdd(v.tf + 3 * q + 2, to_double(T2));
       }
     }
   }
@@ -639,6 +708,20 @@ __device__ __forceinline__ void queue_flush(const View& v, const WarpQueue<STORE
   imb_core<LAT, STORE>(v, xy & 0xffff, xy >> 16, wq.z[s], wq.n[s], mine, f, m);
 }
 
+// the double-FP32 update of covered nodes is long: one out-of-line copy keeps
+// the instruction footprint of the kernel small
+template <class LAT, int STORE>
+__device__ __noinline__ void queue_flush_call(const View& v, const WarpQueue<STORE>& wq, const int count,
+                                              const int lane) {
+  queue_flush<LAT, STORE>(v, wq, count, lane);
+}
+template <class LAT, int STORE>
+__device__ __forceinline__ void flush_queue(const View& v, const WarpQueue<STORE>& wq, const int count,
+                                            const int lane) {
+  if constexpr (STORE == LBM_IMB_STORE_F64DEV) queue_flush_call<LAT, STORE>(v, wq, count, lane);
+  else queue_flush<LAT, STORE>(v, wq, count, lane);
+}
+
 // One lane's node of the warp's row segment, populations f already pulled;
 // cnt is the warp's queue length (warp-uniform).
 template <class LAT, int STORE>
@@ -667,7 +750,7 @@ __device__ __forceinline__ void fused_core(const View& v, const int xx, const in
   cnt += __popc(b);
   __syncwarp();
   if (cnt >= 32) {
-    queue_flush<LAT, STORE>(v, wq, 32, lane);
+    flush_queue<LAT, STORE>(v, wq, 32, lane);
     __syncwarp();
     if (lane < cnt - 32) {
 #pragma unroll
@@ -921,7 +1004,7 @@ __device__ __forceinline__ void pair_node(const View& v, const int x, const int 
 // drain a warp's queue (at the end of its segments)
 template <class LAT, int STORE>
 __device__ __forceinline__ void queue_drain(const View& v, const WarpQueue<STORE>& wq, int& cnt, const int lane) {
-  if (cnt > 0) queue_flush<LAT, STORE>(v, wq, cnt, lane);
+  if (cnt > 0) flush_queue<LAT, STORE>(v, wq, cnt, lane);
   cnt = 0;
   __syncwarp();
 }

@@ -399,30 +399,47 @@ static void launch_pair(const View& v, cudaStream_t s) {
 //   9  the same, 4 CTAs per SM
 template <class LAT, int STORE>
 static void dispatch(const View& v, cudaStream_t s) {
-  switch (v.collide_variant) {
-    case 1: launch_fused<LAT, STORE, 8, false>(v, s); break;
-    case 2:
-      if (STORE != LBM_IMB_STORE_F64) launch_tma<LAT, STORE>(v, s);
-      else launch_fused<LAT, STORE, 4, false>(v, s);
-      break;
-    case 3: launch_fused<LAT, STORE, 6, false>(v, s); break;
-    case 4: launch_fused<LAT, STORE, 4, true>(v, s); break;
-    case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
-    case 6: launch_packed<LAT, STORE, 8>(v, s); break;
-    case 7: launch_packed<LAT, STORE, 5>(v, s); break;
-    case 8: launch_pair<LAT, STORE, 6>(v, s); break;
-    case 9: launch_pair<LAT, STORE, 4>(v, s); break;
-    default: launch_fused<LAT, STORE, 4, false>(v, s);
+  if constexpr (STORE == LBM_IMB_STORE_F64DEV) {
+    // the persistent fused forms, with the register budgets the pair
+    // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
+    // prefetching form at 2 and 3), and the TMA-pipelined form (2); the
+    // other numbers use 0
+    switch (v.collide_variant) {
+      case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
+      case 2: launch_tma<LAT, STORE>(v, s); break;
+      case 3: launch_fused<LAT, STORE, 3, false>(v, s); break;
+      case 4: launch_fused<LAT, STORE, 2, true>(v, s); break;
+      case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
+      default: launch_fused<LAT, STORE, 4, false>(v, s);
+    }
+  } else {
+    switch (v.collide_variant) {
+      case 1: launch_fused<LAT, STORE, 8, false>(v, s); break;
+      case 2:
+        if (STORE != LBM_IMB_STORE_F64) launch_tma<LAT, STORE>(v, s);
+        else launch_fused<LAT, STORE, 4, false>(v, s);
+        break;
+      case 3: launch_fused<LAT, STORE, 6, false>(v, s); break;
+      case 4: launch_fused<LAT, STORE, 4, true>(v, s); break;
+      case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
+      case 6: launch_packed<LAT, STORE, 8>(v, s); break;
+      case 7: launch_packed<LAT, STORE, 5>(v, s); break;
+      case 8: launch_pair<LAT, STORE, 6>(v, s); break;
+      case 9: launch_pair<LAT, STORE, 4>(v, s); break;
+      default: launch_fused<LAT, STORE, 4, false>(v, s);
+    }
   }
 }
 
 void launch_collide(const View& v, cudaStream_t s) {
   if (v.dim == 2) {
     if (v.storage == LBM_IMB_STORE_F64) dispatch<D2Q9, LBM_IMB_STORE_F64>(v, s);
+    else if (v.storage == LBM_IMB_STORE_F64DEV) dispatch<D2Q9, LBM_IMB_STORE_F64DEV>(v, s);
     else if (v.storage == LBM_IMB_STORE_F32DEV) dispatch<D2Q9, LBM_IMB_STORE_F32DEV>(v, s);
     else dispatch<D2Q9, LBM_IMB_STORE_F16DEV>(v, s);
   } else {
     if (v.storage == LBM_IMB_STORE_F64) dispatch<D3Q19, LBM_IMB_STORE_F64>(v, s);
+    else if (v.storage == LBM_IMB_STORE_F64DEV) dispatch<D3Q19, LBM_IMB_STORE_F64DEV>(v, s);
     else if (v.storage == LBM_IMB_STORE_F32DEV) dispatch<D3Q19, LBM_IMB_STORE_F32DEV>(v, s);
     else dispatch<D3Q19, LBM_IMB_STORE_F16DEV>(v, s);
   }

@@ -87,7 +87,7 @@ cudaError_t launch_eps_table_build(int dim, double R, float* tab, cudaStream_t s
 }
 
 int eps_raster_smem_bytes(int dim, int storage, double rmax) {
-  const int esz = storage == LBM_IMB_STORE_F64 ? 8 : 4;
+  const int esz = fp64_eps(storage) ? 8 : 4;
   const long long bytes = raster_bytes(dim, esz, rmax);
   if (bytes > 200 * 1024) return -1;
   return (int)bytes;
@@ -108,10 +108,10 @@ void launch_eps_raster(const View& v, int smem_bytes, cudaStream_t s) {
   if (v.np <= 0) return;
   const RasterSmem cap = raster_caps(v.dim, v.rmax_bins);
   if (v.dim == 2) {
-    if (v.storage == LBM_IMB_STORE_F64) raster_t<2, double>(v, cap, smem_bytes, s);
+    if (fp64_eps(v.storage)) raster_t<2, double>(v, cap, smem_bytes, s);
     else raster_t<2, float>(v, cap, smem_bytes, s);
   } else {
-    if (v.storage == LBM_IMB_STORE_F64) raster_t<3, double>(v, cap, smem_bytes, s);
+    if (fp64_eps(v.storage)) raster_t<3, double>(v, cap, smem_bytes, s);
     else raster_t<3, float>(v, cap, smem_bytes, s);
   }
 }

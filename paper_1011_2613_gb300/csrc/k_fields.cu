@@ -2,6 +2,7 @@
 // global sums.  The fields are the moments of the populations the next
 // collision sees (the stored post-collision state pulled one step, as in K2),
 // with the fluid velocity u = sum_i f_i c_i / rho + g_f / 2.
+#include "dev_df.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -10,12 +11,14 @@ namespace lbm {
 __device__ __forceinline__ double stored_to_f(const void* f, int storage, long long i, double w,
                                               double rho0) {
   if (storage == LBM_IMB_STORE_F64) return static_cast<const double*>(f)[i];
+  if (storage == LBM_IMB_STORE_F64DEV) return w * rho0 + static_cast<const double*>(f)[i];
   if (storage == LBM_IMB_STORE_F32DEV) return w * rho0 + (double)static_cast<const float*>(f)[i];
   return w * rho0 + w * (double)__half2float(static_cast<const __half*>(f)[i]);
 }
 __device__ __forceinline__ void f_to_stored(void* f, int storage, long long i, double w, double rho0,
                                             double val) {
   if (storage == LBM_IMB_STORE_F64) static_cast<double*>(f)[i] = val;
+  else if (storage == LBM_IMB_STORE_F64DEV) static_cast<double*>(f)[i] = val - w * rho0;
   else if (storage == LBM_IMB_STORE_F32DEV) static_cast<float*>(f)[i] = (float)(val - w * rho0);
   else static_cast<__half*>(f)[i] = __float2half_rn((float)((val - w * rho0) / w));
 }
@@ -70,7 +73,7 @@ __global__ void fields_kernel(View v, long long row0, long long nrows, double* r
     double es = 0.0;
     for (int s = 0; s < kMaxOwners; s++) {
       if (v.own[s][n] < 0) break;
-      es += v.storage == LBM_IMB_STORE_F64 ? static_cast<const double*>(v.eps[s])[n]
+      es += fp64_eps(v.storage) ? static_cast<const double*>(v.eps[s])[n]
                                            : (double)static_cast<const float*>(v.eps[s])[n];
     }
     eps_out[dense] = es < 1.0 ? es : 1.0;
@@ -228,3 +231,25 @@ cudaError_t launch_halo_exchange(const SlabHalo& h, int parity, cudaStream_t s) 
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+__global__ void df_probe_kernel(const float* h, const float* l, const double* d, double* to_double,
+                                double* roundtrip, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  to_double[i] = df_to_bits(DF(h[i], l[i]));
+  roundtrip[i] = df_to_bits(df_from_bits(d[i]));
+}
+
+}  // namespace lbm
+
+extern "C" int lbm_imb_probe_df(const float* h, const float* l, const double* d, double* to_double,
+                                double* roundtrip, int64_t n, void* stream) {
+  if (!h || !l || !d || !to_double || !roundtrip || n < 0) return LBM_IMB_EINVAL;
+  if (n == 0) return LBM_IMB_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lbm::df_probe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h, l, d, to_double, roundtrip, (long long)n);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return LBM_IMB_ECUDA;
+  return LBM_IMB_OK;
+}

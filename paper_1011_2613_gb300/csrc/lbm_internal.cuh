@@ -109,6 +109,9 @@ struct View {
   // conversion runs on the FP64 pipe, so none happens per node)
   float tau_f, omega_f, rho0_f, omc_f;
   float fq_f[19], cg3_f[19];
+  // the same as FP32 pairs (high, low) for the double-FP32 collision
+  float tau_df[2], omega_df[2], rho0_df[2], omc_df[2];
+  float fq_df[19][2], cg3_df[19][2];
   int substeps;
   int collide_variant;  // kernel form of the collision
   // covered fractions: 0 exact closed forms, 1 the Eq. 6 table (one radius)
@@ -122,6 +125,15 @@ struct View {
 };
 
 static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
+
+// bytes of one stored population; whether the covered fractions (and the
+// rasteriser) are FP64
+__host__ __device__ inline int pop_bytes(int storage) {
+  return (storage == LBM_IMB_STORE_F64 || storage == LBM_IMB_STORE_F64DEV) ? 8
+         : storage == LBM_IMB_STORE_F32DEV                                 ? 4
+                                                                           : 2;
+}
+__host__ __device__ inline bool fp64_eps(int storage) { return storage == LBM_IMB_STORE_F64 || storage == LBM_IMB_STORE_F64DEV; }
 
 // ---------------------------------------------------------------------------
 // Launchers (one per kernel family; each in its own translation unit).

@@ -121,6 +121,8 @@ def lib():
             L.lbm_imb_batch_get_launch.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.lbm_imb_batch_set_barrier_test.restype = C.c_int
             L.lbm_imb_batch_set_barrier_test.argtypes = [C.c_void_p, C.c_int64, C.c_int]
+            L.lbm_imb_probe_df.restype = C.c_int
+            L.lbm_imb_probe_df.argtypes = [C.c_void_p] * 5 + [C.c_int64, C.c_void_p]
             L.lbm_imb_probe_atan2q1.restype = C.c_int
             L.lbm_imb_probe_atan2q1.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                                 C.c_void_p]
@@ -460,6 +462,22 @@ def probe_atan2q1(y, x):
     _check(lib().lbm_imb_probe_atan2q1(y.data_ptr(), x.data_ptr(), fast.data_ptr(), ref.data_ptr(), y.numel(),
                                         s.cuda_stream), "lbm_imb_probe_atan2q1")
     return fast, ref
+
+
+def probe_df(h, l, d):
+    """FP64 <-> FP32-pair conversions of the double-FP32 storage on device
+    tensors: h, l float32 (the pairs), d float64 (same length); returns
+    (FP64 value of each pair, d split and converted back)."""
+    import torch
+    h, l, d = h.contiguous(), l.contiguous(), d.contiguous()
+    to_double = torch.empty(h.numel(), dtype=torch.float64, device=h.device)
+    roundtrip = torch.empty(d.numel(), dtype=torch.float64, device=d.device)
+    if h.numel() != d.numel() or l.numel() != h.numel():
+        raise ValueError("h, l and d must have the same length")
+    s = torch.cuda.current_stream(h.device)
+    _check(lib().lbm_imb_probe_df(h.data_ptr(), l.data_ptr(), d.data_ptr(), to_double.data_ptr(),
+                                  roundtrip.data_ptr(), h.numel(), s.cuda_stream), "lbm_imb_probe_df")
+    return to_double, roundtrip
 
 
 def slab_rows(ny: int, nslabs: int):

@@ -3,7 +3,9 @@ oracle on the same seeded inputs.
 
 Tolerances (FP64 storage): populations 1e-10 relative, particle forces 1e-9
 relative to the largest force; the two sides differ only in rounding order
-(FMA contraction in the collision, atomic summation of forces).
+(FMA contraction in the collision, atomic summation of forces).  The FP64
+deviation storage with double-FP32 arithmetic ("f64dev") is held to the same
+tolerances: its 48-bit arithmetic on g = f - w rho0 is finer than FP64 on f.
 """
 import math
 
@@ -56,12 +58,14 @@ def run_pair(cfg, steps, f0=None):
 # ---------------------------------------------------------------------------
 # fluid only (beta = 0): pull streaming, walls, body force
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f64", "f64dev"])
 @pytest.mark.parametrize("dim,nx,ny,nz,wall", [(2, 37, 29, 1, 0), (2, 130, 64, 1, 1), (3, 19, 23, 17, 0),
                                                (3, 33, 20, 9, 1)])
-def test_fluid_parity_nonequilibrium(dim, nx, ny, nz, wall):
+def test_fluid_parity_nonequilibrium(dim, nx, ny, nz, wall, storage):
     """Ragged sizes (x not a multiple of the 32-wide warp or 128-wide CTA),
     non-equilibrium start, body force, periodic and wall boundaries."""
-    cfg = fluid_cfg(dim, nx, ny, nz, wall_y=wall, tau=0.71, g=(3e-5, -2e-5, 1e-5 if dim == 3 else 0))
+    cfg = fluid_cfg(dim, nx, ny, nz, wall_y=wall, tau=0.71, g=(3e-5, -2e-5, 1e-5 if dim == 3 else 0),
+                    storage=storage)
     f0 = I.random_populations(np.random.default_rng(5), cfg)
     gpu, ref = run_pair(cfg, 25, f0)
     assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
@@ -76,6 +80,18 @@ def test_population_roundtrip_exact():
     gpu = lbm().Simulation(cfg)
     gpu.set_populations(f0)
     assert np.array_equal(gpu.populations(), f0)
+
+
+def test_population_roundtrip_f64dev():
+    """f -> g = f - w rho0 -> f in FP64: one rounding of g and one of f (g
+    is exact where f is within a factor two of w rho0)."""
+    cfg = fluid_cfg(3, 21, 10, 7, storage="f64dev")
+    f0 = I.random_populations(np.random.default_rng(1), cfg)
+    gpu = lbm().Simulation(cfg)
+    gpu.set_populations(f0)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12).reshape(19, 1, 1, 1)
+    bound = 2.0 ** -53 * (np.abs(f0 - w * cfg.rho_fluid) + np.abs(f0))
+    assert np.all(np.abs(gpu.populations() - f0) <= bound)
 
 
 # ---------------------------------------------------------------------------
@@ -117,10 +133,11 @@ def test_eps_two_owner_cells_and_wrap():
 # ---------------------------------------------------------------------------
 # coupled LB-IMB-DEM
 # ---------------------------------------------------------------------------
-def test_config1_1000_steps():
+@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+def test_config1_1000_steps(storage):
     """D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6,
     1000 steps from rest: the parity target."""
-    cfg = I.config1()
+    cfg = I.config1().replace(storage=storage)
     gpu, ref = run_pair(cfg, 1000)
     assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
     pg, pr = gpu.particles(), ref.particles()
@@ -130,9 +147,11 @@ def test_config1_1000_steps():
     assert np.max(np.abs(pg["vel"] - pr["vel"])) < 1e-12
 
 
-def test_periodic_2d_moving_particles_with_contacts():
+@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+def test_periodic_2d_moving_particles_with_contacts(storage):
     """Fast disks in a dense periodic box collide within the run."""
-    cfg = I.periodic2d_config(nx=100, ny=72, phi=0.25, radius=4.0, seed=9, v0=0.03, density_ratio=4.0)
+    cfg = I.periodic2d_config(nx=100, ny=72, phi=0.25, radius=4.0, seed=9, v0=0.03, density_ratio=4.0,
+                              storage=storage)
     gpu, ref = run_pair(cfg, 150)
     pg, pr = gpu.particles(), ref.particles()
     assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
@@ -140,8 +159,9 @@ def test_periodic_2d_moving_particles_with_contacts():
     assert np.max(np.abs(pg["pos"] - pr["pos"])) < 1e-9
 
 
-def test_spinning_particles_torque_3d():
-    cfg = I.periodic3d_config(nx=28, ny=30, nz=26, phi=0.1, radius=3.75, seed=3, v0=0.01)
+@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+def test_spinning_particles_torque_3d(storage):
+    cfg = I.periodic3d_config(nx=28, ny=30, nz=26, phi=0.1, radius=3.75, seed=3, v0=0.01, storage=storage)
     cfg.omega = 0.003 * np.random.default_rng(2).standard_normal((cfg.n_particles, 3))
     gpu, ref = run_pair(cfg, 40)
     pg, pr = gpu.particles(), ref.particles()
@@ -151,9 +171,10 @@ def test_spinning_particles_torque_3d():
     assert np.max(np.abs(pg["omega"] - pr["omega"])) < 1e-12
 
 
-def test_config3_shape_channel_3d():
+@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+def test_config3_shape_channel_3d(storage):
     """Cut-down config 3 (D3Q19, walls in y, spheres R=3.75, ratio 1000)."""
-    cfg = I.config3_scaled(nx=40, ny=48, nz=36)
+    cfg = I.config3_scaled(nx=40, ny=48, nz=36, storage=storage)
     gpu, ref = run_pair(cfg, 30)
     pg, pr = gpu.particles(), ref.particles()
     assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
@@ -212,7 +233,7 @@ def test_reduced_storage_error(storage, tol_u, tol_f):
 # ---------------------------------------------------------------------------
 # kernel forms of the plain collision: the same populations
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f64", "f32dev", "f16dev"])
+@pytest.mark.parametrize("storage", ["f64", "f32dev", "f16dev", "f64dev"])
 @pytest.mark.parametrize("dim", [2, 3])
 def test_collide_variants_agree(dim, storage):
     """Every kernel form gives bitwise the populations of form 0 after one
@@ -231,7 +252,7 @@ def test_collide_variants_agree(dim, storage):
         sim.set_collide_variant(var)
         sim.step(1)
         assert np.array_equal(sim.populations(), f_base), f"variant {var}"
-        if storage == "f64":
+        if storage in ("f64", "f64dev"):
             ref = O.OracleSim(cfg)
             ref.step(12)
             sim.step(11)
