@@ -167,6 +167,47 @@ def cpu_oracle_sample(steps=4, nx=96, ny=128, nz=96, seed=3):
                       f"and parameters), {steps} steps, single thread, {dt:.1f} s"}
 
 
+# the paper's Table 3: 3D suspension sizes, steps/s on one C2050 and on one
+# E5520 core (FP64)
+TABLE3 = [((32, 64, 32), 1189.4, 65.71), ((64, 64, 64), 305.7, 16.44), ((64, 128, 64), 158.33, 8.167),
+          ((128, 128, 128), 40.25, 2.043), ((128, 256, 128), 22.23, 1.056)]
+
+
+def measure_table3(args, torch, gpu_steps=200, cpu_seconds=2.0):
+    """Table 3's five domain sizes at config-3 parameters (the paper states no
+    particle count): steps/s of the GPU path (graph-timed) and of the
+    single-threaded FP64 oracle (bounded: whole steps for about cpu_seconds
+    each), beside the paper's C2050 and E5520 columns."""
+    from oracle import oracle as O
+    from paper_1011_2613_gb300 import lbm as L
+    rows = []
+    for (nx, ny, nz), gpu_paper, cpu_paper in TABLE3:
+        cfg = I.config3_scaled(nx=nx, ny=ny, nz=nz, seed=3)
+        sim = L.Simulation(cfg)
+        pick_collide(sim, args)
+        sim.step(20)
+        sim.sync()
+        ms = time_graph_steps(sim, torch, gpu_steps)
+        sim.close()
+        del sim
+        ref = O.OracleSim(cfg)
+        n, t0 = 0, time.perf_counter()
+        while n == 0 or time.perf_counter() - t0 < cpu_seconds:
+            ref.step(1)
+            n += 1
+        dt = time.perf_counter() - t0
+        ref.close()
+        g = gpu_steps / (ms * 1e-3)
+        c = n / dt
+        rows.append({"size": f"{nx}x{ny}x{nz}", "particles": cfg.n_particles, "gpu_steps_s": g,
+                     "gpu_mlups": g * cfg.n_nodes / 1e6, "paper_c2050_steps_s": gpu_paper,
+                     "oracle_steps_s": c, "oracle_steps": n, "paper_e5520_steps_s": cpu_paper,
+                     "gpu_over_paper_gpu": g / gpu_paper, "gpu_over_oracle": g / c})
+    torch.cuda.empty_cache()
+    return {"rows": rows, "workload": "Table 3 sizes, D3Q19 channel, config-3 solid fraction 0.128, R=3.75, "
+                                      "density ratio 1000; oracle single-threaded FP64 C on the host"}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands on the host cores."""
     import torch.distributed as dist  # noqa: F401
@@ -530,6 +571,12 @@ def run_ours(args):
             variants["closure_d3q19"] = measure_closure(args, torch)
         except Exception as ex:
             variants["closure_d3q19"] = {"error": str(ex)}
+
+    if not args.no_variants and rank == 0 and cfg.storage == "f64" and not args.no_cpu:
+        try:
+            variants["table3_sizes"] = measure_table3(args, torch)
+        except Exception as ex:
+            variants["table3_sizes"] = {"error": str(ex)}
 
     if not args.no_variants and rank == 0 and cfg.storage == "f64":
         try:

@@ -81,10 +81,30 @@ struct Storage<LBM_IMB_STORE_F64DEV> {
   }
 };
 
+// FP64 arithmetic on the FP64 deviation: the covered-node update of the
+// double-FP32 storage runs on the FP64 pipe while the plain updates of other
+// warps use the FP32 pipe (internal id, not a storage of the C ABI)
+constexpr int kF64DevImb = 16;
+template <>
+struct Storage<kF64DevImb> {
+  using Elem = double;
+  using T = double;
+  using E = double;
+  static constexpr bool DEV = true;
+  static constexpr bool SCALED = false;
+  __device__ static __forceinline__ T load(const Elem* p, int i) { return __ldg(p + i); }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return p[i]; }
+  __device__ static __forceinline__ void store(Elem* p, int i, T v) { p[i] = v; }
+  __device__ static __forceinline__ void store2(Elem* p, Elem* r, int i, T a, T b) {
+    p[i] = a;
+    r[i] = b;
+  }
+};
+
 // a per-simulation constant in the arithmetic type of the storage
 template <int STORE>
 __device__ __forceinline__ typename Storage<STORE>::T pick(const double d, const float f, const float (&p)[2]) {
-  if constexpr (STORE == LBM_IMB_STORE_F64) return d;
+  if constexpr (STORE == LBM_IMB_STORE_F64 || STORE == kF64DevImb) return d;
   else if constexpr (STORE == LBM_IMB_STORE_F64DEV) return DF(p[0], p[1]);
   else return f;
 }
@@ -419,7 +439,7 @@ __device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& 
     k.ic[0] = ir.x; k.ic[1] = ir.y; k.ic[2] = ir.z;
     k.vel[0] = DF(vp.x, vpl.x); k.vel[1] = DF(vp.y, vpl.y); k.vel[2] = DF(vp.z, vpl.z);
     k.w[0] = DF(wp.x, wpl.x); k.w[1] = DF(wp.y, wpl.y); k.w[2] = DF(wp.z, wpl.z);
-  } else if constexpr (Storage<STORE>::DEV) {
+  } else if constexpr (std::is_same<typename Storage<STORE>::T, float>::value) {
     const float4* kp = reinterpret_cast<const float4*>(v.kin) + 4 * q;
     const float4 fr = __ldg(kp);
     const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
@@ -708,12 +728,32 @@ __device__ __forceinline__ void queue_flush(const View& v, const WarpQueue<STORE
   imb_core<LAT, STORE>(v, xy & 0xffff, xy >> 16, wq.z[s], wq.n[s], mine, f, m);
 }
 
-// the double-FP32 update of covered nodes is long: one out-of-line copy keeps
-// the instruction footprint of the kernel small
+// covered nodes of the double-FP32 storage: one out-of-line copy of an FP64
+// update (the pair arithmetic of this update is long and instruction-cache
+// bound; on the FP64 pipe it overlaps the FP32 work of the plain updates)
 template <class LAT, int STORE>
 __device__ __noinline__ void queue_flush_call(const View& v, const WarpQueue<STORE>& wq, const int count,
                                               const int lane) {
-  queue_flush<LAT, STORE>(v, wq, count, lane);
+  if constexpr (STORE == LBM_IMB_STORE_F64DEV) {
+    // queued pairs -> FP64, then the FP64 immersed-boundary update
+    const bool mine = lane < count;
+    const int s = mine ? lane : 0;
+    constexpr int Q = LAT::Q;
+    double f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) f[q] = df_to_bits(wq.f[q * kQueueCap + s]);
+    Moments<double> m;
+    m.rho = df_to_bits(wq.f[Q * kQueueCap + s]);
+    m.drho = df_to_bits(wq.f[(Q + 1) * kQueueCap + s]);
+    m.ux = df_to_bits(wq.f[(Q + 2) * kQueueCap + s]);
+    m.uy = df_to_bits(wq.f[(Q + 3) * kQueueCap + s]);
+    m.uz = df_to_bits(wq.f[(Q + 4) * kQueueCap + s]);
+    m.k = k_of<LAT, kF64DevImb>(m.ux, m.uy, m.uz);
+    const int xy = wq.xy[s];
+    imb_core<LAT, kF64DevImb>(v, xy & 0xffff, xy >> 16, wq.z[s], wq.n[s], mine, f, m);
+  } else {
+    queue_flush<LAT, STORE>(v, wq, count, lane);
+  }
 }
 template <class LAT, int STORE>
 __device__ __forceinline__ void flush_queue(const View& v, const WarpQueue<STORE>& wq, const int count,
