@@ -77,9 +77,9 @@ FP64_OPS = {3: (148.0, 225.0), 2: (68.0, 151.0)}
 # one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
 # case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
 # moves this many bytes per node times its node count (same solid fraction).
-TRAFFIC_B_PER_NODE = {("f64", 3): 375.3, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3, ("f64dev", 3): 387.4}
-ESZ = {"f64": 8, "f32dev": 4, "f16dev": 2, "f64dev": 8}  # bytes per stored population
-DTYPE = {"f64": "f64", "f32dev": "f32", "f16dev": "f32", "f64dev": "f32x2"}  # arithmetic type
+TRAFFIC_B_PER_NODE = {("f64", 3): 375.3, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3, ("dfdev", 3): 387.4}
+ESZ = {"f64": 8, "f32dev": 4, "f16dev": 2, "dfdev": 8}  # bytes per stored population
+DTYPE = {"f64": "f64", "f32dev": "f32", "f16dev": "f32", "dfdev": "f32x2"}  # arithmetic type
 
 # FP64 pipe peak: the nominal 1.25 TFLOP/s of the GB300 FP64 units, i.e.
 # 625 G FP64-pipe operations per second (a DFMA counts two flops, one slot)
@@ -91,7 +91,7 @@ def algorithmic_bytes_per_lup(cfg, owned_fraction):
     every node (4 B), read the covered fraction at owned nodes."""
     Q = 9 if cfg.dim == 2 else 19
     s = ESZ[cfg.storage]
-    se = 8 if cfg.storage in ("f64", "f64dev") else 4
+    se = 8 if cfg.storage in ("f64", "dfdev") else 4
     return 2 * Q * s + 4 + se * owned_fraction
 
 
@@ -548,7 +548,7 @@ def run_ours(args):
     if not args.no_variants and rank == 0 and cfg.storage == "f64":
         steps_done = tuned_steps + args.warmup + 2 * args.steps + (args.steps if e2e else 0)
         forms = [("f32dev", cfg.replace(storage="f32dev")), ("f16dev", cfg.replace(storage="f16dev")),
-                 ("f64dev", cfg.replace(storage="f64dev")),  # FP64 deviation, double-FP32 arithmetic
+                 ("dfdev", cfg.replace(storage="dfdev")),  # FP64 deviation, double-FP32 arithmetic
                  ("f64_eps_table", cfg.replace(eps_method=1))]  # Eq. 6 covered fractions
         for st, c in forms:
             try:
@@ -641,7 +641,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS))
-    ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev", "f64dev"])
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev", "dfdev"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--collide-variant", type=int, default=None,
                     help="fix the collide kernel form instead of autotuning it")

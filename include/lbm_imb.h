@@ -86,8 +86,9 @@ enum {
   LBM_IMB_STORE_F64 = 0,    /* FP64 populations, FP64 arithmetic */
   LBM_IMB_STORE_F32DEV = 1, /* FP32 storage of f_i - w_i rho0, FP32 arithmetic */
   LBM_IMB_STORE_F16DEV = 2, /* FP16 storage of (f_i - w_i rho0)/w_i, FP32 arithmetic */
-  LBM_IMB_STORE_F64DEV = 3  /* FP64 storage of f_i - w_i rho0, double-FP32 arithmetic (48-bit
-                               significands on the deviation: FP64 accuracy on f_i) */
+  LBM_IMB_STORE_DFDEV = 3   /* f_i - w_i rho0 as an unevaluated pair of FP32 numbers (8 bytes,
+                               48-bit significand: finer than FP64 on f_i); pair arithmetic
+                               for plain nodes, FP64 for covered nodes */
 };
 
 /* Problem statement: lattice, relaxation time, body force, particles with
@@ -383,8 +384,8 @@ int lbm_imb_mlp_probe_gemm(const uint16_t* a_host, const uint16_t* b_host, int N
  * elements is not supported.  EINVAL on null pointers or n < 0. */
 int lbm_imb_probe_atan2q1(const double* y, const double* x, double* fast, double* ref, int64_t n, void* stream);
 
-/* Test hook for the FP64 <-> FP32-pair conversions of the double-FP32
- * storage (LBM_IMB_STORE_F64DEV): for device arrays of n elements writes
+/* Test hook for the FP64 <-> FP32-pair conversions of the pair storage
+ * (LBM_IMB_STORE_DFDEV, covered nodes): for device arrays of n elements writes
  * to_double[i] = the FP64 value of the pair (h[i], l[i]) (|l| at most half
  * an FP32 ulp of h) and roundtrip[i] = d[i] split into a pair and converted
  * back, then synchronises the stream.  EINVAL on null pointers or n < 0. */

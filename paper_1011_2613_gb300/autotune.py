@@ -101,7 +101,7 @@ def tuned_batch(cfgs, device=None, path: str | None = None, steps: int = 3):
 
 COLLIDE_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9)
 # the double-FP32 storage has the persistent fused and TMA forms only
-COLLIDE_VARIANTS_BY_STORAGE = {"f64dev": (0, 1, 2, 3, 4, 5)}
+COLLIDE_VARIANTS_BY_STORAGE = {"dfdev": (0, 1, 2, 3, 4, 5)}
 
 
 def collide_variants(storage) -> tuple:

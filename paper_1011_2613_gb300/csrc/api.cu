@@ -515,7 +515,7 @@ static int batch_layout(const lbm_imb_config* cfgs, int n, BatchLayout* B) {
     if (c->dim != cfgs[0].dim || c->storage != cfgs[0].storage) return LBM_IMB_EINVAL;
     if (c->dem_substeps != 1) return LBM_IMB_EUNSUPPORTED;
     if (c->dem_skin != 0.0) return LBM_IMB_EUNSUPPORTED;
-    if (c->storage == LBM_IMB_STORE_F64DEV) return LBM_IMB_EUNSUPPORTED;
+    if (c->storage == LBM_IMB_STORE_DFDEV) return LBM_IMB_EUNSUPPORTED;
     B->member_off[i] = take(B->member[i].total);
   }
   B->total = o;

@@ -63,49 +63,63 @@ struct Storage<LBM_IMB_STORE_F16DEV> {
   }
 };
 
-// FP64 deviation g = f - w rho0, collided in double-FP32 arithmetic
-// (dev_df.cuh): FP64 accuracy with the arithmetic on the FP32 pipe
+// deviation g = f - w rho0 stored as an unevaluated FP32 pair (h, l) and
+// collided in pair arithmetic (dev_df.cuh): FP64 accuracy on f with the
+// arithmetic on the FP32 pipe; a store renormalises the pair
 template <>
-struct Storage<LBM_IMB_STORE_F64DEV> {
-  using Elem = double;
+struct Storage<LBM_IMB_STORE_DFDEV> {
+  using Elem = float2;
   using T = DF;
   using E = double;
   static constexpr bool DEV = true;
   static constexpr bool SCALED = false;
-  __device__ static __forceinline__ T load(const Elem* p, int i) { return df_from_bits(__ldg(p + i)); }
-  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return df_from_bits(p[i]); }
-  __device__ static __forceinline__ void store(Elem* p, int i, T v) { p[i] = df_to_bits(v); }
+  __device__ static __forceinline__ T load(const Elem* p, int i) {
+    const float2 w = __ldg(p + i);
+    return DF(w.x, w.y);
+  }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return DF(p[i].x, p[i].y); }
+  __device__ static __forceinline__ void store(Elem* p, int i, T v) {
+    const DF r = df_norm(v);
+    p[i] = make_float2(r.h, r.l);
+  }
   __device__ static __forceinline__ void store2(Elem* p, Elem* r, int i, T a, T b) {
-    p[i] = df_to_bits(a);
-    r[i] = df_to_bits(b);
+    store(p, i, a);
+    store(r, i, b);
   }
 };
 
-// FP64 arithmetic on the FP64 deviation: the covered-node update of the
-// double-FP32 storage runs on the FP64 pipe while the plain updates of other
-// warps use the FP32 pipe (internal id, not a storage of the C ABI)
-constexpr int kF64DevImb = 16;
+// FP64 arithmetic on the deviation of the pair storage: the covered-node
+// update runs on the FP64 pipe while the plain updates of other warps use
+// the FP32 pipe (internal id, not a storage of the C ABI); pairs <-> FP64 by
+// integer bit operations
+constexpr int kDfDevImb = 16;
 template <>
-struct Storage<kF64DevImb> {
-  using Elem = double;
+struct Storage<kDfDevImb> {
+  using Elem = float2;
   using T = double;
   using E = double;
   static constexpr bool DEV = true;
   static constexpr bool SCALED = false;
-  __device__ static __forceinline__ T load(const Elem* p, int i) { return __ldg(p + i); }
-  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return p[i]; }
-  __device__ static __forceinline__ void store(Elem* p, int i, T v) { p[i] = v; }
+  __device__ static __forceinline__ T load(const Elem* p, int i) {
+    const float2 w = __ldg(p + i);
+    return df_to_bits(DF(w.x, w.y));
+  }
+  __device__ static __forceinline__ T load_shared(const Elem* p, int i) { return df_to_bits(DF(p[i].x, p[i].y)); }
+  __device__ static __forceinline__ void store(Elem* p, int i, T v) {
+    const DF r = df_from_bits(v);
+    p[i] = make_float2(r.h, r.l);
+  }
   __device__ static __forceinline__ void store2(Elem* p, Elem* r, int i, T a, T b) {
-    p[i] = a;
-    r[i] = b;
+    store(p, i, a);
+    store(r, i, b);
   }
 };
 
 // a per-simulation constant in the arithmetic type of the storage
 template <int STORE>
 __device__ __forceinline__ typename Storage<STORE>::T pick(const double d, const float f, const float (&p)[2]) {
-  if constexpr (STORE == LBM_IMB_STORE_F64 || STORE == kF64DevImb) return d;
-  else if constexpr (STORE == LBM_IMB_STORE_F64DEV) return DF(p[0], p[1]);
+  if constexpr (STORE == LBM_IMB_STORE_F64 || STORE == kDfDevImb) return d;
+  else if constexpr (STORE == LBM_IMB_STORE_DFDEV) return DF(p[0], p[1]);
   else return f;
 }
 
@@ -429,7 +443,7 @@ struct Kin {
 template <int STORE>
 __device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& v, const int q) {
   Kin<typename Storage<STORE>::T> k;
-  if constexpr (STORE == LBM_IMB_STORE_F64DEV) {
+  if constexpr (STORE == LBM_IMB_STORE_DFDEV) {
     // 32-float record: high parts, nearest node, then the low parts
     const float4* kp = reinterpret_cast<const float4*>(v.kin) + 8 * q;
     const float4 fr = __ldg(kp), vp = __ldg(kp + 2), wp = __ldg(kp + 3);
@@ -734,7 +748,7 @@ __device__ __forceinline__ void queue_flush(const View& v, const WarpQueue<STORE
 template <class LAT, int STORE>
 __device__ __noinline__ void queue_flush_call(const View& v, const WarpQueue<STORE>& wq, const int count,
                                               const int lane) {
-  if constexpr (STORE == LBM_IMB_STORE_F64DEV) {
+  if constexpr (STORE == LBM_IMB_STORE_DFDEV) {
     // queued pairs -> FP64, then the FP64 immersed-boundary update
     const bool mine = lane < count;
     const int s = mine ? lane : 0;
@@ -748,9 +762,9 @@ __device__ __noinline__ void queue_flush_call(const View& v, const WarpQueue<STO
     m.ux = df_to_bits(wq.f[(Q + 2) * kQueueCap + s]);
     m.uy = df_to_bits(wq.f[(Q + 3) * kQueueCap + s]);
     m.uz = df_to_bits(wq.f[(Q + 4) * kQueueCap + s]);
-    m.k = k_of<LAT, kF64DevImb>(m.ux, m.uy, m.uz);
+    m.k = k_of<LAT, kDfDevImb>(m.ux, m.uy, m.uz);
     const int xy = wq.xy[s];
-    imb_core<LAT, kF64DevImb>(v, xy & 0xffff, xy >> 16, wq.z[s], wq.n[s], mine, f, m);
+    imb_core<LAT, kDfDevImb>(v, xy & 0xffff, xy >> 16, wq.z[s], wq.n[s], mine, f, m);
   } else {
     queue_flush<LAT, STORE>(v, wq, count, lane);
   }
@@ -758,7 +772,7 @@ __device__ __noinline__ void queue_flush_call(const View& v, const WarpQueue<STO
 template <class LAT, int STORE>
 __device__ __forceinline__ void flush_queue(const View& v, const WarpQueue<STORE>& wq, const int count,
                                             const int lane) {
-  if constexpr (STORE == LBM_IMB_STORE_F64DEV) queue_flush_call<LAT, STORE>(v, wq, count, lane);
+  if constexpr (STORE == LBM_IMB_STORE_DFDEV) queue_flush_call<LAT, STORE>(v, wq, count, lane);
   else queue_flush<LAT, STORE>(v, wq, count, lane);
 }
 

@@ -9,10 +9,11 @@
 // intrinsics, so the compiler neither contracts nor reorders them.
 //
 // Why: GB300 issues FP32 at 64 times its FP64 rate.  The collision works on
-// the deviation g = f - w rho0 (|g| is 1e-2 w or less), so 48 bits of g are
-// more than the 53 bits of f: the result is as accurate as the FP64 update
-// of f while no FP64 instruction runs per population.  The FP64 <-> pair
-// conversions of the stored values are integer bit operations.
+// the deviation g = f - w rho0 (|g| is 1e-2 w or less), stored as such a
+// pair, so 48 bits of g are more than the 53 bits of f: the plain update is
+// as accurate as the FP64 update of f while no FP64 instruction runs.  The
+// FP64 <-> pair conversions (for the FP64 update of covered nodes) are
+// integer bit operations.
 #pragma once
 #include <cuda_runtime.h>
 

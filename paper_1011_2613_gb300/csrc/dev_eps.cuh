@@ -91,7 +91,7 @@ __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, c
   // FP32 kinematics record of the particle for the reduced-precision
   // collision: position split into the nearest node (int) and the offset
   // from it (float), velocity and spin (float)
-  if (v.kin != nullptr && v.storage == LBM_IMB_STORE_F64DEV) {
+  if (v.kin != nullptr && v.storage == LBM_IMB_STORE_DFDEV) {
     // 32-float record for the double-FP32 collision: high parts of the
     // offset, velocity and spin, the nearest node, then the low parts
     const int d = lane & 3, part = lane >> 2;

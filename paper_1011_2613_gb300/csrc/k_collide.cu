@@ -399,7 +399,7 @@ static void launch_pair(const View& v, cudaStream_t s) {
 //   9  the same, 4 CTAs per SM
 template <class LAT, int STORE>
 static void dispatch(const View& v, cudaStream_t s) {
-  if constexpr (STORE == LBM_IMB_STORE_F64DEV) {
+  if constexpr (STORE == LBM_IMB_STORE_DFDEV) {
     // the persistent fused forms, with the register budgets the pair
     // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
     // prefetching form at 2 and 3), and the TMA-pipelined form (2); the
@@ -434,12 +434,12 @@ static void dispatch(const View& v, cudaStream_t s) {
 void launch_collide(const View& v, cudaStream_t s) {
   if (v.dim == 2) {
     if (v.storage == LBM_IMB_STORE_F64) dispatch<D2Q9, LBM_IMB_STORE_F64>(v, s);
-    else if (v.storage == LBM_IMB_STORE_F64DEV) dispatch<D2Q9, LBM_IMB_STORE_F64DEV>(v, s);
+    else if (v.storage == LBM_IMB_STORE_DFDEV) dispatch<D2Q9, LBM_IMB_STORE_DFDEV>(v, s);
     else if (v.storage == LBM_IMB_STORE_F32DEV) dispatch<D2Q9, LBM_IMB_STORE_F32DEV>(v, s);
     else dispatch<D2Q9, LBM_IMB_STORE_F16DEV>(v, s);
   } else {
     if (v.storage == LBM_IMB_STORE_F64) dispatch<D3Q19, LBM_IMB_STORE_F64>(v, s);
-    else if (v.storage == LBM_IMB_STORE_F64DEV) dispatch<D3Q19, LBM_IMB_STORE_F64DEV>(v, s);
+    else if (v.storage == LBM_IMB_STORE_DFDEV) dispatch<D3Q19, LBM_IMB_STORE_DFDEV>(v, s);
     else if (v.storage == LBM_IMB_STORE_F32DEV) dispatch<D3Q19, LBM_IMB_STORE_F32DEV>(v, s);
     else dispatch<D3Q19, LBM_IMB_STORE_F16DEV>(v, s);
   }

@@ -11,14 +11,21 @@ namespace lbm {
 __device__ __forceinline__ double stored_to_f(const void* f, int storage, long long i, double w,
                                               double rho0) {
   if (storage == LBM_IMB_STORE_F64) return static_cast<const double*>(f)[i];
-  if (storage == LBM_IMB_STORE_F64DEV) return w * rho0 + static_cast<const double*>(f)[i];
+  if (storage == LBM_IMB_STORE_DFDEV) {
+    const float2 p = static_cast<const float2*>(f)[i];
+    return w * rho0 + ((double)p.x + (double)p.y);
+  }
   if (storage == LBM_IMB_STORE_F32DEV) return w * rho0 + (double)static_cast<const float*>(f)[i];
   return w * rho0 + w * (double)__half2float(static_cast<const __half*>(f)[i]);
 }
 __device__ __forceinline__ void f_to_stored(void* f, int storage, long long i, double w, double rho0,
                                             double val) {
   if (storage == LBM_IMB_STORE_F64) static_cast<double*>(f)[i] = val;
-  else if (storage == LBM_IMB_STORE_F64DEV) static_cast<double*>(f)[i] = val - w * rho0;
+  else if (storage == LBM_IMB_STORE_DFDEV) {
+    const double g = val - w * rho0;
+    const float h = (float)g;
+    static_cast<float2*>(f)[i] = make_float2(h, (float)(g - (double)h));
+  }
   else if (storage == LBM_IMB_STORE_F32DEV) static_cast<float*>(f)[i] = (float)(val - w * rho0);
   else static_cast<__half*>(f)[i] = __float2half_rn((float)((val - w * rho0) / w));
 }

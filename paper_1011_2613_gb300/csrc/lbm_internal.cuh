@@ -129,11 +129,11 @@ static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
 // bytes of one stored population; whether the covered fractions (and the
 // rasteriser) are FP64
 __host__ __device__ inline int pop_bytes(int storage) {
-  return (storage == LBM_IMB_STORE_F64 || storage == LBM_IMB_STORE_F64DEV) ? 8
+  return (storage == LBM_IMB_STORE_F64 || storage == LBM_IMB_STORE_DFDEV) ? 8
          : storage == LBM_IMB_STORE_F32DEV                                 ? 4
                                                                            : 2;
 }
-__host__ __device__ inline bool fp64_eps(int storage) { return storage == LBM_IMB_STORE_F64 || storage == LBM_IMB_STORE_F64DEV; }
+__host__ __device__ inline bool fp64_eps(int storage) { return storage == LBM_IMB_STORE_F64 || storage == LBM_IMB_STORE_DFDEV; }
 
 // ---------------------------------------------------------------------------
 // Launchers (one per kernel family; each in its own translation unit).

@@ -25,7 +25,7 @@ from typing import Optional
 
 import numpy as np
 
-STORAGE = {"f64": 0, "f32dev": 1, "f16dev": 2, "f64dev": 3}
+STORAGE = {"f64": 0, "f32dev": 1, "f16dev": 2, "dfdev": 3}
 
 
 @dataclasses.dataclass

@@ -25,7 +25,7 @@ CASES = {
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cfg3s", choices=sorted(CASES))
-    ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev", "f64dev"])
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev", "dfdev"])
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--no-particles", action="store_true")
     ap.add_argument("--steps", type=int, default=3)

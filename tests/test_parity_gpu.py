@@ -4,7 +4,7 @@ oracle on the same seeded inputs.
 Tolerances (FP64 storage): populations 1e-10 relative, particle forces 1e-9
 relative to the largest force; the two sides differ only in rounding order
 (FMA contraction in the collision, atomic summation of forces).  The FP64
-deviation storage with double-FP32 arithmetic ("f64dev") is held to the same
+deviation storage with double-FP32 arithmetic ("dfdev") is held to the same
 tolerances: its 48-bit arithmetic on g = f - w rho0 is finer than FP64 on f.
 """
 import math
@@ -58,7 +58,7 @@ def run_pair(cfg, steps, f0=None):
 # ---------------------------------------------------------------------------
 # fluid only (beta = 0): pull streaming, walls, body force
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+@pytest.mark.parametrize("storage", ["f64", "dfdev"])
 @pytest.mark.parametrize("dim,nx,ny,nz,wall", [(2, 37, 29, 1, 0), (2, 130, 64, 1, 1), (3, 19, 23, 17, 0),
                                                (3, 33, 20, 9, 1)])
 def test_fluid_parity_nonequilibrium(dim, nx, ny, nz, wall, storage):
@@ -82,15 +82,16 @@ def test_population_roundtrip_exact():
     assert np.array_equal(gpu.populations(), f0)
 
 
-def test_population_roundtrip_f64dev():
-    """f -> g = f - w rho0 -> f in FP64: one rounding of g and one of f (g
-    is exact where f is within a factor two of w rho0)."""
-    cfg = fluid_cfg(3, 21, 10, 7, storage="f64dev")
+def test_population_roundtrip_dfdev():
+    """f -> g = f - w rho0 -> FP32 pair (48 bits) -> f in FP64: g rounded
+    to 48 bits, then one rounding of g and one of f."""
+    cfg = fluid_cfg(3, 21, 10, 7, storage="dfdev")
     f0 = I.random_populations(np.random.default_rng(1), cfg)
     gpu = lbm().Simulation(cfg)
     gpu.set_populations(f0)
     w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12).reshape(19, 1, 1, 1)
-    bound = 2.0 ** -53 * (np.abs(f0 - w * cfg.rho_fluid) + np.abs(f0))
+    g = np.abs(f0 - w * cfg.rho_fluid)
+    bound = 2.0 ** -48 * g + 2.0 ** -53 * (g + np.abs(f0))
     assert np.all(np.abs(gpu.populations() - f0) <= bound)
 
 
@@ -133,7 +134,7 @@ def test_eps_two_owner_cells_and_wrap():
 # ---------------------------------------------------------------------------
 # coupled LB-IMB-DEM
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+@pytest.mark.parametrize("storage", ["f64", "dfdev"])
 def test_config1_1000_steps(storage):
     """D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6,
     1000 steps from rest: the parity target."""
@@ -147,7 +148,7 @@ def test_config1_1000_steps(storage):
     assert np.max(np.abs(pg["vel"] - pr["vel"])) < 1e-12
 
 
-@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+@pytest.mark.parametrize("storage", ["f64", "dfdev"])
 def test_periodic_2d_moving_particles_with_contacts(storage):
     """Fast disks in a dense periodic box collide within the run."""
     cfg = I.periodic2d_config(nx=100, ny=72, phi=0.25, radius=4.0, seed=9, v0=0.03, density_ratio=4.0,
@@ -159,7 +160,7 @@ def test_periodic_2d_moving_particles_with_contacts(storage):
     assert np.max(np.abs(pg["pos"] - pr["pos"])) < 1e-9
 
 
-@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+@pytest.mark.parametrize("storage", ["f64", "dfdev"])
 def test_spinning_particles_torque_3d(storage):
     cfg = I.periodic3d_config(nx=28, ny=30, nz=26, phi=0.1, radius=3.75, seed=3, v0=0.01, storage=storage)
     cfg.omega = 0.003 * np.random.default_rng(2).standard_normal((cfg.n_particles, 3))
@@ -171,7 +172,7 @@ def test_spinning_particles_torque_3d(storage):
     assert np.max(np.abs(pg["omega"] - pr["omega"])) < 1e-12
 
 
-@pytest.mark.parametrize("storage", ["f64", "f64dev"])
+@pytest.mark.parametrize("storage", ["f64", "dfdev"])
 def test_config3_shape_channel_3d(storage):
     """Cut-down config 3 (D3Q19, walls in y, spheres R=3.75, ratio 1000)."""
     cfg = I.config3_scaled(nx=40, ny=48, nz=36, storage=storage)
@@ -233,7 +234,7 @@ def test_reduced_storage_error(storage, tol_u, tol_f):
 # ---------------------------------------------------------------------------
 # kernel forms of the plain collision: the same populations
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f64", "f32dev", "f16dev", "f64dev"])
+@pytest.mark.parametrize("storage", ["f64", "f32dev", "f16dev", "dfdev"])
 @pytest.mark.parametrize("dim", [2, 3])
 def test_collide_variants_agree(dim, storage):
     """Every kernel form gives bitwise the populations of form 0 after one
@@ -252,7 +253,7 @@ def test_collide_variants_agree(dim, storage):
         sim.set_collide_variant(var)
         sim.step(1)
         assert np.array_equal(sim.populations(), f_base), f"variant {var}"
-        if storage in ("f64", "f64dev"):
+        if storage in ("f64", "dfdev"):
             ref = O.OracleSim(cfg)
             ref.step(12)
             sim.step(11)
