@@ -191,6 +191,11 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
  *   thread with paired FP32 arithmetic and aligned pair loads/stores
  *   (reduced-precision storages only; FP64 falls back to 0; 6 CTAs per SM),
  *   9 the same with 4 CTAs per SM.
+ * The pair storage (LBM_IMB_STORE_DFDEV) has its own set: 0, 3 and 1 the
+ * persistent queue form with budgets for 4, 3 and 2 CTAs per SM, 5 and 4
+ * the pulled-ahead form with 3 and 2, 2 the TMA form, 6 the split form
+ * (plain nodes in one launch, then the covered nodes listed by the
+ * rasteriser in a second, in FP64); 7, 8 and 9 fall back to 0.
  * Returns EINVAL outside 0..9.  Not for batch members or batches. */
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
 

@@ -100,8 +100,9 @@ def tuned_batch(cfgs, device=None, path: str | None = None, steps: int = 3):
 
 
 COLLIDE_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9)
-# the double-FP32 storage has the persistent fused and TMA forms only
-COLLIDE_VARIANTS_BY_STORAGE = {"dfdev": (0, 1, 2, 3, 4, 5)}
+# the pair storage has the persistent fused forms, the TMA form and the
+# split form (6)
+COLLIDE_VARIANTS_BY_STORAGE = {"dfdev": (0, 1, 2, 3, 4, 5, 6)}
 
 
 def collide_variants(storage) -> tuple:

@@ -61,6 +61,7 @@ __device__ __forceinline__ bool rows_meet_slab(const View& v, const int ly, cons
 
 __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, const int lane,
                                                    const bool zero_forces) {
+  if (p == 0 && lane == 0 && v.cov_count != nullptr) *v.cov_count = 0;  // the list is rebuilt by the raster
   const int* box = v.lo + 6 * p;
   const int lx = box[0], ly = box[1], lz = box[2];
   const int ex = box[3], ey = box[4], ez = box[5];
@@ -151,6 +152,15 @@ __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, c
 struct RasterSmem {
   int tab_cap, pair_cap, cell_cap;
 };
+
+// bytes of the tables before the covered-node list (the list, cell_cap ints,
+// comes last; the table form keeps only the list)
+__host__ __device__ inline int raster_list_offset(const RasterSmem c, int esz) {
+  const long long b = (long long)c.tab_cap * esz + 12LL * c.pair_cap * esz + (long long)c.tab_cap * 4 +
+                      (long long)c.cell_cap * 4 + c.tab_cap;
+  return (int)((b + 15) & ~15LL);
+}
+
 
 template <typename T>
 __device__ __forceinline__ int classify_cell(const T (*bnd)[64], const float (*bndf)[64], const int idx[3],
@@ -385,7 +395,10 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ T val[3][64];  // value lists
   __shared__ T ax_s[2][64], ax_psi[2][64];  // 2D per-axis tables
   __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
-  __shared__ int n_part, n_need;
+  __shared__ int n_part, n_need, n_cov, cov_base;
+  // nodes whose first owner slot this particle claims (split collision)
+  const bool want_list = v.cov_list != nullptr && v.collide_variant == kCollideSplit;
+  int* s_cov = reinterpret_cast<int*>(smem + (TABLE ? 0 : raster_list_offset(cap, (int)sizeof(T))));
   const double R2 = R64 * R64;
   const float R2f = (float)R2;
 
@@ -396,6 +409,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     }
     n_part = 0;
     n_need = 0;
+    n_cov = 0;
   }
   if (!rows_meet_slab(v, lo[1], ne[1])) return;  // another slab's particle (block-uniform)
   for (int t = threadIdx.x; t < 3 * 64; t += blockDim.x) {
@@ -428,10 +442,19 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     for (int s = 0; s < kMaxOwners; s++) {
       if (atomicCAS(&v.own[s][n], -1, p) == -1) {
         static_cast<T*>(v.eps[s])[n] = e;
+        if (s == 0 && want_list) s_cov[atomicAdd(&n_cov, 1)] = (int)n;
         return;
       }
     }
     atomicOr(v.err, ERR_OWNERS);
+  };
+  // one reservation per particle in the global list, then a block copy
+  auto flush_list = [&]() {
+    if (!want_list) return;
+    __syncthreads();
+    if (threadIdx.x == 0) cov_base = n_cov > 0 ? atomicAdd(v.cov_count, n_cov) : 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_cov; i += blockDim.x) v.cov_list[cov_base + i] = s_cov[i];
   };
   const FastDiv3 cdiv(ne[0], ne[1]);
   for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
@@ -465,7 +488,10 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
             need[(zs[(s >> 2) & 1] * ty + ys[(s >> 1) & 1]) * tx + xs[s & 1]] = 1;
         }
   }
-  if constexpr (TABLE) return;
+  if constexpr (TABLE) {
+    flush_list();
+    return;
+  }
   // per-axis (2D) or per-pair (3D) angle tables
   const T hpi = T(1.57079632679489661923);
   if (DIM == 2) {
@@ -561,6 +587,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     const T e = sum < T(0) ? T(0) : (sum > T(1) ? T(1) : sum);
     if (e > T(0)) claim(idx[0], idx[1], idx[2], e);
   }
+  flush_list();
 }
 
 static inline RasterSmem raster_caps(int dim, double rmax) {
@@ -575,9 +602,9 @@ static inline RasterSmem raster_caps(int dim, double rmax) {
 
 static inline long long raster_bytes(int dim, int esz, double rmax) {
   const RasterSmem c = raster_caps(dim, rmax);
-  long long b = (long long)c.tab_cap * esz + 12LL * c.pair_cap * esz + (long long)c.tab_cap * 4 +
-                (long long)c.cell_cap * 4 + c.tab_cap;
-  return (b + 15) & ~15LL;
+  return (long long)raster_list_offset(c, esz) + (long long)c.cell_cap * 4;
 }
+
+static inline long long raster_list_bytes(int dim, double rmax) { return (long long)raster_caps(dim, rmax).cell_cap * 4; }
 
 }  // namespace lbm

@@ -64,6 +64,61 @@ __global__ void __launch_bounds__(128, MINB) collide_kernel(View v, int ntiles) 
   queue_drain<LAT, STORE>(v, wq, cnt, lane);
 }
 
+// Split form of the pair storage, plain part: persistent row tiles as in
+// form 0; covered nodes are skipped (the rasteriser listed them).
+template <class LAT, int STORE>
+__global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntiles) {
+  using T = typename Storage<STORE>::T;
+  const int nx = v.nx, nz = v.nz;
+  (void)ntiles;
+  for (TileWalk w(blockIdx.x, gridDim.x, (nx + 127) / 128, v.ny_c); w.z < nz; w.next()) {
+    const int x = w.xt * 128 + (int)threadIdx.x;
+    const bool active = x < nx;
+    const int xx = active ? x : nx - 1, y = v.y0 + w.y;
+    const int n = (w.z * v.ny + y) * v.pitch + xx;
+    const bool covered = v.own[0][n] >= 0;
+    if (__all_sync(0xffffffffu, covered || !active)) continue;  // the whole segment is covered
+    T f[LAT::Q];
+    pull<LAT, STORE>(v, xx, y, w.z, n, active, f);
+    plain_core<LAT, STORE>(v, n, active && !covered, f);
+  }
+}
+
+// Split form, covered part: each warp takes 32 entries of the covered-node
+// list (grouped by particle, so the warp's force sums mostly go to one
+// owner), pulls and takes the moments in pair arithmetic, and gives the
+// immersed-boundary update in FP64.
+template <class LAT>
+__global__ void __launch_bounds__(128, 3) collide_covered_kernel(View v) {
+  constexpr int STORE = LBM_IMB_STORE_DFDEV;
+  constexpr int Q = LAT::Q;
+  const int count = *v.cov_count;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int row = v.ny * v.pitch;
+  for (int base = warp * 32; base < count; base += nwarps * 32) {
+    const int i = base + lane;
+    const bool mine = i < count;
+    const int n = v.cov_list[mine ? i : base];
+    const int z = n / row, r = n - z * row;
+    const int y = r / v.pitch, x = r - y * v.pitch;
+    DF f[Q];
+    pull<LAT, STORE>(v, x, y, z, n, true, f);
+    const Moments<DF> md = moments<LAT, STORE>(v, f);
+    double g[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) g[q] = df_to_bits(f[q]);
+    Moments<double> m;
+    m.rho = df_to_bits(md.rho);
+    m.drho = df_to_bits(md.drho);
+    m.ux = df_to_bits(md.ux);
+    m.uy = df_to_bits(md.uy);
+    m.uz = df_to_bits(md.uz);
+    m.k = k_of<LAT, kDfDevImb>(m.ux, m.uy, m.uz);
+    imb_core<LAT, kDfDevImb>(v, x, y, z, n, mine, g, m);
+  }
+}
+
 // CTA-packed form: one CTA per 128-node row tile (no persistence).
 template <class LAT, int STORE, int MINB>
 __global__ void __launch_bounds__(128, MINB) collide_packed_kernel(View v) {
@@ -357,6 +412,24 @@ static void launch_fused(const View& v, cudaStream_t s) {
   else collide_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);
 }
 
+template <class LAT, int STORE>
+static void launch_split(const View& v, cudaStream_t s) {
+  static int grid_a = 0, grid_b = 0;
+  if (grid_a == 0) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
+    grid_a = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
+    grid_b = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
+  collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
+  if (v.cov_list != nullptr) collide_covered_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+}
+
 template <class LAT, int STORE, int MINB>
 static void launch_packed(const View& v, cudaStream_t s) {
   const int smem = 2 * queue_bytes_per_warp<LAT, STORE>();
@@ -402,14 +475,16 @@ static void dispatch(const View& v, cudaStream_t s) {
   if constexpr (STORE == LBM_IMB_STORE_DFDEV) {
     // the persistent fused forms, with the register budgets the pair
     // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
-    // prefetching form at 2 and 3), and the TMA-pipelined form (2); the
-    // other numbers use 0
+    // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
+    // split form (6: plain nodes, then the rasteriser's covered-node list);
+    // the other numbers use 0
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;
       case 3: launch_fused<LAT, STORE, 3, false>(v, s); break;
       case 4: launch_fused<LAT, STORE, 2, true>(v, s); break;
       case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
+      case kCollideSplit: launch_split<LAT, STORE>(v, s); break;
       default: launch_fused<LAT, STORE, 4, false>(v, s);
     }
   } else {

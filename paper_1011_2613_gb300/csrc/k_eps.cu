@@ -100,7 +100,9 @@ void launch_eps_clear(const View& v, bool zero_forces, cudaStream_t s) {
 
 template <int DIM, typename T>
 static void raster_t(const View& v, const RasterSmem cap, int smem_bytes, cudaStream_t s) {
-  if (v.eps_method == 1) eps_raster_kernel<DIM, T, true><<<v.np, 128, 0, s>>>(v, cap);  // no tables
+  if (v.eps_method == 1)  // no tables; the covered-node list only when it is built
+    eps_raster_kernel<DIM, T, true><<<v.np, 128, v.cov_list ? (int)raster_list_bytes(DIM, v.rmax_bins) : 0, s>>>(
+        v, cap);
   else eps_raster_kernel<DIM, T, false><<<v.np, 128, smem_bytes, s>>>(v, cap);
 }
 

@@ -100,6 +100,11 @@ struct View {
   double* vl_ref;
   int* vl_flag;
   long long* vl_builds;
+  // covered-node list of the split collision (pair storage, form
+  // kCollideSplit): the rasteriser appends every node whose first owner slot
+  // it claims; null otherwise
+  int* cov_list;
+  int* cov_count;
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i
@@ -125,6 +130,10 @@ struct View {
 };
 
 static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
+
+// collide form of the pair storage that updates plain and covered nodes in
+// two launches (the covered ones from the rasteriser's list)
+constexpr int kCollideSplit = 6;
 
 // bytes of one stored population; whether the covered fractions (and the
 // rasteriser) are FP64
