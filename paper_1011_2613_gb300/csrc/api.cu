@@ -456,7 +456,7 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
     e = e ? e : cudaStreamSynchronize(h->stream);
     free(hbuf);
     if (e != cudaSuccess) st = LBM_IMB_ECUDA;
-    if (!st && L.smem > 48 * 1024 && lbm::eps_raster_set_attrs(L.smem) != 0) st = LBM_IMB_ECUDA;
+    if (!st && L.smem > 0 && lbm::eps_raster_set_attrs(L.smem) != 0) st = LBM_IMB_ECUDA;
   }
   if (!st) {
     cudaError_t e = cudaMemsetAsync(v.err, 0, 16, h->stream);

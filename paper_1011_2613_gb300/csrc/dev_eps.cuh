@@ -393,6 +393,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ T bnd[3][64];  // signed boundary offsets
   __shared__ float bndf[3][64];
   __shared__ T val[3][64];  // value lists
+  __shared__ T kax[3][64];  // 3D: v (3 R^2 - v^2) / 2 of every axis value v
   __shared__ T ax_s[2][64], ax_psi[2][64];  // 2D per-axis tables
   __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
   __shared__ int n_part, n_need, n_cov, cov_base;
@@ -419,6 +420,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     bndf[d][i] = (float)b;
     if constexpr (TABLE) offc[d][i] = (d < DIM && i < ne[d]) ? (float)((double)(lo[d] + i) - c[d]) : 0.f;
     val[d][i] = (d < DIM && i <= ne[d]) ? fabs(b) : T(0);
+    if (DIM == 3) kax[d][i] = T(0.5) * val[d][i] * (T(3) * R * R - val[d][i] * val[d][i]);
   }
   if constexpr (!TABLE)
     for (int t = threadIdx.x; t < tsize; t += blockDim.x) need[t] = 0;
@@ -516,7 +518,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
       T* e = pr + 4 * (g * cap.pair_cap + r);
       if (z2 > T(0)) {
         const T z = sqrt(z2);
-        e[0] = z;
+        e[0] = (u * w) * z;
         e[1] = atan2_q1(R * z, u * w);
         e[2] = atan2_q1(z, u);
         e[3] = atan2_q1(z, w);
@@ -530,9 +532,17 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     if (need[t]) clist[atomicAdd(&n_need, 1)] = t;
   __syncthreads();
 
-  // pass 2: the needed corner values
-  const T iR = T(1) / R;
+  // pass 2: the needed corner values.  3D: with the face angles
+  // th_a = s_a - pi/2 (s_a the sum of the two vertex angles on the face
+  // X = a), the solid angle Omega = sum(alpha) - pi - (a th_a + b th_b +
+  // c th_c) / R and the face areas A_a = (R^2 - a^2) th_a / 2 -
+  // (b z_ab + c z_ac) / 2 + b c, the divergence form 3P = R^3 Omega -
+  // a A_a - b A_b - c A_c collects to
+  //   3P = R^3 (sum(alpha) - pi) - sum_d k_d th_d + sum_pairs u v z_uv - 3abc,
+  // k_d = v_d (3R^2 - v_d^2) / 2 per axis value, u v z_uv per pair entry.
   const FastDiv3 tdiv(tx, ty);
+  const T R3 = R * R * R;
+  const T piR3 = T(3.14159265358979323846) * R3;
   for (int q = threadIdx.x; q < n_need; q += blockDim.x) {
     const int t = clist[q];
     int i, j, k;
@@ -549,16 +559,15 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
         const T* ab = pr + 4 * (0 * cap.pair_cap + j * tx + i);
         const T* ac = pr + 4 * (1 * cap.pair_cap + k * tx + i);
         const T* bc = pr + 4 * (2 * cap.pair_cap + k * ty + j);
-        const T zab = ab[0], zac = ac[0], zbc = bc[0];
-        const T tha = ab[3] + ac[3] - hpi;
-        const T thb = ab[2] + bc[3] - hpi;
-        const T thc = ac[2] + bc[2] - hpi;
-        const T om = ab[1] + ac[1] + bc[1] - T(2) * hpi - (a * tha + b * thb + cc * thc) * iR;
-        const T R2t = R * R;
-        const T Aa = T(0.5) * (R2t - a * a) * tha - T(0.5) * (b * zab + cc * zac) + b * cc;
-        const T Ab = T(0.5) * (R2t - b * b) * thb - T(0.5) * (a * zab + cc * zbc) + a * cc;
-        const T Ac = T(0.5) * (R2t - cc * cc) * thc - T(0.5) * (a * zac + b * zbc) + a * b;
-        out = (R2t * R * om - a * Aa - b * Ab - cc * Ac) * T(1.0 / 3.0);
+        const T ka = kax[0][i], kb = kax[1][j], kc = kax[2][k];
+        T t3 = fma(R3, (ab[1] + ac[1]) + bc[1], -piR3);
+        t3 = fma(-ka, ab[3] + ac[3], t3);
+        t3 = fma(-kb, ab[2] + bc[3], t3);
+        t3 = fma(-kc, ac[2] + bc[2], t3);
+        t3 = fma(hpi, (ka + kb) + kc, t3);
+        t3 += (ab[0] + ac[0]) + bc[0];
+        t3 = fma(T(-3) * (a * b), cc, t3);
+        out = t3 * T(1.0 / 3.0);
       }
     }
     tab[t] = out;

@@ -128,7 +128,16 @@ static bool set_attrs_t(int bytes) {
          cudaFuncSetAttribute(eps_raster_kernel<3, float, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess;
 }
 
-int eps_raster_set_attrs(int bytes) { return (set_attrs_t<false>(bytes) && set_attrs_t<true>(bytes)) ? 0 : -1; }
+// the attribute only grows (handles with larger particles may coexist); the
+// kernels' static shared memory counts against the same 227 KB, so it is set
+// for every rasterising handle, not only above 48 KB of dynamic memory
+int eps_raster_set_attrs(int bytes) {
+  static int granted = 0;
+  if (bytes <= granted) return 0;
+  if (!(set_attrs_t<false>(bytes) && set_attrs_t<true>(bytes))) return -1;
+  granted = bytes;
+  return 0;
+}
 
 __global__ void atan2_probe_kernel(const double* y, const double* x, double* fast, double* ref, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
