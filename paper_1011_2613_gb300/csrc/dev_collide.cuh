@@ -221,8 +221,23 @@ __device__ __forceinline__ F2 operator-(const F2 a) { return a * F2(-1.f); }  //
 __device__ __forceinline__ F2 operator-(const F2 a, const F2 b) { return fma(b, F2(-1.f), a); }  // one rounding
 
 __device__ __forceinline__ float rcp(const float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp(const double x) { return 1.0 / x; }
+// 1 / x (x > 0, normal): the hardware's approximate reciprocal refined by
+// two Newton-Raphson steps r <- r + r (1 - x r), within an ulp or two of the
+// rounded quotient at four FP64 operations
+__device__ __forceinline__ double rcp(const double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
 __device__ __forceinline__ F2 rcp(const F2 x) { return F2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
+
+// a / b: FP64 through the Newton reciprocal above, other types as written
+template <typename T>
+__device__ __forceinline__ T quot(const T a, const T b) {
+  if constexpr (std::is_same<T, double>::value) return a * rcp(b);
+  else return a / b;
+}
 
 // c . u built from the non-zero components only (after unrolling the
 // direction loop the branches fold, and no 0*u term survives)
@@ -594,7 +609,7 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
     VSy = T(V1y);
     VSz = T(V1z);
   } else if (no > 1) {
-    inv_esum = PT(1) / esum;
+    inv_esum = quot(PT(1), esum);
     VSx = T(vs0 * inv_esum);
     VSy = T(vs1 * inv_esum);
     VSz = T(vs2 * inv_esum);
@@ -602,7 +617,7 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   if (no > 0 && esum > PT(0)) {
     const T eps = esum < PT(1) ? T(esum) : T(1);
     const T th = tau_t - T(0.5);
-    beta = eps * th / ((T(1) - eps) + th);  // Eq. (2)
+    beta = quot(eps * th, (T(1) - eps) + th);  // Eq. (2)
   }
 
   // update, with f (deviation form for DEV storages, unscaled) and the

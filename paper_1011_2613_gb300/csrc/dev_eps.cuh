@@ -218,14 +218,23 @@ __constant__ double kAtanTab[17] = {
 // atan(t) = atan(c) + atan(t'), t' = (t - c)/(1 + t c) = (n - c d)/(d + c n),
 // |t'| <= 1/32 (slightly more if k is off by one); atan(t') is its Taylor
 // series through t'^11 (truncation below 1e-17 relative).  y > x uses
-// pi/2 - atan(x/y).  One FP64 division instead of two plus range logic.
+// pi/2 - atan(x/y).  One reciprocal (approximation + two Newton steps)
+// instead of two divisions plus range logic.
 __device__ __forceinline__ double atan2_q1(const double y, const double x) {
   const bool sw = y > x;
   const double num = sw ? x : y, den = sw ? y : x;
   int k = __float2int_rn(16.f * __fdividef((float)num, (float)den));
   k = k < 0 ? 0 : (k > 16 ? 16 : k);
   const double c = (double)k * 0.0625;
-  const double tp = fma(-c, den, num) / fma(c, num, den);
+  // t' = (n - c d) * (1 / (d + c n)): the hardware's approximate reciprocal
+  // refined by two Newton-Raphson steps r <- r + r (1 - q r) (the relative
+  // error squares at each step); q >= d > 0
+  const double q = fma(c, num, den);
+  double rq;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rq) : "d"(q));
+  rq = fma(rq, fma(-q, rq, 1.0), rq);
+  rq = fma(rq, fma(-q, rq, 1.0), rq);
+  const double tp = fma(-c, den, num) * rq;
   const double s = tp * tp;
   double p = fma(s, -1.0 / 11.0, 1.0 / 9.0);
   p = fma(s, p, -1.0 / 7.0);
