@@ -72,7 +72,7 @@ WORKLOADS = {
 # (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}) on the profiling
 # cases of paper_1011_2613_gb300.profile_case with and without particles:
 # D3Q19 192x384x192 (covered fraction 0.218), D2Q9 2048x4096 (0.067).
-FP64_OPS = {3: (148.0, 225.0), 2: (68.0, 151.0)}
+FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node of
 # one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
 # case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
