@@ -77,7 +77,7 @@ FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
 # one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
 # case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
 # moves this many bytes per node times its node count (same solid fraction).
-TRAFFIC_B_PER_NODE = {("f64", 3): 375.3, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3, ("dfdev", 3): 387.4}
+TRAFFIC_B_PER_NODE = {("f64", 3): 375.3, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3, ("dfdev", 3): 586.2}
 ESZ = {"f64": 8, "f32dev": 4, "f16dev": 2, "dfdev": 8}  # bytes per stored population
 DTYPE = {"f64": "f64", "f32dev": "f32", "f16dev": "f32", "dfdev": "f32x2"}  # arithmetic type
 

@@ -88,7 +88,9 @@ cudaError_t launch_eps_table_build(int dim, double R, float* tab, cudaStream_t s
 
 int eps_raster_smem_bytes(int dim, int storage, double rmax) {
   const int esz = fp64_eps(storage) ? 8 : 4;
-  const long long bytes = raster_bytes(dim, esz, rmax);
+  // the covered-node list region only for the storage whose split form uses it
+  const long long list = storage == LBM_IMB_STORE_DFDEV ? 0 : raster_list_bytes(dim, rmax);
+  const long long bytes = raster_bytes(dim, esz, rmax) - list;
   if (bytes > 200 * 1024) return -1;
   return (int)bytes;
 }
