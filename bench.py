@@ -77,7 +77,31 @@ FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
 # one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
 # case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
 # moves this many bytes per node times its node count (same solid fraction).
-TRAFFIC_B_PER_NODE = {("f64", 3): 375.3, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3, ("dfdev", 3): 586.2}
+TRAFFIC_B_PER_NODE = {("f64", 3): 385.5, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3, ("dfdev", 3): 586.2}
+# forms whose DRAM traffic differs from the storage's entry (FP64: the
+# pulled-ahead forms 4 and 5 read 375 B per node, the others 386 B)
+TRAFFIC_BY_FORM = {("f64", 3, 4): 374.9, ("f64", 3, 5): 374.9}
+
+
+def traffic_per_node(storage, dim, form):
+    return TRAFFIC_BY_FORM.get((storage, dim, form), TRAFFIC_B_PER_NODE.get((storage, dim)))
+
+
+def collide_kernel_name(storage, dim, form):
+    """The name of the collision kernel a form launches (FP64 forms 2, 8 and 9
+    launch form 0's kernel)."""
+    lat = "D3Q19" if dim == 3 else "D2Q9"
+    if storage == "dfdev" and form == 6:
+        return f"collide_plain_kernel<{lat},dfdev> + collide_covered_kernel<{lat}>"
+    if form in (4, 5):
+        return f"collide_prefetch_kernel<{lat},{storage}>"
+    if form in (6, 7) and storage != "dfdev":
+        return f"collide_packed_kernel<{lat},{storage}>"
+    if form in (8, 9) and storage in ("f32dev", "f16dev"):
+        return f"collide_pair_kernel<{lat},{storage}>"
+    if form == 2 and storage != "f64":
+        return f"collide_tma_kernel<{lat},{storage}>"
+    return f"collide_kernel<{lat},{storage}>"
 ESZ = {"f64": 8, "f32dev": 4, "f16dev": 2, "dfdev": 8}  # bytes per stored population
 DTYPE = {"f64": "f64", "f32dev": "f32", "f16dev": "f32", "dfdev": "f32x2"}  # arithmetic type
 
@@ -300,8 +324,9 @@ def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=N
     res = {"mlups": cfg.n_nodes * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
            "collide_ms": t_coll, "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "bytes_per_lup": bpl, "collide_gbs": achieved, "hbm_frac": achieved / peaks["hbm_gbs"],
-           "traffic": (TRAFFIC_B_PER_NODE[(cfg.storage, cfg.dim)] * cfg.n_nodes
-                       if (cfg.storage, cfg.dim) in TRAFFIC_B_PER_NODE else None),
+           "traffic": (traffic_per_node(cfg.storage, cfg.dim, tune["variant"]) * cfg.n_nodes
+                       if traffic_per_node(cfg.storage, cfg.dim, tune["variant"]) is not None else None),
+           "kernel": collide_kernel_name(cfg.storage, cfg.dim, tune["variant"]),
            "collide_variant": tune["variant"], "collide_tuning": tune.get("table")}
     if ref_sim is not None:
         done += args.warmup + 2 * args.steps
@@ -589,8 +614,8 @@ def run_ours(args):
         cpu = cpu_oracle_sample()
 
     sim.close()
-    kname = f"collide_kernel<{'D3Q19' if cfg.dim == 3 else 'D2Q9'},{cfg.storage}>"
-    tb = TRAFFIC_B_PER_NODE.get((cfg.storage, cfg.dim))
+    kname = collide_kernel_name(cfg.storage, cfg.dim, tune["variant"])
+    tb = traffic_per_node(cfg.storage, cfg.dim, tune["variant"])
     traffic = tb * cfg.n_nodes if tb is not None and args.workload in ("cfg3", "cfg3s") else None
     roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname, "bytes_per_lup": bpl,
