@@ -46,3 +46,15 @@ def test_job_value_single_rank():
 
     v, ms = bench.job_value(200.0, 2_000_000, 5, 1)
     assert ms == 200.0 and v == pytest.approx(2_000_000 * 5 / 0.2 / 1e6)
+
+
+def test_collide_kernel_names_and_traffic():
+    """The bench names the kernel a collision form launches and takes the
+    DRAM traffic measured for that form."""
+    import bench
+    assert bench.collide_kernel_name("f64", 3, 5).startswith("collide_prefetch_kernel")
+    assert bench.collide_kernel_name("f64", 3, 9).startswith("collide_kernel")
+    assert bench.collide_kernel_name("f32dev", 3, 9).startswith("collide_pair_kernel")
+    assert "covered" in bench.collide_kernel_name("dfdev", 3, 6)
+    assert bench.traffic_per_node("f64", 3, 5) < bench.traffic_per_node("f64", 3, 0)
+    assert bench.traffic_per_node("f64", 2, 0) is None

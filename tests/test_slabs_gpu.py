@@ -79,3 +79,16 @@ def test_slabs_reduced_precision_storage(storage):
     slabs.step(30)
     fw, fs = whole.populations(), slabs.populations()
     assert float(np.max(np.abs(fs - fw) / np.abs(fw))) < 1e-5
+
+
+def test_slabs_pair_storage():
+    """The halo rows of the pair storage carry both FP32 halves of every
+    population: the slabs follow the whole lattice at FP64 level."""
+    cfg = I.config3_scaled(nx=40, ny=48, nz=32, storage="dfdev")
+    L = lbm()
+    whole = L.Simulation(cfg)
+    slabs = L.Slabs(cfg, 3)
+    whole.step(30)
+    slabs.step(30)
+    fw, fs = whole.populations(), slabs.populations()
+    assert float(np.max(np.abs(fs - fw) / np.abs(fw))) < 1e-12
