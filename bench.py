@@ -573,8 +573,9 @@ def run_ours(args):
     if not args.no_variants and rank == 0 and cfg.storage == "f64":
         steps_done = tuned_steps + args.warmup + 2 * args.steps + (args.steps if e2e else 0)
         forms = [("f32dev", cfg.replace(storage="f32dev")), ("f16dev", cfg.replace(storage="f16dev")),
-                 ("dfdev", cfg.replace(storage="dfdev")),  # FP64 deviation, double-FP32 arithmetic
-                 ("f64_eps_table", cfg.replace(eps_method=1))]  # Eq. 6 covered fractions
+                 ("dfdev", cfg.replace(storage="dfdev")),  # deviation as FP32 pairs, FP64 accuracy
+                 ("f64_eps_table", cfg.replace(eps_method=1)),  # Eq. 6 covered fractions
+                 ("dfdev_eps_table", cfg.replace(storage="dfdev", eps_method=1))]
         for st, c in forms:
             try:
                 variants[st], steps_done = measure_variant(c, args, torch, peaks, st, sim, steps_done)

@@ -28,10 +28,14 @@ def test_table_eps_matches_oracle_table(dim):
     assert 0 < np.max(np.abs(eg - ex)) < 1e-3
 
 
-def test_table_coupled_parity():
-    """Cut-down config 3 with the table: GPU against the oracle's table run."""
-    cfg = I.config3_scaled(nx=40, ny=48, nz=36).replace(eps_method=1)
+@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6)])
+def test_table_coupled_parity(storage, form):
+    """Cut-down config 3 with the table: GPU against the oracle's table run
+    (FP64, and the pair storage in its queue and split forms: the split
+    form's covered-node list comes from the table rasteriser)."""
+    cfg = I.config3_scaled(nx=40, ny=48, nz=36, storage=storage).replace(eps_method=1)
     gpu = lbm().Simulation(cfg)
+    gpu.set_collide_variant(form)
     ref = O.OracleSim(cfg)
     gpu.step(30)
     ref.step(30)

@@ -172,11 +172,16 @@ def test_spinning_particles_torque_3d(storage):
     assert np.max(np.abs(pg["omega"] - pr["omega"])) < 1e-12
 
 
-@pytest.mark.parametrize("storage", ["f64", "dfdev"])
-def test_config3_shape_channel_3d(storage):
+@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6)])
+def test_config3_shape_channel_3d(storage, form):
     """Cut-down config 3 (D3Q19, walls in y, spheres R=3.75, ratio 1000)."""
     cfg = I.config3_scaled(nx=40, ny=48, nz=36, storage=storage)
-    gpu, ref = run_pair(cfg, 30)
+    gpu = lbm().Simulation(cfg)
+    gpu.set_collide_variant(form)
+    ref = O.OracleSim(cfg)
+    gpu.step(30)
+    ref.step(30)
+    gpu.sync()
     pg, pr = gpu.particles(), ref.particles()
     assert rel_err(gpu.populations(), ref.populations()) < POP_TOL
     assert force_err(pg, pr) < FORCE_TOL
