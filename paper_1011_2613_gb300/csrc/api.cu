@@ -123,7 +123,7 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   L->off_tf = take(np * 24);
   L->off_fc = take(np * 24);
   L->off_lo = take(np * 24);
-  L->off_kin = take(np * 64);
+  L->off_kin = take(np * 128);
   L->off_binof = take(np * 4);
   L->off_bincount = take((size_t)nbins * 4);
   L->off_binslot = take((size_t)nbins * lbm::kBinCap * 4);

@@ -132,12 +132,16 @@ __device__ __forceinline__ double shfl_down(const double a, const int d) {
 }
 __device__ __forceinline__ double to_double(const float a) { return (double)a; }
 __device__ __forceinline__ double to_double(const double a) { return a; }
+__device__ __forceinline__ double to_double(const DF a) { return df_to_bits(a); }
 // a stored covered fraction in the particle-side arithmetic type
 template <typename PT, typename E>
 __device__ __forceinline__ PT to_pt(const E a) {
   return (PT)a;
 }
-
+template <>
+__device__ __forceinline__ DF to_pt<DF, double>(const double a) {
+  return df_from_bits(a);
+}
 
 // Sum the per-node force/torque contributions of a warp by particle (key)
 // and add them to the FP64 per-particle accumulators.
@@ -276,6 +280,14 @@ __device__ __forceinline__ float min_image_f(float d, int n, bool periodic) {
   const float L = (float)n;
   if (d > 0.5f * L) d -= L;
   else if (d < -0.5f * L) d += L;
+  return d;
+}
+
+__device__ __forceinline__ DF min_image_df(DF d, int n, bool periodic) {
+  if (!periodic) return d;
+  const float L = (float)n;
+  if (d.h > 0.5f * L) d = d - DF(L);
+  else if (d.h < -0.5f * L) d = d + DF(L);
   return d;
 }
 
@@ -446,7 +458,17 @@ struct Kin {
 template <int STORE>
 __device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& v, const int q) {
   Kin<typename Storage<STORE>::T> k;
-  if constexpr (std::is_same<typename Storage<STORE>::T, float>::value) {
+  if constexpr (STORE == LBM_IMB_STORE_DFDEV) {
+    // 32-float record: high parts, nearest node, then the low parts
+    const float4* kp = reinterpret_cast<const float4*>(v.kin) + 8 * q;
+    const float4 fr = __ldg(kp), vp = __ldg(kp + 2), wp = __ldg(kp + 3);
+    const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
+    const float4 frl = __ldg(kp + 4), vpl = __ldg(kp + 6), wpl = __ldg(kp + 7);
+    k.c[0] = DF(fr.x, frl.x); k.c[1] = DF(fr.y, frl.y); k.c[2] = DF(fr.z, frl.z);
+    k.ic[0] = ir.x; k.ic[1] = ir.y; k.ic[2] = ir.z;
+    k.vel[0] = DF(vp.x, vpl.x); k.vel[1] = DF(vp.y, vpl.y); k.vel[2] = DF(vp.z, vpl.z);
+    k.w[0] = DF(wp.x, wpl.x); k.w[1] = DF(wp.y, wpl.y); k.w[2] = DF(wp.z, wpl.z);
+  } else if constexpr (std::is_same<typename Storage<STORE>::T, float>::value) {
     const float4* kp = reinterpret_cast<const float4*>(v.kin) + 4 * q;
     const float4 fr = __ldg(kp);
     const int4 ir = __ldg(reinterpret_cast<const int4*>(kp) + 1);
@@ -473,7 +495,11 @@ __device__ __forceinline__ Kin<typename Storage<STORE>::T> load_kin(const View& 
 template <bool D3, typename PT>
 __device__ __forceinline__ void node_rel(const View& v, const Kin<PT>& k, const int x, const int y, const int z,
                                          PT (&r)[3], PT (&V)[3]) {
-  if constexpr (sizeof(PT) == 4) {
+  if constexpr (std::is_same<PT, DF>::value) {
+    r[0] = min_image_df(DF(float(x - k.ic[0])) - k.c[0], v.nx, true);
+    r[1] = min_image_df(DF(float(y + v.ygo - k.ic[1])) - k.c[1], v.ny_glob, !v.wall_y);
+    r[2] = D3 ? min_image_df(DF(float(z - k.ic[2])) - k.c[2], v.nz, true) : DF(0.f);
+  } else if constexpr (sizeof(PT) == 4) {
     r[0] = min_image_f(float(x - k.ic[0]) - k.c[0], v.nx, true);
     r[1] = min_image_f(float(y + v.ygo - k.ic[1]) - k.c[1], v.ny_glob, !v.wall_y);
     r[2] = D3 ? min_image_f(float(z - k.ic[2]) - k.c[2], v.nz, true) : 0.f;

@@ -130,6 +130,13 @@ __device__ __forceinline__ bool operator==(const DF x, const DF y) {
 }
 __device__ __forceinline__ bool operator!=(const DF a, const DF b) { return !(a == b); }
 
+__device__ __forceinline__ DF shfl_xor(const DF a, const int d) {
+  return DF(__shfl_xor_sync(0xffffffffu, a.h, d), __shfl_xor_sync(0xffffffffu, a.l, d));
+}
+__device__ __forceinline__ DF shfl_down(const DF a, const int d) {
+  return DF(__shfl_down_sync(0xffffffffu, a.h, d), __shfl_down_sync(0xffffffffu, a.l, d));
+}
+
 // FP64 -> pair with integer operations: h = the significand truncated to 24
 // bits, l = the remaining 29 bits (rounded to 24 bits, 2^-48 of the value);
 // |d| < 2^-126 gives 0, |d| < 2^-74 drops l, non-finite gives NaN.

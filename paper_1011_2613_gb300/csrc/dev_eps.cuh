@@ -92,7 +92,26 @@ __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, c
   // FP32 kinematics record of the particle for the reduced-precision
   // collision: position split into the nearest node (int) and the offset
   // from it (float), velocity and spin (float)
-  if (v.kin != nullptr && lane < 16) {
+  if (v.kin != nullptr && v.storage == LBM_IMB_STORE_DFDEV) {
+    // 32-float record for the double-FP32 collision: high parts of the
+    // offset, velocity and spin, the nearest node, then the low parts
+    const int d = lane & 3, part = lane >> 2;
+    float* rec = v.kin + 32 * p;
+    const int src = part & 3;
+    const bool low = part >= 4;
+    float out = 0.f;
+    if (d < 3 && part != 5) {
+      if (src == 1) {
+        reinterpret_cast<int*>(rec)[lane] = (int)floor(v.pos[3 * p + d] + 0.5);
+      } else {
+        const double x = src == 0 ? v.pos[3 * p + d] - floor(v.pos[3 * p + d] + 0.5)
+                                  : (src == 2 ? v.vel[3 * p + d] : v.omg[3 * p + d]);
+        const float xh = (float)x;
+        out = low ? (float)(x - (double)xh) : xh;
+      }
+    }
+    if (!(d < 3 && src == 1 && !low)) rec[lane] = out;
+  } else if (v.kin != nullptr && lane < 16) {
     const int d = lane & 3, part = lane >> 2;
     float* rec = v.kin + 16 * p;
     if (d == 3) {
@@ -388,7 +407,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
   __shared__ int n_part, n_need, n_cov, cov_base;
   // nodes whose first owner slot this particle claims (split collision)
-  const bool want_list = v.cov_list != nullptr && v.collide_variant == kCollideSplit;
+  const bool want_list = v.cov_list != nullptr && split_form(v.collide_variant);
   int* s_cov = reinterpret_cast<int*>(smem + (TABLE ? 0 : raster_list_offset(cap, (int)sizeof(T))));
   const double R2 = R64 * R64;
   const float R2f = (float)R2;

@@ -119,6 +119,29 @@ __global__ void __launch_bounds__(128, 3) collide_covered_kernel(View v) {
   }
 }
 
+// The same covered part in pair arithmetic throughout (form 7): the
+// update's FP32-pipe instructions instead of the FP64 pipe.
+template <class LAT>
+__global__ void __launch_bounds__(128, 3) collide_covered_pair_kernel(View v) {
+  constexpr int STORE = LBM_IMB_STORE_DFDEV;
+  constexpr int Q = LAT::Q;
+  const int count = *v.cov_count;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int row = v.ny * v.pitch;
+  for (int base = warp * 32; base < count; base += nwarps * 32) {
+    const int i = base + lane;
+    const bool mine = i < count;
+    const int n = v.cov_list[mine ? i : base];
+    const int z = n / row, r = n - z * row;
+    const int y = r / v.pitch, x = r - y * v.pitch;
+    DF f[Q];
+    pull<LAT, STORE>(v, x, y, z, n, true, f);
+    const Moments<DF> m = moments<LAT, STORE>(v, f);
+    imb_core<LAT, STORE>(v, x, y, z, n, mine, f, m);
+  }
+}
+
 // CTA-packed form: one CTA per 128-node row tile (no persistence).
 template <class LAT, int STORE, int MINB>
 __global__ void __launch_bounds__(128, MINB) collide_packed_kernel(View v) {
@@ -412,7 +435,7 @@ static void launch_fused(const View& v, cudaStream_t s) {
   else collide_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);
 }
 
-template <class LAT, int STORE>
+template <class LAT, int STORE, bool PAIR_COVERED>
 static void launch_split(const View& v, cudaStream_t s) {
   static int grid_a = 0, grid_b = 0;
   if (grid_a == 0) {
@@ -422,12 +445,17 @@ static void launch_split(const View& v, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
     grid_a = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
+    if constexpr (PAIR_COVERED)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_pair_kernel<LAT>, 128, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
     grid_b = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
   const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
   collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
-  if (v.cov_list != nullptr) collide_covered_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+  if (v.cov_list == nullptr) return;
+  if constexpr (PAIR_COVERED) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+  else collide_covered_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
 }
 
 template <class LAT, int STORE, int MINB>
@@ -476,15 +504,16 @@ static void dispatch(const View& v, cudaStream_t s) {
     // the persistent fused forms, with the register budgets the pair
     // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
     // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
-    // split form (6: plain nodes, then the rasteriser's covered-node list);
-    // the other numbers use 0
+    // split forms (plain nodes, then the rasteriser's covered-node list: 6
+    // in FP64, 7 in pair arithmetic); the other numbers use 0
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;
       case 3: launch_fused<LAT, STORE, 3, false>(v, s); break;
       case 4: launch_fused<LAT, STORE, 2, true>(v, s); break;
       case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
-      case kCollideSplit: launch_split<LAT, STORE>(v, s); break;
+      case kCollideSplit: launch_split<LAT, STORE, false>(v, s); break;
+      case kCollideSplit + 1: launch_split<LAT, STORE, true>(v, s); break;
       default: launch_fused<LAT, STORE, 4, false>(v, s);
     }
   } else {

@@ -28,7 +28,7 @@ def test_table_eps_matches_oracle_table(dim):
     assert 0 < np.max(np.abs(eg - ex)) < 1e-3
 
 
-@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6)])
+@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6), ("dfdev", 7)])
 def test_table_coupled_parity(storage, form):
     """Cut-down config 3 with the table: GPU against the oracle's table run
     (FP64, and the pair storage in its queue and split forms: the split

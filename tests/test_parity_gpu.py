@@ -172,7 +172,7 @@ def test_spinning_particles_torque_3d(storage):
     assert np.max(np.abs(pg["omega"] - pr["omega"])) < 1e-12
 
 
-@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6)])
+@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6), ("dfdev", 7)])
 def test_config3_shape_channel_3d(storage, form):
     """Cut-down config 3 (D3Q19, walls in y, spheres R=3.75, ratio 1000)."""
     cfg = I.config3_scaled(nx=40, ny=48, nz=36, storage=storage)
