@@ -244,7 +244,8 @@ def test_reduced_storage_error(storage, tol_u, tol_f):
 def test_collide_variants_agree(dim, storage):
     """Every kernel form gives bitwise the populations of form 0 after one
     step (nx = 300 spans ragged row tiles), and the FP64 forms stay within
-    the oracle tolerance after 12 steps."""
+    the oracle tolerance after 12 steps.  Form 7 of the pair storage updates
+    covered nodes in pair arithmetic instead of FP64: within 1e-14 there."""
     if dim == 3:
         cfg = I.config3_scaled(nx=300, ny=20, nz=12).replace(storage=storage)
     else:
@@ -257,7 +258,10 @@ def test_collide_variants_agree(dim, storage):
         sim = L.Simulation(cfg)
         sim.set_collide_variant(var)
         sim.step(1)
-        assert np.array_equal(sim.populations(), f_base), f"variant {var}"
+        if storage == "dfdev" and var == 7:
+            assert rel_err(sim.populations(), f_base) < 1e-14, f"variant {var}"
+        else:
+            assert np.array_equal(sim.populations(), f_base), f"variant {var}"
         if storage in ("f64", "dfdev"):
             ref = O.OracleSim(cfg)
             ref.step(12)
