@@ -77,10 +77,11 @@ FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
 # one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
 # case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
 # moves this many bytes per node times its node count (same solid fraction).
-TRAFFIC_B_PER_NODE = {("f64", 3): 385.5, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3, ("dfdev", 3): 586.2}
+TRAFFIC_B_PER_NODE = {("f64", 3): 385.5, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3}
 # forms whose DRAM traffic differs from the storage's entry (FP64: the
-# pulled-ahead forms 4 and 5 read 375 B per node, the others 386 B)
-TRAFFIC_BY_FORM = {("f64", 3, 4): 374.9, ("f64", 3, 5): 374.9}
+# pulled-ahead forms 4 and 5 read 375 B per node, the others 386 B; the pair
+# storage only for its split forms, both kernels together)
+TRAFFIC_BY_FORM = {("f64", 3, 4): 374.9, ("f64", 3, 5): 374.9, ("dfdev", 3, 6): 586.2, ("dfdev", 3, 7): 625.3}
 
 
 def traffic_per_node(storage, dim, form):
@@ -93,6 +94,8 @@ def collide_kernel_name(storage, dim, form):
     lat = "D3Q19" if dim == 3 else "D2Q9"
     if storage == "dfdev" and form == 6:
         return f"collide_plain_kernel<{lat},dfdev> + collide_covered_kernel<{lat}>"
+    if storage == "dfdev" and form == 7:
+        return f"collide_plain_kernel<{lat},dfdev> + collide_covered_pair_kernel<{lat}>"
     if form in (4, 5):
         return f"collide_prefetch_kernel<{lat},{storage}>"
     if form in (6, 7) and storage != "dfdev":
