@@ -329,7 +329,7 @@ int lbm_imb_dem_forces_static(int32_t dim, const int32_t* extent, int32_t wall_y
  * Not in the paper.  The paper compares the drag it resolves with Wen-Yu and
  * EMMS closures (section "Simulation results"); here the resolved forces of
  * the method are used to train a small network that predicts a particle's
- * drag from its surroundings, and the resolved solve judges its error.
+ * drag from its surroundings, and the resolved solve measures its error.
  *
  * Drag samples: for every particle of a simulation, features
  *   [0] mean solid fraction eps over the nodes at distance (R, R + shell]
