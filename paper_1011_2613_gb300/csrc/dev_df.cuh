@@ -51,6 +51,25 @@ struct DF {
     return DF(r, __fsub_rn(t, __fsub_rn(r, s)));
 #endif
   }
+  // |a| and sqrt(a) (a >= 0): found by argument-dependent lookup only
+  friend __device__ __forceinline__ DF fabs(const DF a) { return a.h < 0.f ? DF(-a.h, -a.l) : a; }
+  // FP32 root of h refined by one Newton step in pair arithmetic (Karp and
+  // Markstein): s = s0 + (a - s0^2) / (2 s0), the residual a - s0^2 exact
+  // through the FMA product error
+  friend __device__ __forceinline__ DF sqrt(const DF x) {
+    // normalised first: after a cancellation l may hold much of the value,
+    // and the FP32 seed must be close to the whole value
+    const float xs = __fadd_rn(x.h, x.l);
+    const DF a(xs, __fsub_rn(x.l, __fsub_rn(xs, x.h)));
+    if (!(a.h > 0.f)) return DF(0.f, 0.f);
+    const float s0 = __fsqrt_rn(a.h);
+    const float p = __fmul_rn(s0, s0);
+    const float e = __fmaf_rn(s0, s0, -p);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.h, p), e), a.l);  // a - s0^2 (a.h - p is exact)
+    const float corr = __fmul_rn(res, __fmul_rn(0.5f, __frcp_rn(s0)));
+    const float hs = __fadd_rn(s0, corr);
+    return DF(hs, __fsub_rn(corr, __fsub_rn(hs, s0)));
+  }
 };
 
 __device__ __forceinline__ DF fast_two_sum(const float a, const float b) {
@@ -124,6 +143,8 @@ __device__ __forceinline__ bool operator<(const DF x, const DF y) {
   return a.h < b.h || (a.h == b.h && a.l < b.l);
 }
 __device__ __forceinline__ bool operator>(const DF a, const DF b) { return b < a; }
+__device__ __forceinline__ bool operator>=(const DF a, const DF b) { return !(a < b); }
+__device__ __forceinline__ bool operator<=(const DF a, const DF b) { return !(b < a); }
 __device__ __forceinline__ bool operator==(const DF x, const DF y) {
   const DF a = df_norm(x), b = df_norm(y);
   return a.h == b.h && a.l == b.l;

@@ -4,6 +4,9 @@
 #pragma once
 #include <math.h>
 
+#include <type_traits>
+
+#include "dev_df.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -164,7 +167,7 @@ __host__ __device__ inline int raster_list_offset(const RasterSmem c, int esz) {
 
 template <typename T>
 __device__ __forceinline__ int classify_cell(const T (*bnd)[64], const float (*bndf)[64], const int idx[3],
-                                             int dim, double R2, float R2f) {
+                                             int dim, const T R2, float R2f) {
   // exact decision in T; the FP64 instantiation first tries FP32 copies of
   // the offsets with a relative margin that cannot flip a decision
   if (sizeof(T) == 8) {
@@ -187,8 +190,8 @@ __device__ __forceinline__ int classify_cell(const T (*bnd)[64], const float (*b
     near2 += nd * nd;
     far2 += fd * fd;
   }
-  if (near2 >= T(R2)) return 0;
-  if (far2 <= T(R2)) return 1;
+  if (near2 >= R2) return 0;
+  if (far2 <= R2) return 1;
   return 2;
 }
 
@@ -204,13 +207,18 @@ __device__ __forceinline__ int split_axis(const T* b, int i, int zero, int (&lo_
   return 2;
 }
 
-// atan(k/16), k = 0..16 (round to nearest)
-__constant__ double kAtanTab[17] = {
-    0.0,                 0.06241880999595735, 0.12435499454676144, 0.18534794999569476,
-    0.24497866312686414, 0.3028848683749714,  0.35877067027057225, 0.4124104415973873,
-    0.4636476090008061,  0.5123894603107377,  0.5585993153435624,  0.6022873461349642,
-    0.6435011087932844,  0.6823165548747481,  0.7188299996216245,  0.7531512809621944,
+// atan(k/16), k = 0..16 (round to nearest); the FP32-pair copy for the
+// rasteriser of the pair storage
+constexpr double kAtanK16[17] = {
+    0.0, 0.06241880999595735, 0.12435499454676144, 0.18534794999569476,
+    0.24497866312686414, 0.3028848683749714, 0.35877067027057225, 0.4124104415973873,
+    0.4636476090008061, 0.5123894603107377, 0.5585993153435624, 0.6022873461349642,
+    0.6435011087932844, 0.6823165548747481, 0.7188299996216245, 0.7531512809621944,
     0.7853981633974483};
+__constant__ double kAtanTab[17] = {
+    kAtanK16[0], kAtanK16[1], kAtanK16[2], kAtanK16[3], kAtanK16[4], kAtanK16[5], kAtanK16[6], kAtanK16[7], kAtanK16[8], kAtanK16[9], kAtanK16[10], kAtanK16[11], kAtanK16[12], kAtanK16[13], kAtanK16[14], kAtanK16[15], kAtanK16[16]};
+__constant__ DF kAtanTabDF[17] = {
+    DF(kAtanK16[0]), DF(kAtanK16[1]), DF(kAtanK16[2]), DF(kAtanK16[3]), DF(kAtanK16[4]), DF(kAtanK16[5]), DF(kAtanK16[6]), DF(kAtanK16[7]), DF(kAtanK16[8]), DF(kAtanK16[9]), DF(kAtanK16[10]), DF(kAtanK16[11]), DF(kAtanK16[12]), DF(kAtanK16[13]), DF(kAtanK16[14]), DF(kAtanK16[15]), DF(kAtanK16[16])};
 
 // atan2(y, x) for y, x >= 0, not both zero (all angles of the exact-volume
 // formulas lie in the first quadrant).  Method: with t = min/max <= 1 and
@@ -245,6 +253,40 @@ __device__ __forceinline__ double atan2_q1(const double y, const double x) {
   return sw ? 1.57079632679489661923 - r : r;
 }
 __device__ __forceinline__ float atan2_q1(const float y, const float x) { return atan2f(y, x); }
+// the same method in pair arithmetic (the pair storage's rasteriser): one
+// pair reciprocal, the series' terms from t'^7 on in FP32 (below 2^-48 of the
+// result), the rest in pairs
+__device__ __forceinline__ DF atan2_q1(const DF y, const DF x) {
+  const bool sw = y > x;
+  const DF num = sw ? x : y, den = sw ? y : x;
+  int k = __float2int_rn(16.f * __fdividef(num.h, den.h));
+  k = k < 0 ? 0 : (k > 16 ? 16 : k);
+  const float c = (float)k * 0.0625f;
+  const DF tp = (num - den * c) * rcp(den + num * c);
+  const DF s = tp * tp;
+  const float sf = s.h;
+  const float tail = __fmaf_rn(sf, __fmaf_rn(sf, -1.f / 11.f, 1.f / 9.f), -1.f / 7.f);
+  DF u = DF(0.2) + s * tail;
+  u = DF(-1.0 / 3.0) + s * u;
+  const DF r = kAtanTabDF[k] + (tp + (tp * s) * u);
+  return sw ? DF(1.57079632679489661923) - r : r;
+}
+
+// conversions of the rasteriser's element type
+__device__ __forceinline__ float to_f32(const double x) { return (float)x; }
+__device__ __forceinline__ float to_f32(const float x) { return x; }
+__device__ __forceinline__ float to_f32(const DF x) { return x.h; }
+template <typename T>
+__device__ __forceinline__ T from_f64(const double x) {
+  if constexpr (std::is_same<T, DF>::value) return df_from_bits(x);
+  else return (T)x;
+}
+// a covered fraction into its slot (FP64 slots for the pair storage)
+template <typename T>
+__device__ __forceinline__ void store_eps(void* slot, const long long n, const T e) {
+  if constexpr (std::is_same<T, DF>::value) static_cast<double*>(slot)[n] = df_to_bits(e);
+  else static_cast<T*>(slot)[n] = e;
+}
 
 // --------------------------------------------------------------------------
 // Exact fraction of one cell, without tables (builds the Eq. 6 table).
@@ -377,7 +419,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
                                                     unsigned char* smem) {
   __syncthreads();  // the block may still be reading the previous particle's tables
   const double R64 = v.rad[p];
-  const T R = T(R64);
+  const T R = from_f64<T>(R64);
   const double c[3] = {v.pos[3 * p], v.pos[3 * p + 1], v.pos[3 * p + 2]};
   int lo[3] = {0, 0, 0}, ne[3] = {1, 1, 1};
 #pragma unroll
@@ -411,6 +453,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   int* s_cov = reinterpret_cast<int*>(smem + (TABLE ? 0 : raster_list_offset(cap, (int)sizeof(T))));
   const double R2 = R64 * R64;
   const float R2f = (float)R2;
+  const T R2t = from_f64<T>(R2);
 
   if (threadIdx.x == 0) {
     for (int d = 0; d < 3; d++) {
@@ -424,9 +467,9 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   if (!rows_meet_slab(v, lo[1], ne[1])) return;  // another slab's particle (block-uniform)
   for (int t = threadIdx.x; t < 3 * 64; t += blockDim.x) {
     const int d = t / 64, i = t % 64;
-    const T b = (d < DIM && i <= ne[d]) ? T(((double)(lo[d] + i) - 0.5) - c[d]) : T(0);
+    const T b = (d < DIM && i <= ne[d]) ? from_f64<T>(((double)(lo[d] + i) - 0.5) - c[d]) : T(0);
     bnd[d][i] = b;
-    bndf[d][i] = (float)b;
+    bndf[d][i] = to_f32(b);
     if constexpr (TABLE) offc[d][i] = (d < DIM && i < ne[d]) ? (float)((double)(lo[d] + i) - c[d]) : 0.f;
     val[d][i] = (d < DIM && i <= ne[d]) ? fabs(b) : T(0);
     if (DIM == 3) kax[d][i] = T(0.5) * val[d][i] * (T(3) * R * R - val[d][i] * val[d][i]);
@@ -452,7 +495,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
 #pragma unroll
     for (int s = 0; s < kMaxOwners; s++) {
       if (atomicCAS(&v.own[s][n], -1, p) == -1) {
-        static_cast<T*>(v.eps[s])[n] = e;
+        store_eps<T>(v.eps[s], n, e);
         if (s == 0 && want_list) s_cov[atomicAdd(&n_cov, 1)] = (int)n;
         return;
       }
@@ -471,7 +514,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
     int idx[3];
     cdiv.split(t, idx[0], idx[1], idx[2]);
-    const int cls = classify_cell<T>(bnd, bndf, idx, DIM, R2, R2f);
+    const int cls = classify_cell<T>(bnd, bndf, idx, DIM, R2t, R2f);
     if (cls == 0) continue;
     if (cls == 1) {
       claim(idx[0], idx[1], idx[2], T(1));

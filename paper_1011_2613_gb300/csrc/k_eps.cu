@@ -111,11 +111,15 @@ static void raster_t(const View& v, const RasterSmem cap, int smem_bytes, cudaSt
 void launch_eps_raster(const View& v, int smem_bytes, cudaStream_t s) {
   if (v.np <= 0) return;
   const RasterSmem cap = raster_caps(v.dim, v.rmax_bins);
+  // the pair storage rasterises in pair arithmetic (FP32 pipe), the FP64
+  // storage in FP64, the others in FP32
   if (v.dim == 2) {
-    if (fp64_eps(v.storage)) raster_t<2, double>(v, cap, smem_bytes, s);
+    if (v.storage == LBM_IMB_STORE_DFDEV) raster_t<2, DF>(v, cap, smem_bytes, s);
+    else if (fp64_eps(v.storage)) raster_t<2, double>(v, cap, smem_bytes, s);
     else raster_t<2, float>(v, cap, smem_bytes, s);
   } else {
-    if (fp64_eps(v.storage)) raster_t<3, double>(v, cap, smem_bytes, s);
+    if (v.storage == LBM_IMB_STORE_DFDEV) raster_t<3, DF>(v, cap, smem_bytes, s);
+    else if (fp64_eps(v.storage)) raster_t<3, double>(v, cap, smem_bytes, s);
     else raster_t<3, float>(v, cap, smem_bytes, s);
   }
 }
@@ -124,7 +128,9 @@ void launch_eps_raster(const View& v, int smem_bytes, cudaStream_t s) {
 template <bool TABLE>
 static bool set_attrs_t(int bytes) {
   const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  return cudaFuncSetAttribute(eps_raster_kernel<2, double, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
+  return cudaFuncSetAttribute(eps_raster_kernel<2, DF, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(eps_raster_kernel<3, DF, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(eps_raster_kernel<2, double, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
          cudaFuncSetAttribute(eps_raster_kernel<2, float, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
          cudaFuncSetAttribute(eps_raster_kernel<3, double, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess &&
          cudaFuncSetAttribute(eps_raster_kernel<3, float, TABLE>, (cudaFuncAttribute)a, bytes) == cudaSuccess;
