@@ -1,7 +1,9 @@
-// Double-FP32 arithmetic for the FP64-accuracy collision on the FP32 pipe.
+// Double-FP32 arithmetic for the FP64-accuracy collision and rasteriser of
+// the pair storage, on the FP32 pipe.
 //
-// A value is the unevaluated sum h + l of two FP32 numbers with |l| at most
-// about half an FP32 ulp of h: 48 significant bits.  The operations are the
+// A value is the unevaluated sum h + l of two FP32 numbers with |l| about
+// half an FP32 ulp of h (a few ulps between renormalisations, see
+// LBM_DF_LAZY): 48 significant bits.  The operations are the
 // error-free transformations of the double-double literature written for
 // FP32 pairs: Knuth's TwoSum, Dekker's Fast2Sum, and the exact product error
 // through FMA (Dekker 1971; Hida, Li and Bailey, "Algorithms for quad-double
@@ -10,10 +12,10 @@
 //
 // Why: GB300 issues FP32 at 64 times its FP64 rate.  The collision works on
 // the deviation g = f - w rho0 (|g| is 1e-2 w or less), stored as such a
-// pair, so 48 bits of g are more than the 53 bits of f: the plain update is
-// as accurate as the FP64 update of f while no FP64 instruction runs.  The
-// FP64 <-> pair conversions (for the FP64 update of covered nodes) are
-// integer bit operations.
+// pair, so 48 bits of g are more than the 53 bits of f: the update is as
+// accurate as the FP64 update of f while no FP64 instruction runs.  The
+// FP64 <-> pair conversions (covered fractions, and the collision forms that
+// update covered nodes in FP64) are integer bit operations.
 #pragma once
 #include <cuda_runtime.h>
 
