@@ -48,10 +48,13 @@ extern "C" int lbm_imb_dem_forces_static(int32_t dim, const int32_t* extent, int
                                          double rmax, const double* pos, const double* vel,
                                          const double* radius, const double* mass, double k_n,
                                          double restitution, double* fc, void* stream) {
-  if ((dim != 2 && dim != 3) || !extent || n < 0 || n > (1ll << 30) || !(rmax > 0.0)) return LBM_IMB_EINVAL;
-  if (wall_y != 0 && wall_y != 1) return LBM_IMB_EINVAL;
+  // the checks of lbm_imb_dem_forces, in its order: with n = 0 there is
+  // nothing to do and no layout to check
   if (n > 0 && (!pos || !vel || !radius || !mass || !fc)) return LBM_IMB_EINVAL;
   if (!(k_n >= 0.0) || !(restitution > 0.0 && restitution <= 1.0)) return LBM_IMB_EINVAL;
+  if (n == 0) return LBM_IMB_OK;
+  if ((dim != 2 && dim != 3) || !extent || n < 0 || n > (1ll << 30) || !(rmax > 0.0)) return LBM_IMB_EINVAL;
+  if (wall_y != 0 && wall_y != 1) return LBM_IMB_EINVAL;
   int ext[3] = {extent[0], extent[1], dim == 3 ? extent[2] : 1};
   for (int d = 0; d < 3; d++)
     if (ext[d] < 1) return LBM_IMB_EINVAL;
@@ -66,7 +69,6 @@ extern "C" int lbm_imb_dem_forces_static(int32_t dim, const int32_t* extent, int
   const size_t off_slot = off_count + up256(nbins * 4);
   const size_t total = off_slot + up256(nbins * lbm::kBinCap * 4);
   if (total > kStaticScratchBytes) return LBM_IMB_EUNSUPPORTED;  // beyond the fixed scratch
-  if (n == 0) return LBM_IMB_OK;
   void* scratch = nullptr;
   st = scratch_address(&scratch);
   if (st) return st;

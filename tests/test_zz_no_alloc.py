@@ -72,3 +72,47 @@ def test_static_scratch_rejects_oversize_problem():
     r = torch.full((1,), 2.0, dtype=torch.float64, device="cuda")
     st, _ = call_static(2, [4096, 4096, 1], 0, pos, pos, r, r, 10.0, 0.9, 2.0)
     assert st == lbm.EUNSUPPORTED
+
+
+def test_static_scratch_allocates_nothing():
+    """The call's defining property: once the library is loaded (the first
+    call also looks up the array's address), further calls leave the
+    device's free memory unchanged.  Every buffer is made before the
+    measurement, so the only allocation that could show is the library's."""
+    import torch
+
+    dim, (ext, pos, vel, rad, mass), kn, e = 3, state(3, 5, 3.0, 31, 1), 40.0, 0.85
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    args = (t(pos), t(vel), t(rad), t(mass))
+    rmax = float(rad.max())
+    st, fc0 = call_static(dim, ext, 1, *args, kn, e, rmax)  # warm-up: loads the module and its array
+    assert st == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        st = _call_into(dim, ext, 1, *args, kn, e, rmax, fc0)
+        assert st == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
+
+
+def _call_into(dim, ext, wall, pos, vel, rad, mass, kn, e, rmax, fc):
+    import torch
+    from paper_1011_2613_gb300 import lbm
+
+    ex = (C.c_int32 * 3)(*ext)
+    return lbm.lib().lbm_imb_dem_forces_static(
+        dim, ex, wall, rad.numel(), rmax, C.c_void_p(pos.data_ptr()), C.c_void_p(vel.data_ptr()),
+        C.c_void_p(rad.data_ptr()), C.c_void_p(mass.data_ptr()), kn, e, C.c_void_p(fc.data_ptr()),
+        C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_static_scratch_no_particles_is_ok_like_workspace_call():
+    """n = 0: nothing to do, so neither call checks the layout (an oversized
+    bin grid is not an error without particles)."""
+    from paper_1011_2613_gb300 import lbm
+
+    ex = (C.c_int32 * 3)(4096, 4096, 1)
+    assert lbm.lib().lbm_imb_dem_forces_static(2, ex, 0, 0, 2.0, None, None, None, None, 10.0, 0.9, None,
+                                                None) == 0
