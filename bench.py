@@ -63,6 +63,8 @@ WORKLOADS = {
                        "density ratio 1000 (profiling case)"),
     "cfg1": dict(make=lambda seed: I.config1(seed=seed),
                  name="D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6, tau=0.6"),
+    "cfg2s": dict(make=lambda seed: I.periodic2d_config(nx=2048, ny=4096, seed=2 + seed - 3),
+                  name="D2Q9 2048x4096 periodic, config-2 solid fraction, disks R=4 (profiling case)"),
 }
 
 
@@ -70,7 +72,7 @@ WORKLOADS = {
 # executes per node, by lattice dimension: (every node: pull, moments, BGK;
 # extra per covered node: the immersed-boundary update).  Counted with ncu
 # (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}) on the profiling
-# cases of paper_1011_2613_gb300.profile_case with and without particles:
+# cases of `bench.py --profile-case` with and without particles:
 # D3Q19 192x384x192 (covered fraction 0.218), D2Q9 2048x4096 (0.067).
 FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node of
@@ -663,6 +665,29 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """A fixed small case for profiling one kernel family under ncu: the
+    workload with the collide form fixed (--collide-variant, default 0),
+    4 warm-up steps, then --steps steps through lbm_imb_step_profiled (one
+    launch per kernel family per step, no graph, so `ncu -s 4` skips
+    exactly the warm-up launches of a family); prints the per-family device
+    times.  --no-particles removes the particles."""
+    from paper_1011_2613_gb300 import lbm as L
+    cfg = WORKLOADS[args.workload]["make"](3).replace(storage=args.storage)
+    if args.no_particles:
+        z = np.zeros((0, 3))
+        cfg = cfg.replace(pos=z, vel=z, omega=z, radius=np.zeros(0), density=np.zeros(0))
+    sim = L.Simulation(cfg)
+    sim.set_collide_variant(args.collide_variant or 0)
+    sim.step(4)
+    sim.sync()
+    k, _ = sim.step_profiled(args.steps)
+    print(json.dumps({"workload": args.workload, "storage": args.storage, "variant": args.collide_variant or 0,
+                      "particles": cfg.n_particles, "nodes": cfg.n_nodes,
+                      "ms_per_step": {n: v / args.steps for n, v in k.items()}}))
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -676,7 +701,13 @@ def main():
                     help="fix the collide kernel form instead of autotuning it")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the small fixed profiling case of one workload/storage/form instead of the bench")
+    ap.add_argument("--no-particles", action="store_true", help="--profile-case without particles")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -134,10 +134,16 @@ typedef struct lbm_imb lbm_imb_t; /* opaque, library-owned host state */
  * config is invalid. */
 size_t lbm_imb_required_bytes(const lbm_imb_config* cfg);
 
-/* Lay out the caller's device block (dev_buf, >= required bytes, 256-byte
- * aligned, owned by the caller and never freed by the library), upload the
- * particles, set the populations to the rest equilibrium w_i rho0 and
- * rasterise eps.  cuda_stream (a cudaStream_t, may be NULL for the legacy
+/* The problem of the paper's section "Numerical scheme" and Table 2: a
+ * D2Q9/D3Q19 lattice with relaxation time tau, a body force on the gas, and
+ * particles with radii and densities (masses as in Table 2's reduced
+ * units), initially in a gas at rest.  Lay out the caller's device block
+ * (dev_buf, >= required bytes, 256-byte aligned, owned by the caller and
+ * never freed by the library), upload the particles, set the populations to
+ * the rest equilibrium w_i rho0 and rasterise eps (covered fraction of each
+ * cell, text after the Omega^S equation).  Particles must be finite, inside
+ * the walls (y in [-1/2, ny - 1/2] when wall_y = 1) and in [-1/2, n) along
+ * periodic axes, else EINVAL.  cuda_stream (a cudaStream_t, may be NULL for the legacy
  * stream) is the stream every later call of this handle uses.  On success
  * *out receives the handle.  The device current at this call is used.
  * A rejected config returns its status (EINVAL, EUNSUPPORTED) before the
@@ -147,9 +153,29 @@ int lbm_imb_init(const lbm_imb_config* cfg, void* dev_buf, size_t bytes,
                  void* cuda_stream, lbm_imb_t** out);
 
 /* Queue n >= 0 time steps on the handle's stream (asynchronous; replays a
- * captured CUDA graph).  Device-side errors (EOWNERS, EBIN) are reported by
- * the next synchronising call. */
+ * captured CUDA graph).  One step is the paper's time step ("Numerical
+ * scheme"): eps from the particle positions, pull streaming and the LBGK
+ * collision with the immersed-boundary term of Eq. (1) (beta of Eq. (2),
+ * Omega^S), the hydrodynamic force and torque of Eq. (3), and the DEM
+ * contacts of Eqs. (4)-(5) with the particle update.  Every
+ * lbm_imb_set_health_check steps (default 100) a health check scans the
+ * stored rest-direction populations and the particle state; a NaN/Inf (or a
+ * particle centre beyond 2^30 lattice units), like the other device-side
+ * errors (EOWNERS, EBIN), is reported by the next synchronising call
+ * (LBM_IMB_ENONFINITE).  The kernels skip a particle whose centre is not
+ * finite instead of indexing the lattice with it. */
 int lbm_imb_step(lbm_imb_t* h, int64_t n);
+
+/* Steps between health checks of lbm_imb_step (0 turns them off). */
+int lbm_imb_set_health_check(lbm_imb_t* h, int64_t every);
+
+/* Run the health check now on the handle's stream and synchronise:
+ * LBM_IMB_ENONFINITE if a stored rest-direction population, a particle
+ * velocity or spin is NaN/Inf or a particle centre is NaN/Inf or beyond
+ * 2^30 lattice units; any other pending device error likewise.  A NaN in
+ * any population reaches the rest direction of some node within one step,
+ * so a check one step after it appeared finds it. */
+int lbm_imb_check_health(lbm_imb_t* h);
 
 /* Kernel families of one time step, in launch order (indices into the
  * timing array of lbm_imb_step_profiled). */
@@ -212,13 +238,18 @@ int lbm_imb_particles(lbm_imb_t* h, double* pos, double* vel, double* omega,
 
 /* Replace particle positions/velocities/spins (host, [n][3], any may be
  * NULL to keep the current value); n must equal the configured count.
- * Enqueued on the stream (the host arrays are read before returning). */
+ * The values are checked on the host first: every given value finite,
+ * positions inside the walls (y in [-1/2, ny - 1/2] when wall_y = 1) and
+ * in [-1/2, n) along periodic axes; EINVAL (nothing copied) otherwise.  Copied on the stream, which is then synchronised. */
 int lbm_imb_set_particles(lbm_imb_t* h, const double* pos, const double* vel,
                           const double* omega, int64_t n);
 
-/* Macroscopic fields of the populations the next collision sees: rho,
- * u = sum_i f_i c_i / rho + g_f/2 (dim components) and eps = min(1, sum of
- * covered fractions) at the current particle positions.  cap = capacity in
+/* Macroscopic fields of the populations the next collision sees (the
+ * moments the LBGK collision of Eq. (1) is built on): rho = sum_i f_i,
+ * u = sum_i f_i c_i / rho + g_f/2 (dim components; the half-force shift of
+ * the reported velocity is a reading, the paper is silent) and
+ * eps = min(1, sum of covered fractions), the solid fraction of the text
+ * after the Omega^S equation, at the current particle positions.  cap = capacity in
  * nodes (>= nx*ny*nz).  on_device = 1: the pointers are device memory, the
  * call is enqueued on the stream; 0: host memory, the call synchronises.
  * Any pointer may be NULL. */
@@ -238,6 +269,25 @@ int lbm_imb_totals(lbm_imb_t* h, double* fluid_mass, double* fluid_momentum,
 
 /* Steps taken since init. */
 int lbm_imb_steps_done(lbm_imb_t* h, int64_t* steps);
+
+/* Checkpoint / resume.  The paper's suspensions run for millions of steps
+ * (section "Simulation results"), which a run survives only by restarting
+ * from saved state.  lbm_imb_save synchronises the stream, reports any
+ * pending device error instead of saving, and writes to the file at `path`
+ * (created or truncated): a header (format version, a hash of the
+ * configuration given to lbm_imb_init, lattice sizes, storage, particle
+ * count, steps taken), the stored post-collision populations in their raw
+ * storage format, and the particle positions, velocities, spins and the
+ * last step's hydrodynamic force and torque.  lbm_imb_load reads such a file
+ * into a handle made from the same configuration (same hash; EINVAL for any
+ * other file or an unreadable one, with the handle unchanged if the header
+ * is rejected) and restores the step count; eps and the DEM neighbour data
+ * are rebuilt by the next step from the loaded positions, so a run that is
+ * saved and resumed continues as it would have (up to the order of the
+ * FP64 force atomics).  Single simulations only: EUNSUPPORTED for batches,
+ * slab decompositions and their members.  Both synchronise. */
+int lbm_imb_save(lbm_imb_t* h, const char* path);
+int lbm_imb_load(lbm_imb_t* h, const char* path);
 
 /* ---- batches of independent suspensions ----
  * A batch advances n independent suspensions (same dim and storage; any
@@ -279,10 +329,6 @@ int lbm_imb_batch_size(lbm_imb_t* h, int* n);
 int lbm_imb_batch_set_launch(lbm_imb_t* batch, int tile_x, int blocks_per_sm);
 int lbm_imb_batch_get_launch(lbm_imb_t* batch, int* tile_x, int* grid);
 
-/* Test hook for the barrier timeout path: poll limit of every barrier wait
- * (default 2^25 polls of ~64 ns) and a number of arrivals the barriers wait
- * for beyond the grid (0 in normal use; > 0 makes every wait run out). */
-int lbm_imb_batch_set_barrier_test(lbm_imb_t* batch, int64_t spin_limit, int phantom_arrivals);
 
 /* ---- standalone DEM contact forces (Eqs. 4-5) ----
  * The cell-list contact kernel of the time step, callable on its own: for n
@@ -376,27 +422,8 @@ int lbm_imb_mlp_gradients(lbm_imb_mlp_t* m, const float* x, const float* t, int6
 int lbm_imb_mlp_train_steps(lbm_imb_mlp_t* m, const float* x, const float* t, int64_t n,
                             int64_t batch, int64_t steps, float lr, float* last_loss);
 int lbm_imb_mlp_destroy(lbm_imb_mlp_t* m);
-/* Test hook for the tensor-core operand layout: D [128][N] = A [128][K] *
- * B [N][K]^T with BF16 host inputs (raw bits, row-major) and FP32 host
- * output, through one tcgen05 product; dev_scratch >= 128 KB + 256,
- * 256-byte aligned; N, K in {16, 32, ..., 128}. */
-int lbm_imb_mlp_probe_gemm(const uint16_t* a_host, const uint16_t* b_host, int N, int K,
-                           float* d_host, void* dev_scratch, size_t scratch_bytes, void* stream);
 
-/* Test hook for the first-quadrant arctangent of the exact-volume formulas
- * (FP64 rasterisation): for device arrays y, x [n] (y, x >= 0, not both
- * zero) writes the library's atan2 to fast [n] and CUDA's atan2 to ref [n]
- * (device arrays, caller-owned), then synchronises the stream.  n > 2^31
- * elements is not supported.  EINVAL on null pointers or n < 0. */
-int lbm_imb_probe_atan2q1(const double* y, const double* x, double* fast, double* ref, int64_t n, void* stream);
 
-/* Test hook for the FP64 <-> FP32-pair conversions of the pair storage
- * (LBM_IMB_STORE_DFDEV, covered nodes): for device arrays of n elements writes
- * to_double[i] = the FP64 value of the pair (h[i], l[i]) (|l| at most half
- * an FP32 ulp of h) and roundtrip[i] = d[i] split into a pair and converted
- * back, then synchronises the stream.  EINVAL on null pointers or n < 0. */
-int lbm_imb_probe_df(const float* h, const float* l, const double* d, double* to_double, double* roundtrip,
-                     int64_t n, void* stream);
 
 /* One lattice decomposed along y into nslabs (2..16) slabs on this device,
  * exchanging halo rows after every collision: the multi-GPU design of the
@@ -419,6 +446,40 @@ size_t lbm_imb_slabs_required_bytes(const lbm_imb_config* cfg, int nslabs);
 int lbm_imb_slabs_init(const lbm_imb_config* cfg, int nslabs, void* dev_buf, size_t bytes,
                        void* cuda_stream, lbm_imb_t** out);
 int lbm_imb_slab_member(lbm_imb_t* h, int i, lbm_imb_t** member);
+
+/* ==================================================================
+ * Test hooks.  Not part of the simulation interface: they expose one
+ * internal piece each (a barrier's timeout path, the tensor-core operand
+ * layout, the arctangent and the FP64 <-> pair conversions of the exact
+ * covered fractions) so that tests can check it against a reference.
+ * ================================================================== */
+
+/* Test hook for the barrier timeout path: poll limit of every barrier wait
+ * (default 2^25 polls of ~64 ns) and a number of arrivals the barriers wait
+ * for beyond the grid (0 in normal use; > 0 makes every wait run out). */
+int lbm_imb_batch_set_barrier_test(lbm_imb_t* batch, int64_t spin_limit, int phantom_arrivals);
+
+/* Test hook for the tensor-core operand layout: D [128][N] = A [128][K] *
+ * B [N][K]^T with BF16 host inputs (raw bits, row-major) and FP32 host
+ * output, through one tcgen05 product; dev_scratch >= 128 KB + 256,
+ * 256-byte aligned; N, K in {16, 32, ..., 128}. */
+int lbm_imb_mlp_probe_gemm(const uint16_t* a_host, const uint16_t* b_host, int N, int K,
+                           float* d_host, void* dev_scratch, size_t scratch_bytes, void* stream);
+
+/* Test hook for the first-quadrant arctangent of the exact-volume formulas
+ * (FP64 rasterisation): for device arrays y, x [n] (y, x >= 0, not both
+ * zero) writes the library's atan2 to fast [n] and CUDA's atan2 to ref [n]
+ * (device arrays, caller-owned), then synchronises the stream.  n > 2^31
+ * elements is not supported.  EINVAL on null pointers or n < 0. */
+int lbm_imb_probe_atan2q1(const double* y, const double* x, double* fast, double* ref, int64_t n, void* stream);
+
+/* Test hook for the FP64 <-> FP32-pair conversions of the pair storage
+ * (LBM_IMB_STORE_DFDEV, covered nodes): for device arrays of n elements writes
+ * to_double[i] = the FP64 value of the pair (h[i], l[i]) (|l| at most half
+ * an FP32 ulp of h) and roundtrip[i] = d[i] split into a pair and converted
+ * back, then synchronises the stream.  EINVAL on null pointers or n < 0. */
+int lbm_imb_probe_df(const float* h, const float* l, const double* d, double* to_double, double* roundtrip,
+                     int64_t n, void* stream);
 
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */

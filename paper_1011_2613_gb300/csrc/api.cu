@@ -2,6 +2,7 @@
 // layout of the caller's device block, the per-step schedule (captured once
 // per ping-pong parity into a CUDA graph), and the synchronising accessors.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -25,6 +26,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kStageMax = 64ull << 20;  // staging for host-side field copies
+constexpr int64_t kHealthEvery = 100;      // default steps between health checks
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -47,6 +49,30 @@ struct Layout {
   size_t total;
 };
 
+// particle state the kernels accept: finite velocities and spins, finite
+// centres inside the walls (y in [-1/2, ny - 1/2] when wall_y) and in
+// [-1/2, n) along periodic axes (the DEM keeps wrapped centres in [0, n);
+// any two centres then differ by less than n + 1/2, which one minimum-image
+// wrap resolves)
+int check_particle_state(int dim, const int ext[3], int wall_y, int64_t n, const double* pos,
+                         const double* vel, const double* omega) {
+  for (int64_t p = 0; p < n; p++) {
+    for (int d = 0; d < 3; d++) {
+      if (vel && !isfinite(vel[3 * p + d])) return LBM_IMB_EINVAL;
+      if (omega && !isfinite(omega[3 * p + d])) return LBM_IMB_EINVAL;
+      if (!pos || d >= dim) continue;
+      const double x = pos[3 * p + d], L = (double)ext[d];
+      if (!isfinite(x)) return LBM_IMB_EINVAL;
+      if (d == 1 && wall_y) {
+        if (x < -0.5 || x > L - 0.5) return LBM_IMB_EINVAL;
+      } else if (x < -0.5 || x >= L) {
+        return LBM_IMB_EINVAL;
+      }
+    }
+  }
+  return LBM_IMB_OK;
+}
+
 int validate(const lbm_imb_config* c) {
   if (!c || c->struct_size < sizeof(lbm_imb_config)) return LBM_IMB_EINVAL;
   if (c->dim != 2 && c->dim != 3) return LBM_IMB_EINVAL;
@@ -66,11 +92,39 @@ int validate(const lbm_imb_config* c) {
     if (!(c->k_n >= 0.0) || !(c->restitution > 0.0 && c->restitution <= 1.0)) return LBM_IMB_EINVAL;
     for (int64_t p = 0; p < c->n_particles; p++) {
       if (!(c->radius[p] > 0.0) || !(c->density[p] > 0.0)) return LBM_IMB_EINVAL;
-      for (int d = 0; d < 3; d++)
-        if (!isfinite(c->pos[3 * p + d])) return LBM_IMB_EINVAL;
+      if (!isfinite(c->radius[p]) || !isfinite(c->density[p])) return LBM_IMB_EINVAL;
     }
+    const int ext[3] = {c->nx, c->ny, c->dim == 3 ? c->nz : 1};
+    const int st = check_particle_state(c->dim, ext, c->wall_y, c->n_particles, c->pos, c->vel, c->omega);
+    if (st) return st;
   }
   return LBM_IMB_OK;
+}
+
+// FNV-1a over the configuration's values (not its pointers or padding):
+// a checkpoint loads only into a simulation of the same configuration
+uint64_t config_hash(const lbm_imb_config* c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; i++) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  const int32_t ints[9] = {c->dim, c->nx, c->ny, c->dim == 3 ? c->nz : 1, c->wall_y, c->storage,
+                           c->dem_substeps, c->eps_method, 0};
+  mix(ints, sizeof(ints));
+  const double dbl[11] = {c->tau, c->body_force[0], c->body_force[1], c->body_force[2], c->gravity[0],
+                          c->gravity[1], c->gravity[2], c->rho_fluid, c->k_n, c->restitution, c->dem_skin};
+  mix(dbl, sizeof(dbl));
+  const int64_t np = c->n_particles;
+  mix(&np, sizeof(np));
+  if (np > 0) {
+    mix(c->radius, sizeof(double) * (size_t)np);
+    mix(c->density, sizeof(double) * (size_t)np);
+  }
+  return h;
 }
 
 int make_layout(const lbm_imb_config* c, Layout* L) {
@@ -147,13 +201,7 @@ int make_layout(const lbm_imb_config* c, Layout* L) {
   return LBM_IMB_OK;
 }
 
-int map_err(int bits) {
-  if (bits & lbm::ERR_TIMEOUT) return LBM_IMB_ETIMEOUT;
-  if (bits & lbm::ERR_OWNERS) return LBM_IMB_EOWNERS;
-  if (bits & lbm::ERR_BIN) return LBM_IMB_EBIN;
-  if (bits & lbm::ERR_NONFINITE) return LBM_IMB_ENONFINITE;
-  return LBM_IMB_OK;
-}
+int map_err(int bits) { return lbm::status_of_err_bits(bits); }
 
 }  // namespace
 
@@ -186,6 +234,8 @@ struct lbm_imb {
   long long N;
   double* stage;
   size_t stage_bytes;
+  int64_t health_every;  // health check every this many steps (0: never)
+  uint64_t cfg_hash;     // of the configuration at init (checkpoints)
 };
 
 namespace {
@@ -228,6 +278,24 @@ void enqueue_step(lbm_imb* h, int src) {
   lbm::launch_eps_raster(v, h->smem, h->stream);
   lbm::launch_collide(v, h->stream);
   lbm::launch_dem(v, h->stream);
+}
+
+// health check of the stored populations and particle state (every member
+// of a batch or slab decomposition); sets ERR_NONFINITE, reported by the
+// next synchronising call
+void enqueue_health(lbm_imb* h) {
+  if (h->is_batch || h->is_slab) {
+    for (int k = 0; k < h->nm; k++) {
+      lbm_imb* m = h->members + k;
+      lbm::launch_health(view_of(m, m->cur), m->f[m->cur], h->stream);
+    }
+    return;
+  }
+  lbm::launch_health(view_of(h, h->cur), h->f[h->cur], h->stream);
+}
+
+void maybe_health(lbm_imb* h) {
+  if (h->health_every > 0 && h->steps % h->health_every == 0) enqueue_health(h);
 }
 
 void try_capture(lbm_imb* h) {
@@ -413,6 +481,8 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   h->N = (long long)c->nx * c->ny * nz;
   h->stage = reinterpret_cast<double*>(base + L.off_stage);
   h->stage_bytes = L.stage_bytes;
+  h->health_every = kHealthEvery;
+  h->cfg_hash = config_hash(c);
 
   // particle state on the host first (derived masses as in the method)
   int st = LBM_IMB_OK;
@@ -675,6 +745,7 @@ int lbm_imb_batch_init(const lbm_imb_config* cfgs, int n, int tile_x, int blocks
   if (!st) {
     h->is_batch = true;
     h->nm = n;
+    h->health_every = kHealthEvery;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->dim = cfgs[0].dim;
     h->v.storage = cfgs[0].storage;
@@ -807,6 +878,7 @@ int lbm_imb_slabs_init(const lbm_imb_config* c, int nslabs, void* dev_buf, size_
   if (!st) {
     h->is_slab = true;
     h->nm = nslabs;
+    h->health_every = kHealthEvery;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     int y_start = 0;
     for (int k = 0; k < nslabs && !st; k++) {
@@ -975,6 +1047,7 @@ int lbm_imb_step(lbm_imb_t* h, int64_t n) {
         h->members[k].cur = h->cur;
         h->members[k].steps = h->steps;
       }
+      maybe_health(h);
     }
     return check_cuda(cudaGetLastError());
   }
@@ -991,6 +1064,7 @@ int lbm_imb_step(lbm_imb_t* h, int64_t n) {
       h->members[k].cur = h->cur;
       h->members[k].steps = h->steps;
     }
+    maybe_health(h);
   }
   return check_cuda(cudaGetLastError());
 }
@@ -1042,6 +1116,7 @@ int lbm_imb_step_profiled(lbm_imb_t* h, int64_t n, double* kernel_ms, double* to
     e = cudaEventRecord(s[4], h->stream);
     h->cur ^= 1;
     h->steps++;
+    maybe_health(h);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1114,6 +1189,10 @@ int lbm_imb_particles(lbm_imb_t* h, double* pos, double* vel, double* omega, dou
 int lbm_imb_set_particles(lbm_imb_t* h, const double* pos, const double* vel, const double* omega,
                           int64_t n) {
   if (!h || n != h->np) return LBM_IMB_EINVAL;
+  const View& gv = h->v;  // ny_glob: the whole lattice's rows (also for a slab)
+  const int ext[3] = {gv.nx, gv.ny_glob, gv.nz};
+  const int st = check_particle_state(h->dim, ext, gv.wall_y, n, pos, vel, omega);
+  if (st) return st;
   const size_t b = 24ull * h->np;
   cudaError_t e = cudaSuccess;
   if (h->np > 0) {
@@ -1252,6 +1331,137 @@ int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant) {
   h->graphs_ok = false;
   h->graphs_tried = false;
   h->v.collide_variant = variant;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_set_health_check(lbm_imb_t* h, int64_t every) {
+  if (!h || h->is_member || every < 0) return LBM_IMB_EINVAL;
+  h->health_every = every;
+  return LBM_IMB_OK;
+}
+
+int lbm_imb_check_health(lbm_imb_t* h) {
+  if (!h || h->is_member) return LBM_IMB_EINVAL;
+  enqueue_health(h);
+  if (cudaGetLastError() != cudaSuccess) return LBM_IMB_ECUDA;
+  return h->is_batch ? batch_read_err(h) : read_err(h);
+}
+
+// ---- checkpoints ----
+// File: a fixed header, then the stored populations of the current lattice
+// (raw storage bytes, Q planes of pitch * ny * nz elements), then the
+// particle arrays pos, vel, omega, force, torque ([n][3] FP64 each).
+namespace {
+struct CkptHeader {
+  char magic[8];        // "LBMIMBCK"
+  uint32_t version;     // 1
+  uint32_t header_bytes;
+  uint64_t cfg_hash;
+  int32_t dim, nx, ny, nz, Q, storage, pitch, esz;
+  int64_t np, steps;
+  uint64_t pop_bytes, particle_bytes;
+};
+constexpr char kCkptMagic[8] = {'L', 'B', 'M', 'I', 'M', 'B', 'C', 'K'};
+
+void ckpt_header(const lbm_imb* h, CkptHeader* H) {
+  memset(H, 0, sizeof(*H));
+  memcpy(H->magic, kCkptMagic, 8);
+  H->version = 1;
+  H->header_bytes = sizeof(CkptHeader);
+  H->cfg_hash = h->cfg_hash;
+  H->dim = h->dim;
+  H->nx = h->v.nx;
+  H->ny = h->v.ny;
+  H->nz = h->v.nz;
+  H->Q = h->Q;
+  H->storage = h->v.storage;
+  H->pitch = h->v.pitch;
+  H->esz = lbm::pop_bytes(h->v.storage);
+  H->np = h->np;
+  H->steps = h->steps;
+  H->pop_bytes = (uint64_t)h->Q * (uint64_t)h->v.plane * (uint64_t)H->esz;
+  H->particle_bytes = 5ull * 24ull * (uint64_t)h->np;
+}
+
+// device range <-> file through the staging area, in chunks
+int ckpt_copy(lbm_imb* h, FILE* fp, unsigned char* dev, uint64_t bytes, bool to_file) {
+  unsigned char* buf = static_cast<unsigned char*>(malloc(h->stage_bytes));
+  if (!buf) return LBM_IMB_ENOMEM;
+  int st = LBM_IMB_OK;
+  for (uint64_t o = 0; o < bytes && !st; o += h->stage_bytes) {
+    const size_t n = (size_t)(bytes - o < h->stage_bytes ? bytes - o : h->stage_bytes);
+    if (to_file) {
+      if (cudaMemcpyAsync(buf, dev + o, n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess)
+        st = LBM_IMB_ECUDA;
+      else if (fwrite(buf, 1, n, fp) != n)
+        st = LBM_IMB_EINVAL;
+    } else {
+      if (fread(buf, 1, n, fp) != n)
+        st = LBM_IMB_EINVAL;
+      else if (cudaMemcpyAsync(dev + o, buf, n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+               cudaStreamSynchronize(h->stream) != cudaSuccess)
+        st = LBM_IMB_ECUDA;
+    }
+  }
+  free(buf);
+  return st;
+}
+
+double* particle_array(lbm_imb* h, int k) {
+  double* a[5] = {h->v.pos, h->v.vel, h->v.omg, h->v.ff, h->v.tf};
+  return a[k];
+}
+}  // namespace
+
+int lbm_imb_save(lbm_imb_t* h, const char* path) {
+  if (!h || !path || h->is_batch || h->is_slab || h->is_member) return h && path ? LBM_IMB_EUNSUPPORTED
+                                                                                     : LBM_IMB_EINVAL;
+  int st = read_err(h);  // a failed run is not saved
+  if (st) return st;
+  CkptHeader H;
+  ckpt_header(h, &H);
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return LBM_IMB_EINVAL;
+  if (fwrite(&H, sizeof(H), 1, fp) != 1) st = LBM_IMB_EINVAL;
+  if (!st) st = ckpt_copy(h, fp, static_cast<unsigned char*>(h->f[h->cur]), H.pop_bytes, true);
+  for (int k = 0; k < 5 && !st && h->np > 0; k++)
+    st = ckpt_copy(h, fp, reinterpret_cast<unsigned char*>(particle_array(h, k)), 24ull * h->np, true);
+  if (fclose(fp) != 0 && !st) st = LBM_IMB_EINVAL;
+  return st;
+}
+
+int lbm_imb_load(lbm_imb_t* h, const char* path) {
+  if (!h || !path || h->is_batch || h->is_slab || h->is_member) return h && path ? LBM_IMB_EUNSUPPORTED
+                                                                                     : LBM_IMB_EINVAL;
+  int st = read_err(h);
+  if (st) return st;
+  CkptHeader want, got;
+  ckpt_header(h, &want);
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return LBM_IMB_EINVAL;
+  if (fread(&got, sizeof(got), 1, fp) != 1 || memcmp(got.magic, kCkptMagic, 8) != 0 || got.version != 1 ||
+      got.header_bytes != sizeof(CkptHeader) || got.cfg_hash != want.cfg_hash || got.dim != want.dim ||
+      got.nx != want.nx || got.ny != want.ny || got.nz != want.nz || got.Q != want.Q ||
+      got.storage != want.storage || got.pitch != want.pitch || got.esz != want.esz || got.np != want.np ||
+      got.pop_bytes != want.pop_bytes || got.particle_bytes != want.particle_bytes || got.steps < 0) {
+    fclose(fp);
+    return LBM_IMB_EINVAL;
+  }
+  st = ckpt_copy(h, fp, static_cast<unsigned char*>(h->f[h->cur]), got.pop_bytes, false);
+  for (int k = 0; k < 5 && !st && h->np > 0; k++)
+    st = ckpt_copy(h, fp, reinterpret_cast<unsigned char*>(particle_array(h, k)), 24ull * h->np, false);
+  fclose(fp);
+  if (st) return st;
+  // Verlet lists (dem_skin > 0) are rebuilt from the loaded positions at the
+  // next step: the same pairs, so the same contact forces
+  if (h->v.dem_skin > 0.0) {
+    const int one = 1;
+    if (cudaMemcpyAsync(h->v.vl_flag, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return LBM_IMB_ECUDA;
+  }
+  h->steps = got.steps;
   return LBM_IMB_OK;
 }
 

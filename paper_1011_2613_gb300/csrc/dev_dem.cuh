@@ -20,6 +20,15 @@ __device__ __forceinline__ int dem_bin_coord(double x, int d, const View& v) {
 }
 
 __device__ __forceinline__ void dem_bin_particle(const View& v, int p) {
+  // a non-finite (or runaway) centre is reported and left out of the bins,
+  // so no other particle meets it; its own contact scan finds nothing
+  bool bad = false;
+  for (int d = 0; d < v.dim; d++) bad |= !(fabs(v.pos[3 * p + d]) <= kPosLimit);
+  if (bad) {
+    v.bin_of[p] = -1;
+    atomicOr(v.err, ERR_NONFINITE);
+    return;
+  }
   int b[3] = {0, 0, 0};
   for (int d = 0; d < v.dim; d++) b[d] = dem_bin_coord(v.pos[3 * p + d], d, v);
   const int bin = (b[2] * v.nb[1] + b[1]) * v.nb[0] + b[0];
@@ -280,7 +289,13 @@ __device__ __forceinline__ void dem_integrate_particle(const View& v, int i, dou
     v.pos[3 * i + d] = x;
   }
   const double I = v.inertia[i];
-  for (int d = 0; d < 3; d++) v.omg[3 * i + d] = __dadd_rn(v.omg[3 * i + d], __dmul_rn(v.tf[3 * i + d] / I, dt));
+  bool bad = false;
+  for (int d = 0; d < 3; d++) {
+    const double w = __dadd_rn(v.omg[3 * i + d], __dmul_rn(v.tf[3 * i + d] / I, dt));
+    v.omg[3 * i + d] = w;
+    bad |= !isfinite(w) || !isfinite(v.vel[3 * i + d]) || !(fabs(v.pos[3 * i + d]) <= kPosLimit);
+  }
+  if (bad) atomicOr(v.err, ERR_NONFINITE);  // reported; the state is left as computed
 }
 
 }  // namespace lbm

@@ -422,6 +422,19 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   const T R = from_f64<T>(R64);
   const double c[3] = {v.pos[3 * p], v.pos[3 * p + 1], v.pos[3 * p + 2]};
   int lo[3] = {0, 0, 0}, ne[3] = {1, 1, 1};
+  // a non-finite (or runaway) centre is reported and the particle covers no
+  // cell: its box is recorded empty so the next clear walks nothing, and no
+  // index is formed from it (block-uniform)
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < DIM; d++) bad |= !(fabs(c[d]) <= kPosLimit);
+  if (bad) {
+    if (threadIdx.x == 0) {
+      for (int d = 0; d < 6; d++) v.lo[6 * p + d] = 0;
+      atomicOr(v.err, ERR_NONFINITE);
+    }
+    return;
+  }
 #pragma unroll
   for (int d = 0; d < DIM; d++) {
     lo[d] = (int)ceil(c[d] - R64 - 0.5);

@@ -154,6 +154,45 @@ __global__ void zero_red_kernel(double* red) {
   if (threadIdx.x < 8) red[threadIdx.x] = 0.0;
 }
 
+// Health check.  A NaN or Inf in any population of a node reaches the
+// node's density and velocity, and through them every population the
+// collision writes there, the rest direction included; a population that
+// streams it elsewhere does the same at the next node one step later.  So
+// the stored rest-direction plane (1/Q of the lattice) shows every
+// non-finite population within one step of its appearance.  The particle
+// state is scanned beside it.  Any hit sets ERR_NONFINITE.
+__device__ __forceinline__ bool stored_finite(const void* f, int storage, long long i) {
+  if (storage == LBM_IMB_STORE_F64) return isfinite(static_cast<const double*>(f)[i]);
+  if (storage == LBM_IMB_STORE_DFDEV) {
+    const float2 p = static_cast<const float2*>(f)[i];
+    return isfinite(p.x) && isfinite(p.y);
+  }
+  if (storage == LBM_IMB_STORE_F32DEV) return isfinite(static_cast<const float*>(f)[i]);
+  return isfinite(__half2float(static_cast<const __half*>(f)[i]));
+}
+
+__global__ void health_kernel(View v, const void* f) {
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.plane; i += stride)
+    bad |= !stored_finite(f, v.storage, i);  // direction 0: the first plane
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3LL * v.np; i += stride)
+    bad |= !(fabs(v.pos[i]) <= kPosLimit) || !isfinite(v.vel[i]) || !isfinite(v.omg[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(v.err, ERR_NONFINITE);
+}
+
+void launch_health(const View& v, const void* f, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long work = v.plane > 3LL * v.np ? v.plane : 3LL * v.np;
+  long long blocks = (work + 255) / 256;
+  const long long cap = 4LL * (sms > 0 ? sms : 1);
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  health_kernel<<<(unsigned)blocks, 256, 0, s>>>(v, f);
+}
+
 void launch_init_equilibrium(const View& v, void* f, cudaStream_t s) {
   const int T = 256;
   const long long blocks = (v.plane + T - 1) / T;

@@ -15,6 +15,20 @@ constexpr int kVerletCap = 48;  // partners per Verlet list
 // device error word bits
 enum : int { ERR_OWNERS = 1, ERR_BIN = 2, ERR_NONFINITE = 4, ERR_TIMEOUT = 8 };
 
+// status of a device error word (the most severe condition first)
+inline int status_of_err_bits(int bits) {
+  if (bits & ERR_TIMEOUT) return LBM_IMB_ETIMEOUT;
+  if (bits & ERR_OWNERS) return LBM_IMB_EOWNERS;
+  if (bits & ERR_BIN) return LBM_IMB_EBIN;
+  if (bits & ERR_NONFINITE) return LBM_IMB_ENONFINITE;
+  return LBM_IMB_OK;
+}
+
+// largest |coordinate| of a particle centre the kernels index with (lattice
+// units); beyond it (or NaN/Inf) the particle is reported as ERR_NONFINITE
+// and skipped, which keeps every box origin and extent inside int range
+constexpr double kPosLimit = 1073741824.0;  // 2^30
+
 // ---------------------------------------------------------------------------
 // Lattice descriptors (interface direction order: rest, then opposite pairs).
 // All loops over directions are unrolled, so every lookup folds to a literal.
@@ -185,6 +199,9 @@ void launch_get_populations(const View& v, const void* f, long long row0, long l
 void launch_set_populations(const View& v, void* f, long long row0, long long nrows, const double* in,
                             cudaStream_t s);
 void launch_totals(const View& v, const void* f, cudaStream_t s);
+// health check: non-finite stored rest populations or particle state set
+// ERR_NONFINITE in the error word
+void launch_health(const View& v, const void* f, cudaStream_t s);
 void launch_drag_samples(const View& v, const double* u, const double* eps, double shell, float* feats,
                          float* target, cudaStream_t s);
 

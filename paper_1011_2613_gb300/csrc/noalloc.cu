@@ -112,5 +112,5 @@ extern "C" int lbm_imb_dem_forces_static(int32_t dim, const int32_t* extent, int
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, v.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return LBM_IMB_ECUDA;
-  return bits ? LBM_IMB_EBIN : LBM_IMB_OK;
+  return lbm::status_of_err_bits(bits);
 }

@@ -93,6 +93,14 @@ def lib():
             L.lbm_imb_set_populations.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
             L.lbm_imb_totals.restype = C.c_int
             L.lbm_imb_totals.argtypes = [C.c_void_p, _dp, _dp, _dp]
+            L.lbm_imb_set_health_check.restype = C.c_int
+            L.lbm_imb_set_health_check.argtypes = [C.c_void_p, C.c_int64]
+            L.lbm_imb_check_health.restype = C.c_int
+            L.lbm_imb_check_health.argtypes = [C.c_void_p]
+            L.lbm_imb_save.restype = C.c_int
+            L.lbm_imb_save.argtypes = [C.c_void_p, C.c_char_p]
+            L.lbm_imb_load.restype = C.c_int
+            L.lbm_imb_load.argtypes = [C.c_void_p, C.c_char_p]
             L.lbm_imb_steps_done.restype = C.c_int
             L.lbm_imb_steps_done.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
             L.lbm_imb_dem_workspace_bytes.restype = C.c_size_t
@@ -289,6 +297,23 @@ class Simulation:
 
     def sync(self):
         _check(lib().lbm_imb_sync(self.h), "lbm_imb_sync")
+
+    def set_health_check(self, every: int):
+        """Steps between the health checks of step() (0: off)."""
+        _check(lib().lbm_imb_set_health_check(self.h, int(every)), "lbm_imb_set_health_check")
+
+    def check_health(self):
+        """Scan the stored state for NaN/Inf now (raises LbmImbError with
+        status ENONFINITE if found)."""
+        _check(lib().lbm_imb_check_health(self.h), "lbm_imb_check_health")
+
+    def save(self, path):
+        """Checkpoint the simulation to a file (lbm_imb_save)."""
+        _check(lib().lbm_imb_save(self.h, os.fsencode(path)), "lbm_imb_save")
+
+    def load(self, path):
+        """Resume from a checkpoint of the same configuration (lbm_imb_load)."""
+        _check(lib().lbm_imb_load(self.h, os.fsencode(path)), "lbm_imb_load")
 
     def steps_done(self) -> int:
         s = C.c_int64()

@@ -35,13 +35,13 @@ def test_tcgen05_product_layout(N, K):
     assert np.max(np.abs(d - ref)) <= 1e-5 * max(1.0, np.abs(ref).max()) * K
 
 
-def _net(seed=0):
+def _net(seed=0, max_batch=4096):
     from paper_1011_2613_gb300 import closure as CL
 
     W, b = M.init_params(seed)
     rng = np.random.default_rng(seed + 1)
     b = [0.05 * rng.standard_normal(v.shape) for v in b]
-    mlp = CL.MLP(max_batch=1024, seed=seed)
+    mlp = CL.MLP(max_batch=max_batch, seed=seed)
     mlp.set_params(CL.layers_to_flat(W, b))
     # the GPU holds FP32 masters: compare against the same FP32 values
     W, b = CL.flat_to_layers(mlp.get_params())
@@ -49,32 +49,48 @@ def _net(seed=0):
 
 
 def test_forward_matches_oracle():
+    """Element by element, within 1e-3 of the largest output, against the
+    oracle with the same bfloat16 rounding points (x, W_l, every hidden
+    activation), FP64 accumulation; and loosely against the unrounded FP64
+    network."""
     import torch
 
     mlp, W, b = _net(3)
     x = np.random.default_rng(4).standard_normal((300, 6)).astype(np.float32)
     y = mlp.predict(torch.tensor(x, device="cuda")).cpu().numpy()
     yr, _ = M.forward(W, b, x.astype(np.float64), bf16=True)
-    assert np.max(np.abs(y - yr)) <= 2e-2 * np.abs(yr).max()
+    err = float(np.max(np.abs(y - yr)) / np.abs(yr).max())
+    print(f"forward: max |y - oracle| / max |oracle| = {err:.2e}")
+    assert err <= 1e-3
     y64, _ = M.forward(W, b, x.astype(np.float64), bf16=False)
     assert np.max(np.abs(y - y64)) <= 6e-2 * np.abs(y64).max()
 
 
-def test_gradients_match_oracle():
+@pytest.mark.parametrize("batch", [256, 1000, 4096])
+def test_gradients_match_oracle(batch):
+    """Every weight and bias gradient element by element within 1e-3 of its
+    tensor's largest entry (the oracle rounds the same operands to bfloat16:
+    x, W_l, the activations and the back-propagated gradients), for a batch
+    of whole tiles, a ragged one and a large one."""
     import torch
     from paper_1011_2613_gb300 import closure as CL
 
     mlp, W, b = _net(5)
     rng = np.random.default_rng(6)
-    x = rng.standard_normal((256, 6)).astype(np.float32)
-    t = rng.standard_normal((256, 3)).astype(np.float32)
+    x = rng.standard_normal((batch, 6)).astype(np.float32)
+    t = rng.standard_normal((batch, 3)).astype(np.float32)
     g, loss = mlp.gradients(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"))
     gW, gb = CL.flat_to_layers(g)
     rW, rb, rloss = M.gradients(W, b, x.astype(np.float64), t.astype(np.float64), bf16=True)
-    assert abs(loss - rloss) <= 2e-2 * rloss
+    assert abs(loss - rloss) <= 1e-3 * rloss
+    worst = 0.0
     for l in range(5):
-        assert np.linalg.norm(gW[l] - rW[l]) <= 5e-2 * np.linalg.norm(rW[l]), l
-        assert np.linalg.norm(gb[l] - rb[l]) <= 5e-2 * max(np.linalg.norm(rb[l]), 1e-12), l
+        ew = float(np.max(np.abs(gW[l] - rW[l])) / np.abs(rW[l]).max())
+        eb = float(np.max(np.abs(gb[l] - rb[l])) / max(np.abs(rb[l]).max(), 1e-30))
+        worst = max(worst, ew, eb)
+        assert ew <= 1e-3, (l, ew)
+        assert eb <= 1e-3, (l, eb)
+    print(f"batch {batch}: worst gradient error {worst:.2e} of the tensor maximum")
 
 
 def test_one_adam_step():
