@@ -582,9 +582,16 @@ static double table_cell_fraction(const oracle_sim* s, const double c[3], double
 /* eps rasterisation: for each particle (ascending id) every node whose cell
  * meets the disk/ball receives (p, e_p) when e_p > 0.  Returns -1 when a node
  * would get more than OR_MAX_OWNERS owners. */
+/* The OpenMP pragmas below matter only to the timing build of this file
+ * (compiled with -fopenmp to time the oracle on all host cores); the parity
+ * build ignores them and runs every loop in the order written.  In the timing
+ * build particles rasterise concurrently (owner slots are appended under a
+ * critical section, so their order on a shared node may differ) and the
+ * force and torque sums are atomic (another summation order). */
 int oracle_rasterize(oracle_sim* s) {
   memset(s->own_n, 0, sizeof(int) * s->N);
   int status = 0;
+#pragma omp parallel for schedule(dynamic, 4)
   for (int p = 0; p < s->np; p++) {
     double c[3] = {s->pos[3 * p], s->pos[3 * p + 1], s->pos[3 * p + 2]};
     double R = s->rad[p];
@@ -610,14 +617,17 @@ int oracle_rasterize(oracle_sim* s) {
                                          : oracle_cell_fraction(s->dim, c[0], c[1], c[2], R, i, j, k);
           if (!(ev > 0.0)) continue;
           long n = node_index(s, idx[0], idx[1], idx[2]);
-          int m = s->own_n[n];
-          if (m >= OR_MAX_OWNERS) {
-            status = -1;
-            continue;
+#pragma omp critical(oracle_owner_slots)
+          {
+            int m = s->own_n[n];
+            if (m >= OR_MAX_OWNERS) {
+              status = -1;
+            } else {
+              s->own_p[n * OR_MAX_OWNERS + m] = p;
+              s->own_e[n * OR_MAX_OWNERS + m] = ev;
+              s->own_n[n] = m + 1;
+            }
           }
-          s->own_p[n * OR_MAX_OWNERS + m] = p;
-          s->own_e[n * OR_MAX_OWNERS + m] = ev;
-          s->own_n[n] = m + 1;
         }
   }
   return status;
@@ -703,6 +713,7 @@ void oracle_destroy(oracle_sim* s) {
 /* pull streaming of the stored post-collision populations into dst */
 static void stream_pull(const oracle_sim* s, const double* src, double* dst) {
   const int Q = s->L.Q;
+#pragma omp parallel for collapse(2)
   for (int z = 0; z < s->n[2]; z++)
     for (int y = 0; y < s->n[1]; y++)
       for (int x = 0; x < s->n[0]; x++) {
@@ -746,10 +757,11 @@ int oracle_step(oracle_sim* s, int nsteps) {
     /* 3-5. collision with IMB, force and torque */
     memset(s->ff, 0, sizeof(double) * 3 * s->np);
     memset(s->tf, 0, sizeof(double) * 3 * s->np);
-    double ftn[19], fo[19];
+#pragma omp parallel for collapse(2)
     for (int z = 0; z < s->n[2]; z++)
       for (int y = 0; y < s->n[1]; y++)
         for (int x = 0; x < s->n[0]; x++) {
+          double ftn[19], fo[19];
           long n = node_index(s, x, y, z);
           for (int i = 0; i < Q; i++) ftn[i] = s->ft[i * s->N + n];
           int no = s->own_n[n];
@@ -775,10 +787,14 @@ int oracle_step(oracle_sim* s, int nsteps) {
                 int p = s->own_p[n * OR_MAX_OWNERS + k];
                 double a = e[k] / esum;
                 double mp[3] = {a * m[0], a * m[1], a * m[2]};
-                for (int d = 0; d < 3; d++) s->ff[3 * p + d] -= mp[d];
-                s->tf[3 * p + 0] -= r[k][1] * mp[2] - r[k][2] * mp[1];
-                s->tf[3 * p + 1] -= r[k][2] * mp[0] - r[k][0] * mp[2];
-                s->tf[3 * p + 2] -= r[k][0] * mp[1] - r[k][1] * mp[0];
+                double tq[3] = {r[k][1] * mp[2] - r[k][2] * mp[1], r[k][2] * mp[0] - r[k][0] * mp[2],
+                                r[k][0] * mp[1] - r[k][1] * mp[0]};
+                for (int d = 0; d < 3; d++) {
+#pragma omp atomic
+                  s->ff[3 * p + d] -= mp[d];
+#pragma omp atomic
+                  s->tf[3 * p + d] -= tq[d];
+                }
               }
             }
           }

@@ -21,8 +21,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
+# timing build: the same source with OpenMP (loops over nodes and particles
+# on all host cores; forces summed atomically), used only to time the oracle
+_LIB_OMP = os.path.join(_HERE, "liblbm_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 # -ffp-contract=off: no fused multiply-add contraction, so that the oracle's
 # rounding is the plain IEEE sequence of the source on x86 and on Arm alike.
@@ -38,54 +42,88 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_timing(force: bool = False):
+    """Compile the OpenMP timing build of the oracle; returns its path, or
+    None if the compiler has no OpenMP (the timing then uses one core)."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + ".tmp%d" % os.getpid()
+        try:
+            subprocess.check_call(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"],
+                                  stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (subprocess.CalledProcessError, OSError):
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def timing_threads() -> int:
+    """Threads the OpenMP timing build uses (OMP_NUM_THREADS, else the
+    host's cores), or 1 without that build."""
+    if build_timing() is None:
+        return 1
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
+
+
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
 
 
-def _load():
-    global _lib
+def _load(timing: bool = False):
+    """The parity build (default) or the OpenMP timing build."""
+    global _lib, _lib_omp
     with _lock:
+        if timing:
+            if _lib_omp is None:
+                path = build_timing()
+                _lib_omp = _declare(C.CDLL(path)) if path else None
+            if _lib_omp is not None:
+                return _lib_omp
         if _lib is None:
-            lib = C.CDLL(build())
-            lib.oracle_area_disk_rect.restype = C.c_double
-            lib.oracle_area_disk_rect.argtypes = [C.c_double] * 7
-            lib.oracle_volume_ball_box.restype = C.c_double
-            lib.oracle_volume_ball_box.argtypes = [C.c_double] * 10
-            lib.oracle_cell_fraction.restype = C.c_double
-            lib.oracle_cell_fraction.argtypes = [C.c_int] + [C.c_double] * 7
-            lib.oracle_set_eps_table.restype = C.c_int
-            lib.oracle_set_eps_table.argtypes = [C.c_void_p]
-            lib.oracle_eps_table_value.restype = C.c_double
-            lib.oracle_eps_table_value.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
-            lib.oracle_collide_node.restype = C.c_double
-            lib.oracle_collide_node.argtypes = [C.c_int, C.c_double, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
-            lib.oracle_dem_advance.restype = None
-            lib.oracle_dem_advance.argtypes = [C.c_int, _ip, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
-                                               _dp, _dp, _dp, C.c_double, C.c_double, C.c_int, _dp]
-            lib.oracle_dem_contacts.restype = None
-            lib.oracle_dem_contacts.argtypes = [C.c_int, _ip, C.c_int, C.c_int, _dp, _dp, _dp, _dp, C.c_double,
-                                                C.c_double, _dp]
-            lib.oracle_create.restype = C.c_void_p
-            lib.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp,
-                                          C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
-                                          _dp, _dp, _dp, _dp, _dp]
-            lib.oracle_destroy.argtypes = [C.c_void_p]
-            lib.oracle_step.restype = C.c_int
-            lib.oracle_step.argtypes = [C.c_void_p, C.c_int]
-            lib.oracle_rasterize.restype = C.c_int
-            lib.oracle_rasterize.argtypes = [C.c_void_p]
-            lib.oracle_num_nodes.restype = C.c_long
-            lib.oracle_num_nodes.argtypes = [C.c_void_p]
-            lib.oracle_num_dirs.restype = C.c_int
-            lib.oracle_num_dirs.argtypes = [C.c_void_p]
-            lib.oracle_get_populations.argtypes = [C.c_void_p, _dp]
-            lib.oracle_set_populations.argtypes = [C.c_void_p, _dp]
-            lib.oracle_get_particles.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp]
-            lib.oracle_get_mass.argtypes = [C.c_void_p, _dp, _dp]
-            lib.oracle_fields.argtypes = [C.c_void_p, _dp, _dp, _dp]
-            lib.oracle_get_owners.argtypes = [C.c_void_p, _ip, _ip, _dp, C.c_int]
-            _lib = lib
+            _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    """Argument and result types of the oracle's C functions."""
+    lib.oracle_area_disk_rect.restype = C.c_double
+    lib.oracle_area_disk_rect.argtypes = [C.c_double] * 7
+    lib.oracle_volume_ball_box.restype = C.c_double
+    lib.oracle_volume_ball_box.argtypes = [C.c_double] * 10
+    lib.oracle_cell_fraction.restype = C.c_double
+    lib.oracle_cell_fraction.argtypes = [C.c_int] + [C.c_double] * 7
+    lib.oracle_set_eps_table.restype = C.c_int
+    lib.oracle_set_eps_table.argtypes = [C.c_void_p]
+    lib.oracle_eps_table_value.restype = C.c_double
+    lib.oracle_eps_table_value.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
+    lib.oracle_collide_node.restype = C.c_double
+    lib.oracle_collide_node.argtypes = [C.c_int, C.c_double, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
+    lib.oracle_dem_advance.restype = None
+    lib.oracle_dem_advance.argtypes = [C.c_int, _ip, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
+                                       _dp, _dp, _dp, C.c_double, C.c_double, C.c_int, _dp]
+    lib.oracle_dem_contacts.restype = None
+    lib.oracle_dem_contacts.argtypes = [C.c_int, _ip, C.c_int, C.c_int, _dp, _dp, _dp, _dp, C.c_double,
+                                        C.c_double, _dp]
+    lib.oracle_create.restype = C.c_void_p
+    lib.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp,
+                                  C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                                  _dp, _dp, _dp, _dp, _dp]
+    lib.oracle_destroy.argtypes = [C.c_void_p]
+    lib.oracle_step.restype = C.c_int
+    lib.oracle_step.argtypes = [C.c_void_p, C.c_int]
+    lib.oracle_rasterize.restype = C.c_int
+    lib.oracle_rasterize.argtypes = [C.c_void_p]
+    lib.oracle_num_nodes.restype = C.c_long
+    lib.oracle_num_nodes.argtypes = [C.c_void_p]
+    lib.oracle_num_dirs.restype = C.c_int
+    lib.oracle_num_dirs.argtypes = [C.c_void_p]
+    lib.oracle_get_populations.argtypes = [C.c_void_p, _dp]
+    lib.oracle_set_populations.argtypes = [C.c_void_p, _dp]
+    lib.oracle_get_particles.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.oracle_get_mass.argtypes = [C.c_void_p, _dp, _dp]
+    lib.oracle_fields.argtypes = [C.c_void_p, _dp, _dp, _dp]
+    lib.oracle_get_owners.argtypes = [C.c_void_p, _ip, _ip, _dp, C.c_int]
+    return lib
 
 
 def _p(a):
@@ -169,8 +207,11 @@ class OracleSim:
     rho_fluid, k_n, restitution, dem_substeps, pos, vel, omega, radius,
     density)."""
 
-    def __init__(self, cfg):
-        lib = _load()
+    def __init__(self, cfg, timing: bool = False):
+        """timing = True: the OpenMP timing build (all host cores, forces
+        summed atomically; for timing only, never for parity)."""
+        lib = _load(timing)
+        self._lib = lib
         self.dim = int(cfg.dim)
         self.shape = (int(cfg.nx), int(cfg.ny), int(cfg.nz) if self.dim == 3 else 1)
         self.np = len(cfg.radius)
@@ -204,11 +245,11 @@ class OracleSim:
         """Eq. 6 table value for a cell centred at ``offset`` from the particle
         centre (before the inside/outside classification and the clamp)."""
         o = [float(x) for x in offset] + [0.0] * (3 - len(offset))
-        return _load().oracle_eps_table_value(self.h, o[0], o[1], o[2])
+        return self._lib.oracle_eps_table_value(self.h, o[0], o[1], o[2])
 
     def close(self):
         if getattr(self, "h", None):
-            _load().oracle_destroy(self.h)
+            self._lib.oracle_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -218,7 +259,7 @@ class OracleSim:
             pass
 
     def step(self, n: int = 1) -> int:
-        st = _load().oracle_step(self.h, int(n))
+        st = self._lib.oracle_step(self.h, int(n))
         self.steps_done += int(n)
         if st != 0:
             raise RuntimeError("oracle: a node exceeded the owner limit")
@@ -227,27 +268,27 @@ class OracleSim:
     def populations(self) -> np.ndarray:
         """Stored post-collision populations, shape (Q, nz, ny, nx)."""
         f = np.zeros(self.Q * self.N)
-        _load().oracle_get_populations(self.h, _p(f))
+        self._lib.oracle_get_populations(self.h, _p(f))
         nx, ny, nz = self.shape
         return f.reshape(self.Q, nz, ny, nx)
 
     def set_populations(self, f):
         f = _f64(f, self.Q * self.N)
-        _load().oracle_set_populations(self.h, _p(f))
+        self._lib.oracle_set_populations(self.h, _p(f))
 
     def particles(self):
         """dict of (np,3) arrays: pos, vel, omega, force (hydrodynamic, last
         step), torque (hydrodynamic, last step), contact (last sub-step)."""
         n3 = 3 * max(self.np, 1)
         a = [np.zeros(n3) for _ in range(6)]
-        _load().oracle_get_particles(self.h, *[_p(x) for x in a])
+        self._lib.oracle_get_particles(self.h, *[_p(x) for x in a])
         keys = ["pos", "vel", "omega", "force", "torque", "contact"]
         return {k: v[: 3 * self.np].reshape(self.np, 3) for k, v in zip(keys, a)}
 
     def masses(self):
         m = np.zeros(max(self.np, 1))
         I = np.zeros(max(self.np, 1))
-        _load().oracle_get_mass(self.h, _p(m), _p(I))
+        self._lib.oracle_get_mass(self.h, _p(m), _p(I))
         return m[: self.np], I[: self.np]
 
     def fields(self):
@@ -255,7 +296,7 @@ class OracleSim:
         rho = np.zeros(self.N)
         u = np.zeros(self.dim * self.N)
         eps = np.zeros(self.N)
-        _load().oracle_fields(self.h, _p(rho), _p(u), _p(eps))
+        self._lib.oracle_fields(self.h, _p(rho), _p(u), _p(eps))
         nx, ny, nz = self.shape
         return rho.reshape(nz, ny, nx), u.reshape(self.dim, nz, ny, nx), eps.reshape(nz, ny, nx)
 
@@ -263,5 +304,5 @@ class OracleSim:
         cnt = np.zeros(self.N, dtype=np.int32)
         ids = np.zeros(self.N * maxo, dtype=np.int32)
         e = np.zeros(self.N * maxo)
-        _load().oracle_get_owners(self.h, cnt.ctypes.data_as(_ip), ids.ctypes.data_as(_ip), _p(e), maxo)
+        self._lib.oracle_get_owners(self.h, cnt.ctypes.data_as(_ip), ids.ctypes.data_as(_ip), _p(e), maxo)
         return cnt, ids.reshape(self.N, maxo), e.reshape(self.N, maxo)

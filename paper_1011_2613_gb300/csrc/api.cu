@@ -73,7 +73,10 @@ int check_particle_state(int dim, const int ext[3], int wall_y, int64_t n, const
   return LBM_IMB_OK;
 }
 
-int validate(const lbm_imb_config* c) {
+// check_positions = false for the per-slab layouts of a decomposed lattice
+// (their configs carry the whole lattice's particles; the whole config was
+// checked first)
+int validate(const lbm_imb_config* c, bool check_positions = true) {
   if (!c || c->struct_size < sizeof(lbm_imb_config)) return LBM_IMB_EINVAL;
   if (c->dim != 2 && c->dim != 3) return LBM_IMB_EINVAL;
   if (c->nx < 2 || c->ny < 2 || c->nz < 1) return LBM_IMB_EINVAL;
@@ -95,7 +98,8 @@ int validate(const lbm_imb_config* c) {
       if (!isfinite(c->radius[p]) || !isfinite(c->density[p])) return LBM_IMB_EINVAL;
     }
     const int ext[3] = {c->nx, c->ny, c->dim == 3 ? c->nz : 1};
-    const int st = check_particle_state(c->dim, ext, c->wall_y, c->n_particles, c->pos, c->vel, c->omega);
+    const int st = check_particle_state(c->dim, ext, c->wall_y, c->n_particles, check_positions ? c->pos : nullptr,
+                                        c->vel, c->omega);
     if (st) return st;
   }
   return LBM_IMB_OK;
@@ -127,8 +131,8 @@ uint64_t config_hash(const lbm_imb_config* c) {
   return h;
 }
 
-int make_layout(const lbm_imb_config* c, Layout* L) {
-  int st = validate(c);
+int make_layout(const lbm_imb_config* c, Layout* L, bool check_positions = true) {
+  int st = validate(c, check_positions);
   if (st) return st;
   const int nz = c->dim == 3 ? c->nz : 1;
   L->Q = c->dim == 2 ? 9 : 19;
@@ -831,7 +835,7 @@ static int slab_layout(const lbm_imb_config* c, int ns, SlabLayout* S) {
     if (S->ny_s[k] < 2) return LBM_IMB_EUNSUPPORTED;
     lbm_imb_config cs;
     slab_config(c, S->ny_s[k], &cs);
-    st = make_layout(&cs, &S->L[k]);
+    st = make_layout(&cs, &S->L[k], false);
     if (st) return st;
     S->off[k] = o;
     o = align_up(o + S->L[k].total);

@@ -460,10 +460,13 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ T kax[3][64];  // 3D: v (3 R^2 - v^2) / 2 of every axis value v
   __shared__ T ax_s[2][64], ax_psi[2][64];  // 2D per-axis tables
   __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
-  __shared__ int n_part, n_need, n_cov, cov_base;
-  // nodes whose first owner slot this particle claims (split collision)
+  __shared__ int n_part, n_need, cov_base, cov_wsum[4];
+  // nodes whose first owner slot this particle claims (split collision):
+  // one flag per cell of the box, compacted in box order (x fastest, then
+  // y, then z) at the end, so that the list holds each particle's nodes in
+  // row order and consecutive entries are mostly adjacent in memory
   const bool want_list = v.cov_list != nullptr && split_form(v.collide_variant);
-  int* s_cov = reinterpret_cast<int*>(smem + (TABLE ? 0 : raster_list_offset(cap, (int)sizeof(T))));
+  unsigned char* s_flag = smem + (TABLE ? 0 : raster_list_offset(cap, (int)sizeof(T)));
   const double R2 = R64 * R64;
   const float R2f = (float)R2;
   const T R2t = from_f64<T>(R2);
@@ -475,7 +478,6 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     }
     n_part = 0;
     n_need = 0;
-    n_cov = 0;
   }
   if (!rows_meet_slab(v, lo[1], ne[1])) return;  // another slab's particle (block-uniform)
   for (int t = threadIdx.x; t < 3 * 64; t += blockDim.x) {
@@ -489,39 +491,74 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   }
   if constexpr (!TABLE)
     for (int t = threadIdx.x; t < tsize; t += blockDim.x) need[t] = 0;
+  if (want_list)
+    for (int t = threadIdx.x; t < ncell; t += blockDim.x) s_flag[t] = 0;
   __syncthreads();
 
   // pass 1: full cells claim their node at once; partial cells are listed
   // and mark the corner values they combine
-  auto claim = [&](int ci, int cj, int ck, T e) {
+  // node offset of box cell (ci, cj, ck); false if the cell is not a node of
+  // this lattice (beyond a wall, or outside this slab's computed rows)
+  auto node_of = [&](int ci, int cj, int ck, long long& n) -> bool {
     int i = lo[0] + ci, j = lo[1] + cj, k = lo[2] + ck;
     if (v.wall_y) {
-      if (j < 0 || j >= v.ny_glob) return;
+      if (j < 0 || j >= v.ny_glob) return false;
     } else {
       j = wrap_idx(j, v.ny_glob);
     }
     j -= v.ygo;  // local row; only this slab's computed rows
-    if (j < v.y0 || j >= v.y0 + v.ny_c) return;
+    if (j < v.y0 || j >= v.y0 + v.ny_c) return false;
     i = wrap_idx(i, v.nx);
     k = wrap_idx(k, v.nz);
-    const long long n = ((long long)k * v.ny + j) * v.pitch + i;
+    n = ((long long)k * v.ny + j) * v.pitch + i;
+    return true;
+  };
+  auto claim = [&](int ci, int cj, int ck, T e) {
+    long long n;
+    if (!node_of(ci, cj, ck, n)) return;
 #pragma unroll
     for (int s = 0; s < kMaxOwners; s++) {
       if (atomicCAS(&v.own[s][n], -1, p) == -1) {
         store_eps<T>(v.eps[s], n, e);
-        if (s == 0 && want_list) s_cov[atomicAdd(&n_cov, 1)] = (int)n;
+        if (s == 0 && want_list) s_flag[(ck * ne[1] + cj) * ne[0] + ci] = 1;
         return;
       }
     }
     atomicOr(v.err, ERR_OWNERS);
   };
-  // one reservation per particle in the global list, then a block copy
+  // the flagged cells in box order: a block scan of per-thread counts over
+  // contiguous cell ranges, one reservation per particle in the global list
   auto flush_list = [&]() {
     if (!want_list) return;
     __syncthreads();
-    if (threadIdx.x == 0) cov_base = n_cov > 0 ? atomicAdd(v.cov_count, n_cov) : 0;
+    const int per = (ncell + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int t0 = min((int)threadIdx.x * per, ncell), t1 = min(t0 + per, ncell);
+    int c = 0;
+    for (int t = t0; t < t1; t++) c += s_flag[t];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) cov_wsum[wid] = incl;
     __syncthreads();
-    for (int i = threadIdx.x; i < n_cov; i += blockDim.x) v.cov_list[cov_base + i] = s_cov[i];
+    int wbase = 0, total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      wbase += w < wid ? cov_wsum[w] : 0;
+      total += cov_wsum[w];
+    }
+    if (threadIdx.x == 0) cov_base = total > 0 ? atomicAdd(v.cov_count, total) : 0;
+    __syncthreads();
+    int o = cov_base + wbase + incl - c;
+    for (int t = t0; t < t1; t++) {
+      if (!s_flag[t]) continue;
+      const int ci = t % ne[0], cj = (t / ne[0]) % ne[1], ck = t / (ne[0] * ne[1]);
+      long long n = 0;
+      node_of(ci, cj, ck, n);
+      v.cov_list[o++] = (int)n;
+    }
   };
   const FastDiv3 cdiv(ne[0], ne[1]);
   for (int t = threadIdx.x; t < ncell; t += blockDim.x) {

@@ -1,22 +1,33 @@
 // K7: the learned drag closure's network on the 5th-generation tensor cores.
 //
 // MLP 6 -> 128 -> 128 -> 128 -> 128 -> 3 with ReLU, BF16 operands and FP32
-// accumulation.  Every layer product (forward: H_l = act(H_{l-1} W_l^T + b);
-// backward: dH_{l-1} = (dH_l W_l) * relu'(H_{l-1})) is a 128-sample tile
-// times a weight matrix, issued as tcgen05.mma (kind::f16, M = 128, N = 16 or
-// 128, K = 16 per instruction) by one thread of the CTA, with both operands
-// in shared memory in the canonical K-major layout without swizzle (8x8
-// core matrices of 128 contiguous bytes; LBO = stride between core matrices
-// along K, SBO = stride between 8-row groups) and the accumulator in tensor
-// memory.  Completion is signalled through tcgen05.commit on an mbarrier;
-// the epilogue reads the accumulator with tcgen05.ld (32 lanes x 16 columns
-// per instruction), adds the bias, applies ReLU and writes the next operand.
-// Weight gradients dW_l = dH_l^T H_{l-1} are a reduction over the minibatch
-// done on the FP32 cores; Adam keeps FP32 master weights and refreshes the
-// BF16 tiles (W in [out][in] and W^T in [in][out] core-matrix order).
+// accumulation.  Every product of a training step runs as tcgen05.mma
+// (kind::f16, M = 128, N = 16 or 128, K = 16 per instruction) issued by one
+// thread of the CTA, with both operands in shared memory in the canonical
+// K-major layout without swizzle (8x8 core matrices of 128 contiguous bytes;
+// LBO = stride between core matrices along K, SBO = stride between 8-row
+// groups) and the FP32 accumulator in tensor memory:
+//   forward   H_l = act(H_{l-1} W_l^T + b_l)           (128-sample tile x W_l)
+//   backward  dH_{l-1} = (dH_l W_l) * relu'(H_{l-1})   (128-sample tile x W_l^T)
+//   weights   dW_l = dH_l^T H_{l-1}                    (K = the minibatch)
+// Completion is signalled through tcgen05.commit on an mbarrier; epilogues
+// read the accumulator with tcgen05.ld (32 lanes x 16 columns per
+// instruction).  A training step is four launches: forward (keeps the
+// activations), backward (gradients of the pre-activations, bias gradients),
+// the weight-gradient products, and Adam fused with the refresh of the BF16
+// operand tiles.
+//
+// Operand staging overlaps the products: the forward and backward kernels
+// request every weight tile with bulk copies (cp.async.bulk, one mbarrier
+// per tile) at launch and wait for a tile only before its first product;
+// the weight-gradient kernel streams its operands through a ring of shared
+// memory stages (bulk copies completing on per-stage "full" barriers, the
+// products releasing a stage through tcgen05.commit on its "empty" barrier),
+// so the copies of later K blocks run under the products of earlier ones.
 //
 // Every wait on an mbarrier is bounded: after the poll limit the kernel sets
-// an error flag, frees its tensor memory and returns.
+// an error flag, waits (bounded) for its copies and products in flight, frees
+// its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,6 +44,8 @@ constexpr int OUT = 3;      // outputs
 constexpr int KIN = 16;     // padded input width
 constexpr int NOUT = 16;    // padded output width
 constexpr int TILE = 128;   // samples per CTA tile
+constexpr int KB = 64;      // samples per K block of the weight-gradient products
+constexpr int NSTAGE = 4;   // shared-memory stages of the weight-gradient pipeline
 constexpr long long kPollLimit = 1ll << 26;
 enum : int { MERR_TIMEOUT = 1 };
 
@@ -41,12 +54,23 @@ __host__ __device__ constexpr int lay_out(int l) { return l == 4 ? OUT : H; }
 __host__ __device__ constexpr int lay_in(int l) { return l == 0 ? IN : H; }
 __host__ __device__ constexpr int lay_N(int l) { return l == 4 ? NOUT : H; }
 __host__ __device__ constexpr int lay_K(int l) { return l == 0 ? KIN : H; }
+// rows (features) of the layer inputs act_l and output gradients dact_l
+__host__ __device__ constexpr int act_rows(int l) { return l == 0 ? KIN : H; }
+__host__ __device__ constexpr int dact_rows(int l) { return l == 4 ? NOUT : H; }
 
 // --------------------------------------------------------------------------
 // canonical K-major layout without swizzle: element (r, k) of an R x K tile
 // --------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int cm_index(int r, int k, int K) {
   return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// element (feature r, sample m) of the [feature][sample] arrays the
+// weight-gradient products read: 64-sample blocks, each an R x 64 tile in the
+// canonical K-major layout (K = samples), stored one after the other so that
+// a block is one contiguous bulk copy
+__host__ __device__ __forceinline__ size_t tblock_index(int r, int m, int R) {
+  return (size_t)(m >> 6) * (size_t)(R * KB) + (size_t)cm_index(r, m & (KB - 1), KB);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -72,6 +96,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
+// make barrier initialisations visible to the async proxy (bulk copies,
+// tensor-core commits) before any of them can arrive
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // bounded wait for the phase with the given parity; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
@@ -85,6 +116,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+
+// arrive on the barrier expecting `bytes` of bulk-copy data in this phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// bulk copy global -> this CTA's shared memory, completing on `bar`
+// (addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(static_cast<unsigned long long>(__cvta_generic_to_global(src))), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -132,21 +179,28 @@ __device__ __forceinline__ void tmem_free(uint32_t taddr) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols));
 }
 
-// D (128 x N) = A (128 x K) * B (N x K)^T, issued by thread 0, waited by all;
+// D (128 x N) = A (128 x K) * B (N x K)^T, issued by thread 0 (after its
+// operand barrier `wbar`, if any, has completed phase 0), waited by all;
 // returns false on timeout.  Caller has fenced the operand writes.
 __device__ __forceinline__ bool tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int N, int K,
-                                        uint32_t tmem_d, uint64_t* bar, uint32_t& phase) {
+                                        uint32_t tmem_d, uint64_t* bar, uint32_t& phase,
+                                        uint64_t* wbar = nullptr) {
+  int issued = 1;
   if (threadIdx.x == 0) {
-    tc_fence_after();
-    const uint32_t idesc = instr_desc(128, N);
-    for (int kk = 0; kk < K; kk += 16) {
-      // the K-chunk starts at core-matrix column kk/8: byte offset (kk/8)*128
-      const uint64_t ad = smem_desc(A + (kk >> 3) * 64, K);
-      const uint64_t bd = smem_desc(B + (kk >> 3) * 64, K);
-      tc_mma(tmem_d, ad, bd, idesc, kk > 0 ? 1 : 0);
+    issued = wbar == nullptr || mbar_wait(wbar, 0) ? 1 : 0;
+    if (issued) {
+      tc_fence_after();
+      const uint32_t idesc = instr_desc(128, N);
+      for (int kk = 0; kk < K; kk += 16) {
+        // the K-chunk starts at core-matrix column kk/8: byte offset (kk/8)*128
+        const uint64_t ad = smem_desc(A + (kk >> 3) * 64, K);
+        const uint64_t bd = smem_desc(B + (kk >> 3) * 64, K);
+        tc_mma(tmem_d, ad, bd, idesc, kk > 0 ? 1 : 0);
+      }
+      tc_commit(bar);
     }
-    tc_commit(bar);
   }
+  if (__syncthreads_and(issued) == 0) return false;  // the operands never arrived: nothing issued
   const bool ok = mbar_wait(bar, phase);
   phase ^= 1u;
   tc_fence_after();
@@ -157,52 +211,80 @@ __device__ __forceinline__ bool tc_gemm(const __nv_bfloat16* A, const __nv_bfloa
 // parameter block (device), see lbm_imb_mlp_* in the header
 // --------------------------------------------------------------------------
 struct Params {
-  float* w[5];             // FP32 master weights [out][in]
-  float* b[5];             // FP32 biases
-  float* mw[5];            // Adam first moments
-  float* vw[5];            // Adam second moments
-  float* mb[5];
-  float* vb[5];
-  float* gw[5];            // weight gradients
+  // flat parameter vectors in the interface order (W_1, b_1, ..., W_5, b_5):
+  // FP32 masters, Adam moments, gradients; w[l], b[l], ... point into them
+  float* p;
+  float* m;
+  float* v;
+  float* g;
+  float* w[5];
+  float* b[5];
+  float* gw[5];
   float* gb[5];
   __nv_bfloat16* wt[5];    // BF16 W in [N][K] core-matrix order (forward B operand)
   __nv_bfloat16* wtt[5];   // BF16 W^T in [N=in][K=out] core-matrix order (backward B operand)
   float* norm;             // x_mean[6], x_std[6], y_mean[3], y_std[3]
-  // activations of the current minibatch (BF16, row-major [sample][feature])
-  __nv_bfloat16* act[5];   // act[0] = normalised input (KIN wide), act[l] = H_l (H wide)
-  __nv_bfloat16* dact[5];  // dact[l] = dL/dpre-activation of layer l (N wide)
+  // activations of the current minibatch in the [feature][sample] block
+  // layout of tblock_index: actT[l] = input of layer l (actT[0] = the
+  // normalised x, KIN rows; actT[l] = H_l, H rows), dactT[l] = gradient of
+  // layer l's pre-activation output (H rows; NOUT rows for l = 4)
+  __nv_bfloat16* actT[5];
+  __nv_bfloat16* dactT[5];
   float* y;                // network output, normalised [B][NOUT]
   float* loss;             // [1]
   int* err;                // [1]
 };
 
-__device__ __forceinline__ void stage_weights(__nv_bfloat16* dst, const __nv_bfloat16* src, int elems) {
-  const uint4* s = reinterpret_cast<const uint4*>(src);
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  for (int i = threadIdx.x; i < elems / 8; i += blockDim.x) d[i] = s[i];
+// offsets of W_l and b_l in the flat parameter vector
+__host__ __device__ constexpr int off_w(int l) {
+  return l == 0 ? 0 : off_w(l - 1) + lay_out(l - 1) * lay_in(l - 1) + lay_out(l - 1);
 }
+__host__ __device__ constexpr int off_b(int l) { return off_w(l) + lay_out(l) * lay_in(l); }
+constexpr int kNumParams = off_b(4) + OUT;
+static_assert(off_w(1) % 4 == 0 && off_w(2) % 4 == 0 && off_w(3) % 4 == 0 && off_b(1) % 4 == 0,
+              "float4 gradient sums need 16-byte aligned weight rows");
 
-// shared memory of the forward/backward kernels
+// bytes of the BF16 operand tiles
+__host__ __device__ constexpr uint32_t tile_bytes(int l) { return (uint32_t)(lay_N(l) * lay_K(l) * 2); }
+
+// shared memory of the forward kernel
 struct SmemFwd {
   __nv_bfloat16 w1[H * KIN];
   __nv_bfloat16 w[3][H * H];
   __nv_bfloat16 w5[NOUT * H];
   __nv_bfloat16 a[TILE * H];     // current activation tile (K-major)
   __nv_bfloat16 x[TILE * KIN];   // input tile
-  uint64_t bar;
+  uint64_t wbar[5];              // weight tile l arrived
+  uint64_t bar;                  // products done
   uint32_t tmem;
 };
 
+// thread 0: one barrier per weight tile, all tiles requested at once
+__device__ __forceinline__ void request_tiles(uint64_t* wbar, __nv_bfloat16* const* dst,
+                                              __nv_bfloat16* const* src, const uint32_t* bytes, int n) {
+  for (int i = 0; i < n; i++) mbar_init(&wbar[i], 1);
+  mbar_init_fence();
+  for (int i = 0; i < n; i++) {
+    mbar_expect_tx(&wbar[i], bytes[i]);
+    bulk_g2s(dst[i], src[i], bytes[i], &wbar[i]);
+  }
+}
+
 // forward pass over tiles of 128 samples; train = 1 keeps the activations
+// (actT) and the normalised outputs (y) for the backward pass
 __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float* x, int B, int train,
                                                           float* y_out) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SmemFwd& S = *reinterpret_cast<SmemFwd*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
-  stage_weights(S.w1, P.wt[0], H * KIN);
-  for (int l = 0; l < 3; l++) stage_weights(S.w[l], P.wt[l + 1], H * H);
-  stage_weights(S.w5, P.wt[4], NOUT * H);
-  if (tid == 0) mbar_init(&S.bar, 1);
+  if (tid == 0) {
+    __nv_bfloat16* dst[5] = {S.w1, S.w[0], S.w[1], S.w[2], S.w5};
+    __nv_bfloat16* src[5] = {P.wt[0], P.wt[1], P.wt[2], P.wt[3], P.wt[4]};
+    const uint32_t bytes[5] = {tile_bytes(0), tile_bytes(1), tile_bytes(2), tile_bytes(3), tile_bytes(4)};
+    request_tiles(S.wbar, dst, src, bytes, 5);
+    mbar_init(&S.bar, 1);
+    mbar_init_fence();
+  }
   if (warp == 0) tmem_alloc(&S.tmem);
   tc_fence_before();
   __syncthreads();
@@ -215,14 +297,14 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
   for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int row = t * TILE + tid;  // this thread's sample (row of the tile)
     const bool valid = row < B;
-    // normalised input -> BF16 operand
+    // normalised input -> BF16 operand (rows past the batch are zero)
 #pragma unroll
     for (int k = 0; k < KIN; k++) {
       float v = 0.f;
       if (k < IN && valid) v = (x[(size_t)row * IN + k] - nm[k]) / nm[IN + k];
       const __nv_bfloat16 bv = __float2bfloat16_rn(v);
       S.x[cm_index(tid, k, KIN)] = bv;
-      if (train && valid) P.act[0][(size_t)row * KIN + k] = bv;
+      if (train) P.actT[0][tblock_index(k, row, KIN)] = bv;
     }
     proxy_fence();
     tc_fence_before();
@@ -230,7 +312,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
     for (int l = 0; l < 5 && ok; l++) {
       const __nv_bfloat16* A = l == 0 ? S.x : S.a;
       const __nv_bfloat16* Bm = l == 0 ? S.w1 : (l == 4 ? S.w5 : S.w[l - 1]);
-      ok = tc_gemm(A, Bm, lay_N(l), lay_K(l), tmem, &S.bar, phase);
+      ok = tc_gemm(A, Bm, lay_N(l), lay_K(l), tmem, &S.bar, phase, &S.wbar[l]);
       if (!ok) break;
       // epilogue: this warp's 32 rows
       const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
@@ -244,7 +326,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
             const float hv = fmaxf(r[i] + bias[c0 + i], 0.f);
             const __nv_bfloat16 bv = __float2bfloat16_rn(hv);
             S.a[cm_index(tid, c0 + i, H)] = bv;
-            if (train && valid) P.act[l + 1][(size_t)row * H + c0 + i] = bv;
+            if (train) P.actT[l + 1][tblock_index(c0 + i, row, H)] = valid ? bv : __float2bfloat16_rn(0.f);
           }
         } else if (valid) {
 #pragma unroll
@@ -261,28 +343,59 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
     }
   }
   if (!ok && tid == 0) atomicOr(P.err, MERR_TIMEOUT);
+  if (tid == 0)  // copies still in flight must land before the CTA's memory is released
+    for (int i = 0; i < 5; i++) mbar_wait(&S.wbar[i], 0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_free(tmem);
 }
 
-// backward (data) pass: dY from the loss, then dH_{l-1} = (dH_l W_l) * relu'(H_{l-1})
+// backward (data) pass: dY from the loss, then dH_{l-1} = (dH_l W_l) * relu'(H_{l-1});
+// writes the pre-activation gradients (BF16, for the weight products) and adds
+// this tile's column sums (FP32, before rounding) to the bias gradients
 struct SmemBwd {
   __nv_bfloat16 w5t[H * NOUT];   // W5^T: N = 128 (in), K = 16 (out, padded)
   __nv_bfloat16 wt[3][H * H];    // W4^T, W3^T, W2^T
   __nv_bfloat16 d[TILE * H];     // current gradient tile (K-major)
+  float colsum[4][H];            // per-warp column sums of the gradient tile
+  uint64_t wbar[4];
   uint64_t bar;
   uint32_t tmem;
 };
+
+// column sums of one 16-column slice over the warp's 32 samples, by lane 0
+__device__ __forceinline__ void warp_colsum16(const float (&g)[16], float* out) {
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    float v = g[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) out[i] = v;
+  }
+}
+
+// the CTA's per-warp column sums [4][n] -> atomic adds into gb[n]
+__device__ __forceinline__ void flush_colsum(float (*colsum)[H], float* gb, int n) {
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    atomicAdd(gb + c, (colsum[0][c] + colsum[1][c]) + (colsum[2][c] + colsum[3][c]));
+  __syncthreads();
+}
 
 __global__ void __launch_bounds__(128) mlp_backward_kernel(Params P, const float* tgt, int B) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SmemBwd& S = *reinterpret_cast<SmemBwd*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
-  stage_weights(S.w5t, P.wtt[4], H * NOUT);
-  for (int l = 0; l < 3; l++) stage_weights(S.wt[l], P.wtt[3 - l], H * H);  // W4^T, W3^T, W2^T
-  if (tid == 0) mbar_init(&S.bar, 1);
+  // barrier k <-> the product with W_{4-k}^T: k = 0 W5^T (w5t), 1 W4^T, 2 W3^T, 3 W2^T
+  if (tid == 0) {
+    __nv_bfloat16* dst[4] = {S.w5t, S.wt[0], S.wt[1], S.wt[2]};
+    __nv_bfloat16* src[4] = {P.wtt[4], P.wtt[3], P.wtt[2], P.wtt[1]};
+    const uint32_t bytes[4] = {tile_bytes(4), tile_bytes(3), tile_bytes(2), tile_bytes(1)};
+    request_tiles(S.wbar, dst, src, bytes, 4);
+    mbar_init(&S.bar, 1);
+    mbar_init_fence();
+  }
   if (warp == 0) tmem_alloc(&S.tmem);
   tc_fence_before();
   __syncthreads();
@@ -298,44 +411,49 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(Params P, const float
     const int row = t * TILE + tid;
     const bool valid = row < B;
     // dL/dy of the normalised output (mean squared error)
+    float g[NOUT];
 #pragma unroll
     for (int k = 0; k < NOUT; k++) {
-      float g = 0.f;
+      g[k] = 0.f;
       if (k < OUT && valid) {
         const float th = (tgt[(size_t)row * OUT + k] - nm[2 * IN + k]) / nm[2 * IN + OUT + k];
         const float e = P.y[(size_t)row * NOUT + k] - th;
         lsum += e * e;
-        g = scale * e;
+        g[k] = scale * e;
       }
-      const __nv_bfloat16 bg = __float2bfloat16_rn(g);
+      const __nv_bfloat16 bg = __float2bfloat16_rn(g[k]);
       S.d[cm_index(tid, k, NOUT)] = bg;
-      if (valid) P.dact[4][(size_t)row * NOUT + k] = bg;
+      P.dactT[4][tblock_index(k, row, NOUT)] = bg;
     }
+    warp_colsum16(g, S.colsum[warp]);
+    flush_colsum(S.colsum, P.gb[4], OUT);
     proxy_fence();
     tc_fence_before();
     __syncthreads();
     // layers 4..1: product with W_l, then the ReLU mask of H_l's pre-activation
     for (int l = 4; l >= 1 && ok; l--) {
-      // B operand of step l is W_l^T (staged: w5t = W_4^T, wt[3 - l] = W_l^T)
+      // B operand of step l is W_l^T (staged: w5t = W_5^T, wt[3 - l] = W_l^T)
       const __nv_bfloat16* Bt = l == 4 ? S.w5t : S.wt[3 - l];
-      ok = tc_gemm(S.d, Bt, H, l == 4 ? NOUT : H, tmem, &S.bar, phase);
+      ok = tc_gemm(S.d, Bt, H, l == 4 ? NOUT : H, tmem, &S.bar, phase, &S.wbar[4 - l]);
       if (!ok) break;
       const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
       for (int c0 = 0; c0 < H; c0 += 16) {
-        float r[16];
+        float r[16], gl[16];
         tc_ld16(lane_base + c0, r);
 #pragma unroll
         for (int i = 0; i < 16; i++) {
-          float g = 0.f;
+          gl[i] = 0.f;
           if (valid) {
-            const float hv = __bfloat162float(P.act[l][(size_t)row * H + c0 + i]);
-            g = hv > 0.f ? r[i] : 0.f;
+            const float hv = __bfloat162float(P.actT[l][tblock_index(c0 + i, row, H)]);
+            gl[i] = hv > 0.f ? r[i] : 0.f;
           }
-          const __nv_bfloat16 bg = __float2bfloat16_rn(g);
+          const __nv_bfloat16 bg = __float2bfloat16_rn(gl[i]);
           S.d[cm_index(tid, c0 + i, H)] = bg;
-          if (valid) P.dact[l - 1][(size_t)row * H + c0 + i] = bg;
+          P.dactT[l - 1][tblock_index(c0 + i, row, H)] = bg;
         }
+        warp_colsum16(gl, S.colsum[warp] + c0);
       }
+      flush_colsum(S.colsum, P.gb[l - 1], H);
       proxy_fence();
       tc_fence_before();
       __syncthreads();
@@ -345,67 +463,161 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(Params P, const float
   for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
   if ((tid & 31) == 0 && lsum != 0.f) atomicAdd(P.loss, lsum / (float)(B * OUT));
   if (!ok && tid == 0) atomicOr(P.err, MERR_TIMEOUT);
+  if (tid == 0)
+    for (int i = 0; i < 4; i++) mbar_wait(&S.wbar[i], 0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_free(tmem);
 }
 
-// dW_l[o][i] = sum_m dact[l][m][o] * act[l][m][i],  db_l[o] = sum_m dact[l][m][o]
-// (FP32 cores; one 32x32 output block per CTA, minibatch in chunks of 64)
-__global__ void __launch_bounds__(256) mlp_wgrad_kernel(Params P, int B, int l) {
-  const int OUTl = lay_out(l), INl = lay_in(l);
-  const int Nst = lay_N(l), Kst = lay_K(l);  // row strides of dact[l] and act[l]
-  const int o0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
-  __shared__ float sd[64][33], sa[64][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  float bacc = 0.f;
-  for (int m0 = 0; m0 < B; m0 += 64) {
-    for (int e = threadIdx.x; e < 64 * 32; e += 256) {
-      const int mm = e >> 5, c = e & 31, m = m0 + mm;
-      sd[mm][c] = (m < B && o0 + c < OUTl) ? __bfloat162float(P.dact[l][(size_t)m * Nst + o0 + c]) : 0.f;
-      sa[mm][c] = (m < B && i0 + c < INl) ? __bfloat162float(P.act[l][(size_t)m * Kst + i0 + c]) : 0.f;
+// Weight gradients on the tensor cores.  CTA (l, s) accumulates, for layer l,
+// the products over 64-sample blocks s*per .. (s+1)*per - 1 of the minibatch
+// in tensor memory and adds its partial sum to gw[l]:
+//   l = 0..3: D [out][in] = dactT_l (M = 128) x actT_l^T (N = 16 for l = 0, else 128)
+//   l = 4:    D [in][out] = actT_4 (M = 128) x dactT_4^T (N = 16), i.e. dW_5^T
+// Thread 0 streams the blocks through NSTAGE shared-memory stages and issues
+// the products; stage s is refilled once the products reading it are done.
+struct SmemWg {
+  __nv_bfloat16 a[NSTAGE][H * KB];
+  __nv_bfloat16 b[NSTAGE][H * KB];
+  uint64_t full[NSTAGE], empty[NSTAGE], done;
+  uint32_t tmem;
+  int ok, mma;
+};
+
+__global__ void __launch_bounds__(128) mlp_wgrad_kernel(Params P, int nblk_total, int per) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  SmemWg& S = *reinterpret_cast<SmemWg*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int l = blockIdx.y;
+  const int j0 = blockIdx.x * per;
+  const int nblk = min(per, nblk_total - j0);
+  if (nblk <= 0) return;  // block-uniform, before any barrier or allocation
+  const bool last = l == 4;
+  const __nv_bfloat16* Ag = last ? P.actT[4] : P.dactT[l];
+  const __nv_bfloat16* Bg = last ? P.dactT[4] : P.actT[l];
+  const int N = last ? NOUT : act_rows(l);
+  const uint32_t abytes = (uint32_t)(H * KB * 2), bbytes = (uint32_t)(N * KB * 2);
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; s++) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int mm = 0; mm < 64; mm++) {
-      const float av = sa[mm][tx];
-#pragma unroll
-      for (int j = 0; j < 4; j++) acc[j] += sd[mm][ty + 8 * j] * av;
-      if (blockIdx.x == 0 && ty == 0) bacc += sd[mm][tx];
+    mbar_init(&S.done, 1);
+    mbar_init_fence();
+    S.ok = 1;
+    S.mma = 0;
+  }
+  if (warp == 0) tmem_alloc(&S.tmem);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+  if (tid == 0) {
+    int use[NSTAGE];       // use count of the last load issued to each stage
+    bool landed[NSTAGE];   // that load has been waited for
+    for (int s = 0; s < NSTAGE; s++) {
+      use[s] = -1;
+      landed[s] = true;
     }
-    __syncthreads();
-  }
+    auto load = [&](int j) {
+      const int s = j % NSTAGE;
+      mbar_expect_tx(&S.full[s], abytes + bbytes);
+      bulk_g2s(S.a[s], Ag + (size_t)(j0 + j) * (H * KB), abytes, &S.full[s]);
+      bulk_g2s(S.b[s], Bg + (size_t)(j0 + j) * (N * KB), bbytes, &S.full[s]);
+      use[s] = j / NSTAGE;
+      landed[s] = false;
+    };
+    bool ok = true, any_mma = false;
+    for (int j = 0; j < nblk && j < NSTAGE; j++) load(j);
+    const uint32_t idesc = instr_desc(128, N);
+    for (int j = 0; j < nblk && ok; j++) {
+      const int s = j % NSTAGE;
+      ok = mbar_wait(&S.full[s], (uint32_t)((j / NSTAGE) & 1));
+      if (!ok) break;
+      landed[s] = true;
+      tc_fence_after();
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const int o = o0 + ty + 8 * j, i = i0 + tx;
-    if (o < OUTl && i < INl) P.gw[l][o * INl + i] = acc[j];
+      for (int kk = 0; kk < KB; kk += 16) {
+        const uint64_t ad = smem_desc(S.a[s] + (kk >> 3) * 64, KB);
+        const uint64_t bd = smem_desc(S.b[s] + (kk >> 3) * 64, KB);
+        tc_mma(tmem, ad, bd, idesc, (j > 0 || kk > 0) ? 1 : 0);
+      }
+      any_mma = true;
+      tc_commit(&S.empty[s]);
+      // refill the stage the previous block used, once its products are done
+      const int jr = j - 1 + NSTAGE;
+      if (j >= 1 && jr < nblk) {
+        const int sp = (j - 1) % NSTAGE;
+        ok = mbar_wait(&S.empty[sp], (uint32_t)(((j - 1) / NSTAGE) & 1));
+        if (ok) load(jr);
+      }
+    }
+    if (any_mma) tc_commit(&S.done);  // tracks every product issued
+    if (!ok) {
+      S.ok = 0;
+      for (int s = 0; s < NSTAGE; s++)  // copies in flight land before exit
+        if (!landed[s]) mbar_wait(&S.full[s], (uint32_t)(use[s] & 1));
+    }
+    S.mma = any_mma ? 1 : 0;
+    if (!any_mma) S.ok = 0;
   }
-  if (blockIdx.x == 0 && ty == 0 && o0 + tx < OUTl) P.gb[l][o0 + tx] = bacc;
+  __syncthreads();
+  bool ok = S.ok != 0;
+  // every thread waits for the products issued (bounded; also on the error path)
+  if (S.mma && !mbar_wait(&S.done, 0)) ok = false;
+  tc_fence_after();
+  if (__syncthreads_and(ok ? 1 : 0)) {
+    // epilogue: lane = row of D, 16 columns per load
+    const int r = warp * 32 + (tid & 31);
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc_ld16(lane_base + c0, v);
+      if (last) {  // D = dW_5^T: row = input feature r, column = output o
+        for (int o = 0; o < OUT; o++) atomicAdd(P.gw[4] + o * H + r, v[o]);
+      } else if (l == 0) {  // D = dW_1: row = output r, columns = the 6 inputs
+        for (int i = 0; i < IN; i++) atomicAdd(P.gw[0] + r * IN + i, v[i]);
+      } else {
+        float4* dst = reinterpret_cast<float4*>(P.gw[l] + r * H + c0);
+#pragma unroll
+        for (int q = 0; q < 4; q++) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(P.err, MERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_free(tmem);
 }
 
-// Adam on the FP32 masters, then the BF16 operand tiles
-__global__ void mlp_adam_kernel(Params P, int l, float lr, float c1, float c2) {
-  const int OUTl = lay_out(l), INl = lay_in(l);
-  const int nw = OUTl * INl;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Adam on the flat FP32 masters, one thread per parameter, and the refresh of
+// the BF16 operand tiles of every weight (W in [out][in] order for the
+// forward products, W^T for the backward ones; the zero padding of the tiles
+// is never touched)
+__global__ void mlp_adam_kernel(Params P, float lr, float c1, float c2) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kNumParams) return;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  if (i < nw) {
-    const float g = P.gw[l][i];
-    const float m = b1 * P.mw[l][i] + (1.f - b1) * g;
-    const float v = b2 * P.vw[l][i] + (1.f - b2) * g * g;
-    P.mw[l][i] = m;
-    P.vw[l][i] = v;
-    P.w[l][i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
-  }
-  if (i < OUTl) {
-    const float g = P.gb[l][i];
-    const float m = b1 * P.mb[l][i] + (1.f - b1) * g;
-    const float v = b2 * P.vb[l][i] + (1.f - b2) * g * g;
-    P.mb[l][i] = m;
-    P.vb[l][i] = v;
-    P.b[l][i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+  const float g = P.g[e];
+  const float m = b1 * P.m[e] + (1.f - b1) * g;
+  const float v = b2 * P.v[e] + (1.f - b2) * g * g;
+  P.m[e] = m;
+  P.v[e] = v;
+  const float w = P.p[e] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+  P.p[e] = w;
+  const int ow[5] = {off_w(0), off_w(1), off_w(2), off_w(3), off_w(4)};  // folded at compile time
+  int l = 0;
+  while (l < 4 && e >= ow[l + 1]) l++;
+  const int k = e - ow[l];
+  if (k < lay_out(l) * lay_in(l)) {
+    const int o = k / lay_in(l), i = k % lay_in(l);
+    const __nv_bfloat16 bw = __float2bfloat16_rn(w);
+    P.wt[l][cm_index(o, i, lay_K(l))] = bw;
+    P.wtt[l][cm_index(i, o, lay_N(l))] = bw;
   }
 }
 
@@ -419,11 +631,6 @@ __global__ void mlp_pack_kernel(Params P, int l) {
   P.wt[l][cm_index(n, k, K)] = __float2bfloat16_rn(wv);
   // backward operand W^T: [n' = in][k' = out], K' = N (padded out width)
   P.wtt[l][cm_index(k, n, N)] = __float2bfloat16_rn(wv);
-}
-
-__global__ void mlp_zero_kernel(float* p, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = 0.f;
 }
 
 // GEMM probe: D (128 x N) = A (128 x K) * B (N x K)^T through the same
@@ -476,45 +683,38 @@ struct lbm_imb_mlp {
   int64_t max_batch;
   int64_t adam_t;
   int grid;
-  float* loss_host_tmp;
 };
 
 namespace {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// samples of the per-minibatch arrays: whole 128-sample tiles
+int64_t padded_batch(int64_t B) { return (B + TILE - 1) / TILE * TILE; }
+
 struct MlpLayout {
-  size_t off[64];
+  size_t off[32];
   size_t total;
 };
 
 // sizes of every array of the parameter block, in a fixed order
 void mlp_sizes(int64_t B, size_t* sz, int* n) {
+  const size_t Bp = (size_t)padded_batch(B);
   int k = 0;
-  for (int l = 0; l < 5; l++) {
-    const size_t nw = (size_t)lay_out(l) * lay_in(l), nb = lay_out(l);
-    sz[k++] = nw * 4;  // w
-    sz[k++] = nb * 4;  // b
-    sz[k++] = nw * 4;  // mw
-    sz[k++] = nw * 4;  // vw
-    sz[k++] = nb * 4;  // mb
-    sz[k++] = nb * 4;  // vb
-    sz[k++] = nw * 4;  // gw
-    sz[k++] = nb * 4;  // gb
-    sz[k++] = (size_t)lay_N(l) * lay_K(l) * 2;  // wt
-    sz[k++] = (size_t)lay_N(l) * lay_K(l) * 2;  // wtt
-  }
-  sz[k++] = 32 * 4;                              // norm
-  for (int l = 0; l < 5; l++) sz[k++] = (size_t)B * (l == 0 ? KIN : H) * 2;  // act
-  for (int l = 0; l < 5; l++) sz[k++] = (size_t)B * (l == 4 ? NOUT : H) * 2;  // dact
-  sz[k++] = (size_t)B * NOUT * 4;                // y
-  sz[k++] = 16;                                  // loss
-  sz[k++] = 16;                                  // err
+  for (int i = 0; i < 4; i++) sz[k++] = (size_t)kNumParams * 4;  // p, m, v, g
+  for (int l = 0; l < 5; l++) sz[k++] = (size_t)lay_N(l) * lay_K(l) * 2;  // wt
+  for (int l = 0; l < 5; l++) sz[k++] = (size_t)lay_N(l) * lay_K(l) * 2;  // wtt
+  sz[k++] = 32 * 4;                                                        // norm
+  for (int l = 0; l < 5; l++) sz[k++] = Bp * act_rows(l) * 2;              // actT
+  for (int l = 0; l < 5; l++) sz[k++] = Bp * dact_rows(l) * 2;             // dactT
+  sz[k++] = Bp * NOUT * 4;                                                 // y
+  sz[k++] = 16;                                                            // loss
+  sz[k++] = 16;                                                            // err
   *n = k;
 }
 
 int mlp_layout(int64_t B, MlpLayout* L) {
   if (B < 1 || B > (1ll << 24)) return LBM_IMB_EINVAL;
-  size_t sz[64];
+  size_t sz[32];
   int n = 0;
   mlp_sizes(B, sz, &n);
   size_t o = 0;
@@ -529,30 +729,24 @@ int mlp_layout(int64_t B, MlpLayout* L) {
 void mlp_bind(lbm_imb_mlp* h, unsigned char* base, const MlpLayout& L) {
   int k = 0;
   Params& P = h->P;
+  P.p = (float*)(base + L.off[k++]);
+  P.m = (float*)(base + L.off[k++]);
+  P.v = (float*)(base + L.off[k++]);
+  P.g = (float*)(base + L.off[k++]);
   for (int l = 0; l < 5; l++) {
-    P.w[l] = (float*)(base + L.off[k++]);
-    P.b[l] = (float*)(base + L.off[k++]);
-    P.mw[l] = (float*)(base + L.off[k++]);
-    P.vw[l] = (float*)(base + L.off[k++]);
-    P.mb[l] = (float*)(base + L.off[k++]);
-    P.vb[l] = (float*)(base + L.off[k++]);
-    P.gw[l] = (float*)(base + L.off[k++]);
-    P.gb[l] = (float*)(base + L.off[k++]);
-    P.wt[l] = (__nv_bfloat16*)(base + L.off[k++]);
-    P.wtt[l] = (__nv_bfloat16*)(base + L.off[k++]);
+    P.w[l] = P.p + off_w(l);
+    P.b[l] = P.p + off_b(l);
+    P.gw[l] = P.g + off_w(l);
+    P.gb[l] = P.g + off_b(l);
   }
+  for (int l = 0; l < 5; l++) P.wt[l] = (__nv_bfloat16*)(base + L.off[k++]);
+  for (int l = 0; l < 5; l++) P.wtt[l] = (__nv_bfloat16*)(base + L.off[k++]);
   P.norm = (float*)(base + L.off[k++]);
-  for (int l = 0; l < 5; l++) P.act[l] = (__nv_bfloat16*)(base + L.off[k++]);
-  for (int l = 0; l < 5; l++) P.dact[l] = (__nv_bfloat16*)(base + L.off[k++]);
+  for (int l = 0; l < 5; l++) P.actT[l] = (__nv_bfloat16*)(base + L.off[k++]);
+  for (int l = 0; l < 5; l++) P.dactT[l] = (__nv_bfloat16*)(base + L.off[k++]);
   P.y = (float*)(base + L.off[k++]);
   P.loss = (float*)(base + L.off[k++]);
   P.err = (int*)(base + L.off[k++]);
-}
-
-int n_params() {
-  int n = 0;
-  for (int l = 0; l < 5; l++) n += lay_out(l) * lay_in(l) + lay_out(l);
-  return n;
 }
 
 cudaError_t pack_all(lbm_imb_mlp* h) {
@@ -565,6 +759,7 @@ cudaError_t pack_all(lbm_imb_mlp* h) {
 
 int smem_fwd() { return (int)sizeof(SmemFwd) + 1024; }
 int smem_bwd() { return (int)sizeof(SmemBwd) + 1024; }
+int smem_wg() { return (int)sizeof(SmemWg) + 1024; }
 
 int read_mlp_err(lbm_imb_mlp* h) {
   int bits = 0;
@@ -593,12 +788,28 @@ cudaError_t launch_backward(lbm_imb_mlp* h, const float* t, int B) {
   return cudaGetLastError();
 }
 
+// weight-gradient products: the minibatch's 64-sample blocks split over
+// enough CTAs per layer that the five layers fill about one wave
 cudaError_t launch_wgrad(lbm_imb_mlp* h, int B) {
-  for (int l = 0; l < 5; l++) {
-    dim3 g((lay_in(l) + 31) / 32, (lay_out(l) + 31) / 32);
-    mlp_wgrad_kernel<<<g, 256, 0, h->stream>>>(h->P, B, l);
-  }
+  const int nblk = (int)(padded_batch(B) / KB);
+  int splits = h->grid / 5;
+  if (splits < 1) splits = 1;
+  int per = (nblk + splits - 1) / splits;
+  if (per < 2) per = 2 < nblk ? 2 : nblk;  // at least two blocks per CTA where there are two
+  const int gx = (nblk + per - 1) / per;
+  mlp_wgrad_kernel<<<dim3(gx, 5), 128, smem_wg(), h->stream>>>(h->P, nblk, per);
   return cudaGetLastError();
+}
+
+// one training step's products on the minibatch x [B][6], t [B][3]: the
+// gradients (flat, zeroed first) and the loss
+cudaError_t launch_gradients(lbm_imb_mlp* h, const float* x, const float* t, int B) {
+  cudaError_t e = cudaMemsetAsync(h->P.g, 0, (size_t)kNumParams * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->P.loss, 0, 4, h->stream);
+  if (e == cudaSuccess) e = launch_forward(h, x, B, 1, nullptr);
+  if (e == cudaSuccess) e = launch_backward(h, t, B);
+  if (e == cudaSuccess) e = launch_wgrad(h, B);
+  return e;
 }
 }  // namespace
 
@@ -629,12 +840,13 @@ int lbm_imb_mlp_init(void* dev_buf, size_t bytes, int64_t max_batch, uint64_t se
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bwd());
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_wg());
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 128 * 128 * 2 + 64);
   if (e == cudaSuccess) e = cudaMemsetAsync(dev_buf, 0, L.total, h->stream);
   // He-uniform initial weights (host xorshift), zero biases and moments
   if (e == cudaSuccess) {
-    const int np = n_params();
-    float* hp = (float*)malloc(sizeof(float) * np);
+    float* hp = (float*)malloc(sizeof(float) * kNumParams);
     uint64_t s = seed * 0x9E3779B97F4A7C15ull + 1;
     int k = 0;
     for (int l = 0; l < 5; l++) {
@@ -647,14 +859,7 @@ int lbm_imb_mlp_init(void* dev_buf, size_t bytes, int64_t max_batch, uint64_t se
       }
       for (int i = 0; i < lay_out(l); i++) hp[k++] = 0.f;
     }
-    k = 0;
-    for (int l = 0; l < 5 && e == cudaSuccess; l++) {
-      const int nw = lay_out(l) * lay_in(l), nb = lay_out(l);
-      e = cudaMemcpyAsync(h->P.w[l], hp + k, 4 * nw, cudaMemcpyHostToDevice, h->stream);
-      k += nw;
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h->P.b[l], hp + k, 4 * nb, cudaMemcpyHostToDevice, h->stream);
-      k += nb;
-    }
+    e = cudaMemcpyAsync(h->P.p, hp, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, h->stream);
     float norm[32];
     for (int i = 0; i < 32; i++) norm[i] = (i >= IN && i < 2 * IN) || i >= 2 * IN + OUT ? 1.f : 0.f;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->P.norm, norm, sizeof(norm), cudaMemcpyHostToDevice, h->stream);
@@ -672,21 +877,13 @@ int lbm_imb_mlp_init(void* dev_buf, size_t bytes, int64_t max_batch, uint64_t se
 
 int lbm_imb_mlp_num_params(int* n) {
   if (!n) return LBM_IMB_EINVAL;
-  *n = n_params();
+  *n = kNumParams;
   return LBM_IMB_OK;
 }
 
 int lbm_imb_mlp_set_params(lbm_imb_mlp_t* h, const float* params) {
   if (!h || !params) return LBM_IMB_EINVAL;
-  int k = 0;
-  cudaError_t e = cudaSuccess;
-  for (int l = 0; l < 5 && e == cudaSuccess; l++) {
-    const int nw = lay_out(l) * lay_in(l), nb = lay_out(l);
-    e = cudaMemcpyAsync(h->P.w[l], params + k, 4 * nw, cudaMemcpyHostToDevice, h->stream);
-    k += nw;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->P.b[l], params + k, 4 * nb, cudaMemcpyHostToDevice, h->stream);
-    k += nb;
-  }
+  cudaError_t e = cudaMemcpyAsync(h->P.p, params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = pack_all(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return e == cudaSuccess ? LBM_IMB_OK : LBM_IMB_ECUDA;
@@ -694,15 +891,7 @@ int lbm_imb_mlp_set_params(lbm_imb_mlp_t* h, const float* params) {
 
 int lbm_imb_mlp_get_params(lbm_imb_mlp_t* h, float* params) {
   if (!h || !params) return LBM_IMB_EINVAL;
-  int k = 0;
-  cudaError_t e = cudaSuccess;
-  for (int l = 0; l < 5 && e == cudaSuccess; l++) {
-    const int nw = lay_out(l) * lay_in(l), nb = lay_out(l);
-    e = cudaMemcpyAsync(params + k, h->P.w[l], 4 * nw, cudaMemcpyDeviceToHost, h->stream);
-    k += nw;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(params + k, h->P.b[l], 4 * nb, cudaMemcpyDeviceToHost, h->stream);
-    k += nb;
-  }
+  cudaError_t e = cudaMemcpyAsync(params, h->P.p, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return e == cudaSuccess ? LBM_IMB_OK : LBM_IMB_ECUDA;
 }
@@ -738,20 +927,9 @@ int lbm_imb_mlp_predict(lbm_imb_mlp_t* h, const float* x, float* y, int64_t n) {
 int lbm_imb_mlp_gradients(lbm_imb_mlp_t* h, const float* x, const float* t, int64_t B, float* grads,
                           float* loss) {
   if (!h || !x || !t || B < 1 || B > h->max_batch) return LBM_IMB_EINVAL;
-  cudaError_t e = cudaMemsetAsync(h->P.loss, 0, 4, h->stream);
-  if (e == cudaSuccess) e = launch_forward(h, x, (int)B, 1, nullptr);
-  if (e == cudaSuccess) e = launch_backward(h, t, (int)B);
-  if (e == cudaSuccess) e = launch_wgrad(h, (int)B);
-  if (e == cudaSuccess && grads) {
-    int k = 0;
-    for (int l = 0; l < 5 && e == cudaSuccess; l++) {
-      const int nw = lay_out(l) * lay_in(l), nb = lay_out(l);
-      e = cudaMemcpyAsync(grads + k, h->P.gw[l], 4 * nw, cudaMemcpyDeviceToHost, h->stream);
-      k += nw;
-      if (e == cudaSuccess) e = cudaMemcpyAsync(grads + k, h->P.gb[l], 4 * nb, cudaMemcpyDeviceToHost, h->stream);
-      k += nb;
-    }
-  }
+  cudaError_t e = launch_gradients(h, x, t, (int)B);
+  if (e == cudaSuccess && grads)
+    e = cudaMemcpyAsync(grads, h->P.g, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, h->P.loss, 4, cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return LBM_IMB_ECUDA;
   return read_mlp_err(h);
@@ -767,18 +945,13 @@ int lbm_imb_mlp_train_steps(lbm_imb_mlp_t* h, const float* x, const float* t, in
     int64_t B = batch;
     if (pos + B > n) pos = 0;
     if (B > n) B = n;
-    e = cudaMemsetAsync(h->P.loss, 0, 4, h->stream);
-    if (e == cudaSuccess) e = launch_forward(h, x + pos * IN, (int)B, 1, nullptr);
-    if (e == cudaSuccess) e = launch_backward(h, t + pos * OUT, (int)B);
-    if (e == cudaSuccess) e = launch_wgrad(h, (int)B);
+    e = launch_gradients(h, x + pos * IN, t + pos * OUT, (int)B);
     h->adam_t++;
     const float c1 = 1.f - powf(0.9f, (float)h->adam_t), c2 = 1.f - powf(0.999f, (float)h->adam_t);
-    for (int l = 0; l < 5 && e == cudaSuccess; l++) {
-      const int nw = lay_out(l) * lay_in(l);
-      mlp_adam_kernel<<<(nw + 255) / 256, 256, 0, h->stream>>>(h->P, l, lr, c1, c2);
+    if (e == cudaSuccess) {
+      mlp_adam_kernel<<<(kNumParams + 255) / 256, 256, 0, h->stream>>>(h->P, lr, c1, c2);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = pack_all(h);
     pos += B;
   }
   if (e == cudaSuccess && last_loss) e = cudaMemcpyAsync(last_loss, h->P.loss, 4, cudaMemcpyDeviceToHost, h->stream);
