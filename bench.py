@@ -181,19 +181,34 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(steps=4, nx=96, ny=128, nz=96, seed=3):
-    """The FP64 CPU oracle on a bounded sample of the 3D workload: a
-    nx x ny x nz sub-channel at the same solid fraction and parameters."""
+# The bounded CPU sample of the headline workload: a cut-down config 3 at the
+# same solid fraction and physics, timed through the OpenMP build of the
+# FP64 oracle on every host core.  The same sample serves cpu_baseline and
+# --impl reference.
+CPU_SAMPLE = dict(nx=64, ny=96, nz=64, seed=3)
+
+
+def cpu_oracle_sample(steps=None, warmup=0, seconds=15.0):
+    """Time the oracle (OpenMP timing build, all host cores) on CPU_SAMPLE:
+    `warmup` untimed steps, then `steps` steps (or as many whole steps as fit
+    in about `seconds`).  Returns the cpu_baseline record."""
     from oracle import oracle as O
-    cfg = I.config3_scaled(nx=nx, ny=ny, nz=nz, seed=seed)
-    sim = O.OracleSim(cfg)
-    t0 = time.perf_counter()
-    sim.step(steps)
+    cfg = I.config3_scaled(**CPU_SAMPLE)
+    threads = O.timing_threads()
+    sim = O.OracleSim(cfg, timing=True)
+    if warmup:
+        sim.step(warmup)
+    n, t0 = 0, time.perf_counter()
+    while (steps is not None and n < steps) or (steps is None and (n == 0 or time.perf_counter() - t0 < seconds)):
+        sim.step(1)
+        n += 1
     dt = time.perf_counter() - t0
     sim.close()
-    return {"value": cfg.n_nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"D3Q19 {nx}x{ny}x{nz} channel, {cfg.n_particles} spheres R=3.75 (config-3 solid fraction "
-                      f"and parameters), {steps} steps, single thread, {dt:.1f} s"}
+    return {"value": cfg.n_nodes * n / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "nproc": os.cpu_count(), "steps": n, "seconds": dt,
+            "sample": f"D3Q19 {CPU_SAMPLE['nx']}x{CPU_SAMPLE['ny']}x{CPU_SAMPLE['nz']} channel, {cfg.n_particles} "
+                      f"spheres R=3.75 (config-3 solid fraction and parameters), {n} steps in {dt:.1f} s, FP64 "
+                      f"oracle (OpenMP build) on {threads} threads"}
 
 
 # the paper's Table 3: 3D suspension sizes, steps/s on one C2050 and on one
@@ -238,27 +253,20 @@ def measure_table3(args, torch, gpu_steps=200, cpu_seconds=2.0):
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands on the host cores."""
+    """Reference arm: the CPU oracle as it stands (its OpenMP timing build)
+    on the host cores, each step one step of the bounded CPU sample."""
     import torch.distributed as dist  # noqa: F401
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import oracle as O
-    cfg = I.config3_scaled(nx=64, ny=96, nz=64, seed=3)
-    sim = O.OracleSim(cfg)
-    sim.step(args.warmup)
-    t0 = time.perf_counter()
-    sim.step(args.steps)
-    dt = time.perf_counter() - t0
-    v = cfg.n_nodes * args.steps / dt / 1e6
-    sample = (f"D3Q19 64x96x64 channel, {cfg.n_particles} spheres R=3.75 at config-3 solid fraction and parameters; "
-              f"each step is this bounded sample of the workload")
+    rec = cpu_oracle_sample(steps=args.steps, warmup=args.warmup)
+    v = rec["value"]
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": rec["seconds"] / rec["steps"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["name"] + " (bounded CPU sample)", "storage": "f64"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": rec["cores"], "kind": "oracle", "sample": rec["sample"]},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -386,7 +394,7 @@ def measure_slabs(cfg, args, torch, nslabs, ref_sim, steps_target):
             "exchange": "device halo kernel, populations crossing each face only"}, steps_target
 
 
-def measure_batch(args, torch, peaks, n=32, seed=4):
+def measure_batch(args, torch, peaks, n=32, seed=4, fp64_peak=None):
     """Config-4 batch: n independent D2Q9 FP64 suspensions of uneven sizes in
     one persistent graph-replayed launch per step (launch shape from the
     autotuner), against the same lattices stepped one after another."""
@@ -408,6 +416,13 @@ def measure_batch(args, torch, peaks, n=32, seed=4):
     batch.sync()
     ms = e0.elapsed_time(e1)
     tile_x, grid = batch.launch()
+    # FP64-pipe work of the collisions (the batch step also rasterises and
+    # moves the particles inside the same launch, so this is a lower bound
+    # on the collision's share of the pipe)
+    per_node, per_cov = FP64_OPS[2]
+    ops = 0.0
+    for m in batch.members:
+        ops += (per_node + per_cov * owned_fraction(m, torch)) * m.N
     batch.close()
     del batch
     sep_ms = 0.0
@@ -423,10 +438,27 @@ def measure_batch(args, torch, peaks, n=32, seed=4):
             "mlups": nodes * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
             "separate_mlups": nodes * args.steps / (sep_ms * 1e-3) / 1e6,
             "separate_ms_per_step": sep_ms / args.steps, "speedup_vs_separate": sep_ms / ms,
+            "fp64_gops": ops / (ms / args.steps * 1e-3) / 1e9,
+            "fp64_pipe_frac": (ops / (ms / args.steps * 1e-3) / 1e9 / fp64_peak) if fp64_peak else None,
+            "bytes_per_lup": 2 * 9 * 8 + 4, "hbm_frac": nodes * (2 * 9 * 8 + 4) / (ms / args.steps * 1e-3) / 1e9 /
+            peaks["hbm_gbs"],
             "tile_x": tile_x, "grid": grid, "blocks_per_sm": rec["blocks_per_sm"],
             "launch_shape_from_cache": cached,
             "workload": "32 D2Q9 FP64 periodic suspensions, nx 256-1024 x ny 512-4096 (log-uniform), "
                         "10-2000 disks R 4-8, density ratio log-uniform [2.5,1500]"}
+
+
+# algorithmic flops of one training sample: forward, backward-data and
+# weight-gradient products of 6 -> 128 -> 128 -> 128 -> 128 -> 3
+MLP_FLOPS_PER_SAMPLE = 3 * 2 * (6 * 128 + 3 * 128 * 128 + 128 * 3)
+
+
+def peaks_bf16_sustained():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("bf16_tflops_sustained", d.get("bf16_tflops", 0.0)))
+    return 1700.0
 
 
 def measure_closure(args, torch, n=128, snapshots=20):
@@ -441,7 +473,9 @@ def measure_closure(args, torch, n=128, snapshots=20):
                                               snapshots=snapshots)
     tr = seeds <= 8
     trm = torch.tensor(tr, device=x.device)
-    mlp, train_s, loss = CL.train_closure(x[trm], t[trm], batch=8192, epochs=30, lr=1e-3)
+    batch, epochs = 8192, 30
+    mlp, train_s, loss = CL.train_closure(x[trm], t[trm], batch=batch, epochs=epochs, lr=1e-3)
+    trained = max(1, epochs * int(trm.sum().item()) // batch) * batch  # samples through forward + backward
     xte = x[~trm].contiguous()
     tte = t[~trm].cpu().numpy()
     pred = mlp.predict(xte)
@@ -468,6 +502,8 @@ def measure_closure(args, torch, n=128, snapshots=20):
             "held_out_rel_error": {"mlp": CL.rel_error(pred, tte), "wen_yu_fit": CL.rel_error(wy(xte_np), tte),
                                    "stokes": CL.rel_error(xte_np[:, 1:4], tte)},
             "by_phi": by_phi, "wen_yu_exponent": float(wy.k), "train_seconds": train_s, "last_loss": loss,
+            "train_tflops": MLP_FLOPS_PER_SAMPLE * trained / train_s / 1e12,
+            "train_tflops_peak_bf16_sustained": peaks_bf16_sustained(),
             "resolved_s_per_particle_step": cost, "mlp_s_per_particle": infer_s,
             "speedup_vs_resolved": cost / infer_s,
             "workload": f"D3Q19 {n}^3 periodic, phi 0.05-0.4, R=3.75, ratio 1000, FP32-dev DNS; samples after "
@@ -475,16 +511,57 @@ def measure_closure(args, torch, n=128, snapshots=20):
 
 
 def measure_validation():
-    """Fixed sphere in a simple cubic array (phi ~ 0.008, Re_p ~ 0.1, FP64,
-    exact covered fractions): steady drag factor against Hasimoto's result
-    for sphere radii 3 to 8 lattice units."""
+    """The fixed-sphere array (one sphere per periodic cube, phi ~ 0.008,
+    body force on the gas, tau 1, exact covered fractions), run to steady
+    state: at Re_p ~ 0.2 against Hasimoto's dilute-array result for d/l = 6
+    to 24 (FP64; R = 12 in the FP32-deviation storage), and at Re_p ~ 2 the
+    drag factor's convergence under refinement (d/l = 6 to 16, FP64)."""
     from paper_1011_2613_gb300 import validation as V
     t0 = time.perf_counter()
     rows = [V.fixed_sphere_drag(R) for R in (3.0, 4.5, 6.0, 8.0)]
+    rows.append(V.fixed_sphere_drag(12.0, relax=8.0, storage="f32dev"))
+    rows2 = [V.fixed_sphere_drag(R, relax=8.0, re_p=2.0) for R in (3.0, 4.5, 6.0, 8.0)]
     keep = ("R", "L", "phi", "steps", "K", "K_hasimoto", "rel_error", "re_p", "force_balance")
-    return {"rows": [{k: r[k] for k in keep} for r in rows], "seconds": time.perf_counter() - t0,
+    return {"re_0.2": [{k: r[k] for k in keep} for r in rows],
+            "re_2": [{k: r[k] for k in keep if k not in ("K_hasimoto", "rel_error")} for r in rows2],
+            "largest_d_over_l": 24, "seconds": time.perf_counter() - t0,
             "workload": "one fixed sphere per periodic cube (simple cubic array), body force on the gas, "
-                        "tau 1, run from rest for 10 drag relaxation times"}
+                        "tau 1, run from rest to steady state"}
+
+
+def oracle_check(torch, steps=40, nx=40, ny=48, nz=36):
+    """Every storage against the FP64 CPU oracle (parity build) on a
+    cut-down config 3 the oracle runs in seconds: velocity-field L2
+    (relative), particle position max (lattice units), relative mass drift,
+    particle force max (relative), after `steps` steps."""
+    from oracle import oracle as O
+    from paper_1011_2613_gb300 import lbm as L
+    cfg = I.config3_scaled(nx=nx, ny=ny, nz=nz)
+    ref = O.OracleSim(cfg)
+    ref.step(steps)
+    _, ur, _ = ref.fields()
+    pr = ref.particles()
+    mr = float(ref.populations().sum())
+    out = {}
+    for st in ("f64", "dfdev", "f32dev", "f16dev"):
+        sim = L.Simulation(cfg.replace(storage=st))
+        sim.step(steps)
+        sim.sync()
+        _, ug, _ = sim.fields()
+        pg = sim.particles()
+        d = pg["pos"] - pr["pos"]
+        for ax, n in enumerate(sim.shape):
+            if not (ax == 1 and cfg.wall_y):
+                d[:, ax] -= n * np.round(d[:, ax] / n)
+        out[st] = {"u_l2": float(np.linalg.norm(ug - ur) / np.linalg.norm(ur)),
+                   "pos_max": float(np.sqrt((d ** 2).sum(axis=1)).max()),
+                   "mass_drift": abs(float(sim.populations().sum()) - mr) / mr,
+                   "force_max_rel": float(np.max(np.abs(pg["force"] - pr["force"]))) / float(np.max(np.abs(pr["force"])))}
+        sim.close()
+    ref.close()
+    torch.cuda.empty_cache()
+    out["case"] = f"D3Q19 {nx}x{ny}x{nz} channel, {cfg.n_particles} spheres (config-3 physics), {steps} steps"
+    return out
 
 
 def compare_to(ref, sim, torch):
@@ -510,6 +587,13 @@ def compare_to(ref, sim, torch):
             "mass_drift_rel": abs(mlo - m64) / m64}
 
 
+def sig(x, n=4):
+    """x rounded to n significant digits (compact JSON)."""
+    if x is None or not isinstance(x, (int, float)) or x == 0 or not math.isfinite(x):
+        return x
+    return float(f"{x:.{n}g}")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -527,17 +611,20 @@ def run_ours(args):
     cfg = wl["make"](3 + rank)
     cfg.storage = args.storage
 
-    from paper_1011_2613_gb300 import autotune
     sim = L.Simulation(cfg)
     tune, tuned_steps = pick_collide(sim, args)
     sim.step(args.warmup)
     sim.sync()
-    launches = sim.launches_per_step() * args.steps
+    s0 = sim.steps_done()
+    per_step = sim.launches_per_step()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         ms = time_graph_steps(sim, torch, args.steps)
+    # our kernels inside the timed region: the step graphs, plus the health
+    # check (every 100 steps) where the region crosses a multiple of 100
+    launches = per_step * args.steps + (s0 + args.steps) // 100 - s0 // 100
     value, ms = job_value(ms, cfg.n_nodes, args.steps, world, dist if world > 1 else None, "cuda")
     if world > 1:
         dist.barrier()
@@ -548,6 +635,11 @@ def run_ours(args):
     bpl = algorithmic_bytes_per_lup(cfg, fo)
     t_coll = kms["collide"] / args.steps
     achieved = bpl * cfg.n_nodes / (t_coll * 1e-3) / 1e9
+
+    # the FP64 pipe's measured throughput (test hook), clocks sampled meanwhile
+    with ClockSampler(local) as clk_fp64:
+        fp64_peak, fp64_ms = L.probe_fp64_rate()
+    fp64_clocks = clk_fp64.summary()
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -575,8 +667,9 @@ def run_ours(args):
                "path": "lbm_imb_set_particles -> lbm_imb_step(1) -> lbm_imb_particles, pinned host buffers"}
 
     variants = {}
-    if not args.no_variants and rank == 0 and cfg.storage == "f64":
-        steps_done = tuned_steps + args.warmup + 2 * args.steps + (args.steps if e2e else 0)
+    full = rank == 0 and not args.no_variants and cfg.storage == "f64"
+    if full:
+        steps_done = sim.steps_done()
         forms = [("f32dev", cfg.replace(storage="f32dev")), ("f16dev", cfg.replace(storage="f16dev")),
                  ("dfdev", cfg.replace(storage="dfdev")),  # deviation as FP32 pairs, FP64 accuracy
                  ("f64_eps_table", cfg.replace(eps_method=1)),  # Eq. 6 covered fractions
@@ -590,77 +683,104 @@ def run_ours(args):
             variants["slabs4_f64"], steps_done = measure_slabs(cfg, args, torch, 4, sim, steps_done)
         except Exception as ex:
             variants["slabs4_f64"] = {"error": str(ex)}
-
-    if not args.no_variants and rank == 0 and cfg.storage == "f64":
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    legs = {"batch32_d2q9_f64": lambda: measure_batch(args, torch, peaks, fp64_peak=fp64_peak),
+            "closure_d3q19": lambda: measure_closure(args, torch),
+            "oracle_check": lambda: oracle_check(torch),
+            "table3_sizes": lambda: measure_table3(args, torch),
+            "validation_fixed_sphere": lambda: measure_validation()}
+    for name, fn in legs.items():
+        if not full or (args.no_cpu and name in ("oracle_check", "table3_sizes")):
+            continue
         try:
-            variants["batch32_d2q9_f64"] = measure_batch(args, torch, peaks)
+            variants[name] = fn()
         except Exception as ex:
-            variants["batch32_d2q9_f64"] = {"error": str(ex)}
-
-    if not args.no_variants and rank == 0 and cfg.storage == "f64":
-        try:
-            variants["closure_d3q19"] = measure_closure(args, torch)
-        except Exception as ex:
-            variants["closure_d3q19"] = {"error": str(ex)}
-
-    if not args.no_variants and rank == 0 and cfg.storage == "f64" and not args.no_cpu:
-        try:
-            variants["table3_sizes"] = measure_table3(args, torch)
-        except Exception as ex:
-            variants["table3_sizes"] = {"error": str(ex)}
-
-    if not args.no_variants and rank == 0 and cfg.storage == "f64":
-        try:
-            variants["validation_fixed_sphere"] = measure_validation()
-        except Exception as ex:
-            variants["validation_fixed_sphere"] = {"error": str(ex)}
+            variants[name] = {"error": str(ex)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_sample()
 
-    sim.close()
     kname = collide_kernel_name(cfg.storage, cfg.dim, tune["variant"])
     tb = traffic_per_node(cfg.storage, cfg.dim, tune["variant"])
     traffic = tb * cfg.n_nodes if tb is not None and args.workload in ("cfg3", "cfg3s") else None
     roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname, "bytes_per_lup": bpl,
-                "owned_fraction": fo, "peak_src": peaks["src"],
-                "traffic_src": "ncu capture of the 192x384x192 case scaled by nodes" if traffic else None}
+                "owned_fraction": fo, "peak_src": peaks["src"]}
     if cfg.storage == "f64":
         # the FP64 collision is bound by the FP64 pipe, not by HBM
         per_node, per_cov = FP64_OPS[cfg.dim]
         ops = (per_node + per_cov * fo) * cfg.n_nodes
         gops = ops / (t_coll * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
-                    "unit": "G FP64-pipe op/s", "frac": gops / FP64_PIPE_PEAK_GOPS, "traffic": traffic,
-                    "kernel": kname, "ops_per_node": per_node,
+        roofline = {"bound": "alu", "achieved": gops, "peak": fp64_peak, "unit": "G FP64-pipe op/s",
+                    "frac": gops / fp64_peak, "traffic": traffic, "kernel": kname, "ops_per_node": per_node,
                     "ops_per_covered_node": per_cov, "owned_fraction": fo,
-                    "peak_src": "nominal FP64 1.25 TFLOP/s of the profiling recipe / 2 flops per DFMA"}
+                    "peak_src": "measured in this run: lbm_imb_probe_fp64_rate (FMA chains on every SM)"}
     else:
         roofline = roof_hbm
     if rank == 0:
+        detail = {"variants": variants, "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+                  "profiled_ms_per_step": tot / args.steps, "collide_tuning": tune.get("table"),
+                  "fp64_probe": {"gops": fp64_peak, "ms": fp64_ms, "clocks": fp64_clocks}}
+        print("bench detail " + json.dumps(detail))  # not the result line: context for the compact summary
         clocks = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPE[cfg.storage],
-            "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE[cfg.storage], "data": "synthetic",
             "config": {"workload": wl["name"], "storage": cfg.storage, "nodes": cfg.n_nodes,
                        "particles": cfg.n_particles, "l2": "inputs larger than L2 (two lattices, "
-                       f"{2 * (19 if cfg.dim == 3 else 9) * ESZ[cfg.storage] * cfg.n_nodes / 1e9:.1f} GB)", "graph": "CUDA graph per step"},
-            "roofline": roofline,
-            "roofline_hbm": roof_hbm,
-            "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
-            "profiled_ms_per_step": tot / args.steps,
-            "collide_variant": tune["variant"], "collide_tuning": tune.get("table"),
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "e2e": e2e,
-            "cpu_baseline": cpu,
-            "variants": variants,
+                       f"{2 * (19 if cfg.dim == 3 else 9) * ESZ[cfg.storage] * cfg.n_nodes / 1e9:.1f} GB)",
+                       "graph": "CUDA graph per step"},
+            "roofline": {k: (sig(v) if isinstance(v, float) else v) for k, v in roofline.items()
+                         if k not in ("ops_per_node", "ops_per_covered_node", "owned_fraction")},
+            "roofline_hbm": {k: sig(roof_hbm[k]) for k in ("achieved", "peak", "frac", "bytes_per_lup")},
+            "kernel_ms_per_step": {k: sig(v / args.steps) for k, v in kms.items()},
+            "collide_variant": tune["variant"], "gpu_launches": launches,
+            "clocks": clocks, "fp64_probe_clocks": {k: fp64_clocks.get(k) for k in ("sm_mhz", "reasons")},
+            "e2e": {k: (sig(v) if isinstance(v, float) else v) for k, v in e2e.items() if k != "path"} if e2e else None,
+            "cpu_baseline": {k: (sig(v) if isinstance(v, float) else v) for k, v in cpu.items()
+                             if k in ("value", "unit", "cores", "kind", "nproc", "sample")} if cpu else None,
         }
-        print(json.dumps(line))
+        if variants:
+            line["variants_fields"] = ["mlups", "collide_hbm_frac", "traffic/alg", "u_l2_vs_fp64_run"]
+            line["variants"] = {}
+            for k in ("dfdev", "f32dev", "f16dev", "f64_eps_table", "dfdev_eps_table"):
+                r = variants.get(k, {})
+                if "mlups" in r:
+                    alg = r["bytes_per_lup"] * cfg.n_nodes
+                    line["variants"][k] = [sig(r["mlups"]), sig(r["hbm_frac"], 3),
+                                           sig(r["traffic"] / alg, 3) if r.get("traffic") else None,
+                                           sig(r.get("velocity_l2_rel"), 2)]
+            r = variants.get("slabs4_f64", {})
+            if "mlups" in r:
+                line["variants"]["slabs4_f64"] = [sig(r["mlups"]), None, None,
+                                                  sig(r["particles_vs_whole_rel"]["force"], 2)]
+            oc = variants.get("oracle_check", {})
+            if "f64" in oc:
+                line["vs_oracle_fields"] = ["u_l2", "pos_max_lu", "mass_drift", "force_max_rel"]
+                line["vs_oracle"] = {k: [sig(oc[k][f], 2) for f in ("u_l2", "pos_max", "mass_drift", "force_max_rel")]
+                                     for k in ("f64", "dfdev", "f32dev", "f16dev") if k in oc}
+            b = variants.get("batch32_d2q9_f64", {})
+            if "mlups" in b:
+                line["batch32"] = {"mlups": sig(b["mlups"]), "vs_separate": sig(b["speedup_vs_separate"], 3),
+                                   "fp64_pipe_frac": sig(b["fp64_pipe_frac"], 3), "hbm_frac": sig(b["hbm_frac"], 3)}
+            c = variants.get("closure_d3q19", {})
+            if "held_out_rel_error" in c:
+                e = c["held_out_rel_error"]
+                line["closure"] = {"mlp_err": sig(e["mlp"], 3), "wen_yu_fit_err": sig(e["wen_yu_fit"], 3),
+                                   "stokes_err": sig(e["stokes"], 3), "train_tflops": sig(c["train_tflops"], 3),
+                                   "speedup_vs_resolved": sig(c["speedup_vs_resolved"], 3)}
+            t3 = variants.get("table3_sizes", {})
+            if "rows" in t3:
+                line["table3_gpu_over_c2050"] = [sig(r["gpu_over_paper_gpu"], 3) for r in t3["rows"]]
+            vf = variants.get("validation_fixed_sphere", {})
+            if "re_0.2" in vf:
+                line["validation_re0.2_K_err"] = {str(r["R"]): sig(r["rel_error"], 3) for r in vf["re_0.2"]}
+                line["validation_re2_K"] = {str(r["R"]): sig(r["K"], 4) for r in vf["re_2"]}
+        print(json.dumps(line, separators=(",", ":")))
     if world > 1:
         dist.destroy_process_group()
 
@@ -673,6 +793,23 @@ def run_profile_case(args):
     exactly the warm-up launches of a family); prints the per-family device
     times.  --no-particles removes the particles."""
     from paper_1011_2613_gb300 import lbm as L
+    if args.workload == "mlp":  # the closure network: 4 + steps training steps on minibatches of 8192
+        import torch
+        from paper_1011_2613_gb300 import closure as CL
+        mlp = CL.MLP(max_batch=8192, seed=1)
+        g = torch.Generator(device="cpu").manual_seed(1)
+        x = torch.randn(65536, 6, generator=g).cuda()
+        t = torch.randn(65536, 3, generator=g).cuda()
+        mlp.train(x, t, batch=8192, steps=4, lr=1e-3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(mlp.stream)
+        loss = mlp.train(x, t, batch=8192, steps=args.steps, lr=1e-3)
+        e1.record(mlp.stream)
+        e1.synchronize()
+        print(json.dumps({"workload": "mlp", "batch": 8192, "us_per_train_step": e0.elapsed_time(e1) * 1e3 / args.steps,
+                          "loss": loss}))
+        mlp.close()
+        return
     cfg = WORKLOADS[args.workload]["make"](3).replace(storage=args.storage)
     if args.no_particles:
         z = np.zeros((0, 3))
@@ -694,7 +831,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS) + ["mlp"],
+                    help="mlp: only with --profile-case (training steps of the closure network)")
     ap.add_argument("--storage", default="f64", choices=["f64", "f32dev", "f16dev", "dfdev"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--collide-variant", type=int, default=None,
@@ -708,6 +846,8 @@ def main():
     if args.profile_case:
         run_profile_case(args)
         return
+    if args.workload == "mlp":
+        ap.error("--workload mlp is a --profile-case workload")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -451,7 +451,8 @@ int lbm_imb_slab_member(lbm_imb_t* h, int i, lbm_imb_t** member);
  * Test hooks.  Not part of the simulation interface: they expose one
  * internal piece each (a barrier's timeout path, the tensor-core operand
  * layout, the arctangent and the FP64 <-> pair conversions of the exact
- * covered fractions) so that tests can check it against a reference.
+ * covered fractions) so that tests can check it against a reference, and
+ * one measures the FP64 pipe the FP64 collision is bound by.
  * ================================================================== */
 
 /* Test hook for the barrier timeout path: poll limit of every barrier wait
@@ -480,6 +481,16 @@ int lbm_imb_probe_atan2q1(const double* y, const double* x, double* fast, double
  * back, then synchronises the stream.  EINVAL on null pointers or n < 0. */
 int lbm_imb_probe_df(const float* h, const float* l, const double* d, double* to_double, double* roundtrip,
                      int64_t n, void* stream);
+
+/* Test hook for the FP64 pipe's throughput, the peak the FP64 collision is
+ * measured against: sink_len threads (a multiple of 256; dev_sink holds one
+ * double per thread, device, caller-owned) each run 8 independent chains of
+ * 32 * trips fused multiply-adds; one warm-up launch, then one launch timed
+ * with CUDA events on `stream`.  *gops = FP64-pipe operations (one per FMA)
+ * per second / 1e9, *ms_out (may be NULL) the timed launch's duration.
+ * Synchronises the stream.  EINVAL on bad sizes or pointers. */
+int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64_t trips, double* gops, double* ms_out,
+                            void* stream);
 
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */

@@ -156,8 +156,8 @@ struct RasterSmem {
   int tab_cap, pair_cap, cell_cap;
 };
 
-// bytes of the tables before the covered-node list (the list, cell_cap ints,
-// comes last; the table form keeps only the list)
+// bytes of the tables before the covered-node flags (the flags, one byte
+// per cell, come last; the table form keeps only the flags)
 __host__ __device__ inline int raster_list_offset(const RasterSmem c, int esz) {
   const long long b = (long long)c.tab_cap * esz + 12LL * c.pair_cap * esz + (long long)c.tab_cap * 4 +
                       (long long)c.cell_cap * 4 + c.tab_cap;
@@ -711,11 +711,14 @@ static inline RasterSmem raster_caps(int dim, double rmax) {
   return c;
 }
 
-static inline long long raster_bytes(int dim, int esz, double rmax) {
-  const RasterSmem c = raster_caps(dim, rmax);
-  return (long long)raster_list_offset(c, esz) + (long long)c.cell_cap * 4;
+// the covered-node flags: one byte per cell of the box
+static inline long long raster_list_bytes(int dim, double rmax) {
+  return ((long long)raster_caps(dim, rmax).cell_cap + 15) & ~15LL;
 }
 
-static inline long long raster_list_bytes(int dim, double rmax) { return (long long)raster_caps(dim, rmax).cell_cap * 4; }
+static inline long long raster_bytes(int dim, int esz, double rmax) {
+  const RasterSmem c = raster_caps(dim, rmax);
+  return (long long)raster_list_offset(c, esz) + raster_list_bytes(dim, rmax);
+}
 
 }  // namespace lbm

@@ -299,3 +299,56 @@ extern "C" int lbm_imb_probe_df(const float* h, const float* l, const double* d,
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return LBM_IMB_ECUDA;
   return LBM_IMB_OK;
 }
+
+namespace lbm {
+
+// FP64 pipe rate: every thread runs 8 independent chains of fused
+// multiply-adds (one FP64-pipe slot each), 32 per loop trip; the chains'
+// sums are stored so that nothing is optimised away
+__global__ void __launch_bounds__(256) fp64_rate_kernel(double* sink, long long trips) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) a[k] = 1.0 + 1e-9 * (double)(i + k);
+  const double m = 0.9999999999, c = 1e-13;
+  for (long long t = 0; t < trips; t++) {
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int k = 0; k < 8; k++) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) s += a[k];
+  sink[i] = s;
+}
+
+}  // namespace lbm
+
+extern "C" int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64_t trips, double* gops,
+                                       double* ms_out, void* stream) {
+  if (!dev_sink || sink_len < 256 || sink_len % 256 || sink_len > (1ll << 30) || trips < 1 || !gops)
+    return LBM_IMB_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LBM_IMB_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LBM_IMB_ECUDA;
+  }
+  const unsigned blocks = (unsigned)(sink_len / 256);
+  lbm::fp64_rate_kernel<<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);  // warm-up
+  cudaEventRecord(e0, s);
+  lbm::fp64_rate_kernel<<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess || !(ms > 0.f)) return LBM_IMB_ECUDA;
+  *gops = (double)sink_len * (double)trips * 32.0 / (ms * 1e-3) / 1e9;
+  if (ms_out) *ms_out = ms;
+  return LBM_IMB_OK;
+}

@@ -274,6 +274,7 @@ __device__ __forceinline__ void request_tiles(uint64_t* wbar, __nv_bfloat16* con
 // (actT) and the normalised outputs (y) for the backward pass
 __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float* x, int B, int train,
                                                           float* y_out) {
+  if (*(volatile const int*)P.err != 0) return;  // a wait already timed out: skip the work
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SmemFwd& S = *reinterpret_cast<SmemFwd*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -384,6 +385,7 @@ __device__ __forceinline__ void flush_colsum(float (*colsum)[H], float* gb, int 
 }
 
 __global__ void __launch_bounds__(128) mlp_backward_kernel(Params P, const float* tgt, int B) {
+  if (*(volatile const int*)P.err != 0) return;  // a wait already timed out: skip the work
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SmemBwd& S = *reinterpret_cast<SmemBwd*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -487,6 +489,7 @@ struct SmemWg {
 };
 
 __global__ void __launch_bounds__(128) mlp_wgrad_kernel(Params P, int nblk_total, int per) {
+  if (*(volatile const int*)P.err != 0) return;  // a wait already timed out: skip the work
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SmemWg& S = *reinterpret_cast<SmemWg*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
