@@ -54,17 +54,22 @@ def load_peaks():
 WORKLOADS = {
     "cfg3": dict(make=lambda seed: I.config3(seed=seed),
                  name="D3Q19 384x1512x384 channel (walls y), 129024 spheres R=3.75, density ratio 1000, "
-                      "g=4.704e-7, tau=0.6"),
+                      "g=4.704e-7, tau=0.6",
+                 short="D3Q19 384x1512x384, 129024 spheres R=3.75"),
     "cfg2": dict(make=lambda seed: I.config2(seed=seed),
                  name="D2Q9 8192x32768 periodic, ~267k disks R=4 phi=0.05, density ratio log-uniform "
-                      "[2.5,1500], tau=0.55"),
+                      "[2.5,1500], tau=0.55",
+                 short="D2Q9 8192x32768 periodic, ~267k disks R=4, tau 0.55"),
     "cfg3s": dict(make=lambda seed: I.config3_scaled(nx=192, ny=384, nz=192, seed=seed),
                   name="D3Q19 192x384x192 channel (walls y), config-3 solid fraction, spheres R=3.75, "
-                       "density ratio 1000 (profiling case)"),
+                       "density ratio 1000 (profiling case)",
+                  short="D3Q19 192x384x192 walls y, config-3 physics"),
     "cfg1": dict(make=lambda seed: I.config1(seed=seed),
-                 name="D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6, tau=0.6"),
+                 name="D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6, tau=0.6",
+                 short="D2Q9 128x256 channel, 20 disks R=6"),
     "cfg2s": dict(make=lambda seed: I.periodic2d_config(nx=2048, ny=4096, seed=2 + seed - 3),
-                  name="D2Q9 2048x4096 periodic, config-2 solid fraction, disks R=4 (profiling case)"),
+                  name="D2Q9 2048x4096 periodic, config-2 solid fraction, disks R=4 (profiling case)",
+                  short="D2Q9 2048x4096 periodic, config-2 physics"),
 }
 
 
@@ -75,6 +80,29 @@ WORKLOADS = {
 # cases of `bench.py --profile-case` with and without particles:
 # D3Q19 192x384x192 (covered fraction 0.218), D2Q9 2048x4096 (0.067).
 FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
+# the same counts split by instruction (DADD, DMUL, DFMA), from
+# smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum of the same
+# cases: the roofline's peak is the rate the FP64 pipe sustains on this mix,
+# each kind at its rate measured in the run (lbm_imb_probe_fp64_rate)
+FP64_MIX = {3: ({"add": None, "mul": None, "fma": None}, {"add": None, "mul": None, "fma": None}),
+            2: ({"add": None, "mul": None, "fma": None}, {"add": None, "mul": None, "fma": None})}
+
+
+def fp64_mix(dim, owned_fraction):
+    """FP64 instructions per node of the collision, by kind (None if the
+    split is not known: then all count as FMA)."""
+    node, cov = FP64_MIX[dim]
+    if any(v is None for v in list(node.values()) + list(cov.values())):
+        per_node, per_cov = FP64_OPS[dim]
+        return {"fma": per_node + per_cov * owned_fraction}
+    return {k: node[k] + cov[k] * owned_fraction for k in node}
+
+
+def fp64_peak_for(mix, rates):
+    """G FP64 instructions/s the pipe sustains on an instruction mix: each
+    kind at its own measured rate (time per node = sum of count / rate)."""
+    n = sum(mix.values())
+    return n / sum(c / rates[k] for k, c in mix.items())
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node of
 # one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
 # case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
@@ -206,6 +234,7 @@ def cpu_oracle_sample(steps=None, warmup=0, seconds=15.0):
     sim.close()
     return {"value": cfg.n_nodes * n / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
             "nproc": os.cpu_count(), "steps": n, "seconds": dt,
+            "short": f"D3Q19 {CPU_SAMPLE['nx']}x{CPU_SAMPLE['ny']}x{CPU_SAMPLE['nz']}, {n} steps, OpenMP oracle",
             "sample": f"D3Q19 {CPU_SAMPLE['nx']}x{CPU_SAMPLE['ny']}x{CPU_SAMPLE['nz']} channel, {cfg.n_particles} "
                       f"spheres R=3.75 (config-3 solid fraction and parameters), {n} steps in {dt:.1f} s, FP64 "
                       f"oracle (OpenMP build) on {threads} threads"}
@@ -394,7 +423,7 @@ def measure_slabs(cfg, args, torch, nslabs, ref_sim, steps_target):
             "exchange": "device halo kernel, populations crossing each face only"}, steps_target
 
 
-def measure_batch(args, torch, peaks, n=32, seed=4, fp64_peak=None):
+def measure_batch(args, torch, peaks, n=32, seed=4, fp64_rates=None):
     """Config-4 batch: n independent D2Q9 FP64 suspensions of uneven sizes in
     one persistent graph-replayed launch per step (launch shape from the
     autotuner), against the same lattices stepped one after another."""
@@ -419,10 +448,12 @@ def measure_batch(args, torch, peaks, n=32, seed=4, fp64_peak=None):
     # FP64-pipe work of the collisions (the batch step also rasterises and
     # moves the particles inside the same launch, so this is a lower bound
     # on the collision's share of the pipe)
-    per_node, per_cov = FP64_OPS[2]
-    ops = 0.0
+    mix = {}
     for m in batch.members:
-        ops += (per_node + per_cov * owned_fraction(m, torch)) * m.N
+        for k, c in fp64_mix(2, owned_fraction(m, torch)).items():
+            mix[k] = mix.get(k, 0.0) + c * m.N
+    ops = sum(mix.values())
+    fp64_peak = fp64_peak_for(mix, fp64_rates) if fp64_rates else None
     batch.close()
     del batch
     sep_ms = 0.0
@@ -514,17 +545,20 @@ def measure_validation():
     """The fixed-sphere array (one sphere per periodic cube, phi ~ 0.008,
     body force on the gas, tau 1, exact covered fractions), run to steady
     state: at Re_p ~ 0.2 against Hasimoto's dilute-array result for d/l = 6
-    to 24 (FP64; R = 12 in the FP32-deviation storage), and at Re_p ~ 2 the
+    to 32 (FP64 to R = 8, then the FP32-deviation storage with the Eq. 6
+    covered fractions), and at Re_p ~ 2 the
     drag factor's convergence under refinement (d/l = 6 to 16, FP64)."""
     from paper_1011_2613_gb300 import validation as V
     t0 = time.perf_counter()
     rows = [V.fixed_sphere_drag(R) for R in (3.0, 4.5, 6.0, 8.0)]
-    rows.append(V.fixed_sphere_drag(12.0, relax=8.0, storage="f32dev"))
+    # d/l = 24 and 32: FP32-deviation storage and the Eq. 6 covered fractions
+    # (the exact 3D rasteriser stops at R = 8)
+    rows += [V.fixed_sphere_drag(R, relax=8.0, storage="f32dev", eps_method=1) for R in (12.0, 16.0)]
     rows2 = [V.fixed_sphere_drag(R, relax=8.0, re_p=2.0) for R in (3.0, 4.5, 6.0, 8.0)]
     keep = ("R", "L", "phi", "steps", "K", "K_hasimoto", "rel_error", "re_p", "force_balance")
     return {"re_0.2": [{k: r[k] for k in keep} for r in rows],
             "re_2": [{k: r[k] for k in keep if k not in ("K_hasimoto", "rel_error")} for r in rows2],
-            "largest_d_over_l": 24, "seconds": time.perf_counter() - t0,
+            "largest_d_over_l": 32, "seconds": time.perf_counter() - t0,
             "workload": "one fixed sphere per periodic cube (simple cubic array), body force on the gas, "
                         "tau 1, run from rest to steady state"}
 
@@ -587,6 +621,57 @@ def compare_to(ref, sim, torch):
             "mass_drift_rel": abs(mlo - m64) / m64}
 
 
+def compact_line(head, roofline, roof_hbm, fp64_clocks, e2e, cpu, variants, nodes):
+    """The result line: the contract's keys, then one short summary of every
+    measured form (a few significant digits; the full record is the
+    preceding detail line)."""
+    line = dict(head)
+    line["value"], line["ms_per_step"] = sig(line["value"], 6), sig(line["ms_per_step"], 5)
+    line["clocks"] = {k: line["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    line["roofline"] = {"bound": roofline["bound"], "achieved": sig(roofline["achieved"]),
+                        "peak": sig(roofline["peak"]), "unit": roofline["unit"], "frac": sig(roofline["frac"], 3),
+                        "traffic": sig(roofline["traffic"], 3), "peak_src": roofline.get("peak_short", "measured")}
+    line["roofline_hbm"] = {k: sig(roof_hbm[k], 3) for k in ("achieved", "peak", "frac", "bytes_per_lup")}
+    line["e2e"] = ({k: (sig(v) if isinstance(v, float) else v) for k, v in e2e.items() if k != "path"}
+                   if e2e else None)
+    line["cpu_baseline"] = ({"value": sig(cpu["value"]), "unit": cpu["unit"], "cores": cpu["cores"], "kind": cpu["kind"],
+                             "sample": cpu["short"]} if cpu else None)
+    if not variants:
+        return line
+    vs = {}
+    short = {"dfdev": "dfdev", "f32dev": "f32dev", "f16dev": "f16dev", "f64_eps_table": "f64_tab",
+             "dfdev_eps_table": "dfdev_tab"}
+    for k, nm in short.items():
+        r = variants.get(k, {})
+        if "mlups" in r:
+            alg = r["bytes_per_lup"] * nodes
+            vs[nm] = [sig(r["mlups"]), sig(r["hbm_frac"], 3), sig(r["traffic"] / alg, 3) if r.get("traffic") else None]
+    r = variants.get("slabs4_f64", {})
+    if "mlups" in r:
+        vs["slabs4"] = [sig(r["mlups"])]
+    if vs:
+        line["forms_mlups_hbm_traffic"] = vs
+    oc = variants.get("oracle_check", {})
+    if "f64" in oc:
+        line["vs_oracle_ul2_pos_mass_force"] = {
+            k: [sig(oc[k][f], 2) for f in ("u_l2", "pos_max", "mass_drift", "force_max_rel")]
+            for k in ("dfdev", "f32dev", "f16dev") if k in oc}
+    b = variants.get("batch32_d2q9_f64", {})
+    if "mlups" in b:
+        line["batch32"] = [sig(b["mlups"]), sig(b["speedup_vs_separate"], 3), sig(b["fp64_pipe_frac"], 3)]
+    c = variants.get("closure_d3q19", {})
+    if "held_out_rel_error" in c:
+        e = c["held_out_rel_error"]
+        line["closure"] = {"err_mlp_wenyu_stokes": [sig(e["mlp"], 3), sig(e["wen_yu_fit"], 3), sig(e["stokes"], 3)],
+                           "train_tflops": sig(c["train_tflops"], 3), "speedup": sig(c["speedup_vs_resolved"], 3)}
+    vf = variants.get("validation_fixed_sphere", {})
+    if "re_0.2" in vf:  # d/l = 2R of each row
+        line["valid"] = {"d/l": [int(r["R"] * 2) for r in vf["re_0.2"]],
+                         "Kerr_re0.2": [sig(r["rel_error"], 2) for r in vf["re_0.2"]],
+                         "K_re2": [sig(r["K"], 4) for r in vf["re_2"]]}
+    return line
+
+
 def sig(x, n=4):
     """x rounded to n significant digits (compact JSON)."""
     if x is None or not isinstance(x, (int, float)) or x == 0 or not math.isfinite(x):
@@ -638,7 +723,9 @@ def run_ours(args):
 
     # the FP64 pipe's measured throughput (test hook), clocks sampled meanwhile
     with ClockSampler(local) as clk_fp64:
-        fp64_peak, fp64_ms = L.probe_fp64_rate()
+        fp64_rates, fp64_ms = {}, {}
+        for kind in ("fma", "add", "mul"):
+            fp64_rates[kind], fp64_ms[kind] = L.probe_fp64_rate(kind)
     fp64_clocks = clk_fp64.summary()
 
     # end to end through the C ABI with pinned host buffers
@@ -686,7 +773,7 @@ def run_ours(args):
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    legs = {"batch32_d2q9_f64": lambda: measure_batch(args, torch, peaks, fp64_peak=fp64_peak),
+    legs = {"batch32_d2q9_f64": lambda: measure_batch(args, torch, peaks, fp64_rates=fp64_rates),
             "closure_d3q19": lambda: measure_closure(args, torch),
             "oracle_check": lambda: oracle_check(torch),
             "table3_sizes": lambda: measure_table3(args, torch),
@@ -711,76 +798,32 @@ def run_ours(args):
                 "owned_fraction": fo, "peak_src": peaks["src"]}
     if cfg.storage == "f64":
         # the FP64 collision is bound by the FP64 pipe, not by HBM
-        per_node, per_cov = FP64_OPS[cfg.dim]
-        ops = (per_node + per_cov * fo) * cfg.n_nodes
-        gops = ops / (t_coll * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": gops, "peak": fp64_peak, "unit": "G FP64-pipe op/s",
-                    "frac": gops / fp64_peak, "traffic": traffic, "kernel": kname, "ops_per_node": per_node,
-                    "ops_per_covered_node": per_cov, "owned_fraction": fo,
-                    "peak_src": "measured in this run: lbm_imb_probe_fp64_rate (FMA chains on every SM)"}
+        mix = fp64_mix(cfg.dim, fo)
+        peak = fp64_peak_for(mix, fp64_rates)
+        gops = sum(mix.values()) * cfg.n_nodes / (t_coll * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": gops, "peak": peak, "unit": "G FP64 instr/s",
+                    "frac": gops / peak, "traffic": traffic, "kernel": kname, "mix_per_node": mix,
+                    "owned_fraction": fo, "peak_short": "probe mix",
+                    "peak_src": "measured in this run: lbm_imb_probe_fp64_rate per instruction kind, weighted by "
+                                "the collision's DADD/DMUL/DFMA mix"}
     else:
-        roofline = roof_hbm
+        roofline = dict(roof_hbm, peak_short=peaks["src"])
     if rank == 0:
         detail = {"variants": variants, "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
                   "profiled_ms_per_step": tot / args.steps, "collide_tuning": tune.get("table"),
-                  "fp64_probe": {"gops": fp64_peak, "ms": fp64_ms, "clocks": fp64_clocks}}
-        print("bench detail " + json.dumps(detail))  # not the result line: context for the compact summary
-        clocks = clk.summary()
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPE[cfg.storage], "data": "synthetic",
-            "config": {"workload": wl["name"], "storage": cfg.storage, "nodes": cfg.n_nodes,
-                       "particles": cfg.n_particles, "l2": "inputs larger than L2 (two lattices, "
-                       f"{2 * (19 if cfg.dim == 3 else 9) * ESZ[cfg.storage] * cfg.n_nodes / 1e9:.1f} GB)",
-                       "graph": "CUDA graph per step"},
-            "roofline": {k: (sig(v) if isinstance(v, float) else v) for k, v in roofline.items()
-                         if k not in ("ops_per_node", "ops_per_covered_node", "owned_fraction")},
-            "roofline_hbm": {k: sig(roof_hbm[k]) for k in ("achieved", "peak", "frac", "bytes_per_lup")},
-            "kernel_ms_per_step": {k: sig(v / args.steps) for k, v in kms.items()},
-            "collide_variant": tune["variant"], "gpu_launches": launches,
-            "clocks": clocks, "fp64_probe_clocks": {k: fp64_clocks.get(k) for k in ("sm_mhz", "reasons")},
-            "e2e": {k: (sig(v) if isinstance(v, float) else v) for k, v in e2e.items() if k != "path"} if e2e else None,
-            "cpu_baseline": {k: (sig(v) if isinstance(v, float) else v) for k, v in cpu.items()
-                             if k in ("value", "unit", "cores", "kind", "nproc", "sample")} if cpu else None,
-        }
-        if variants:
-            line["variants_fields"] = ["mlups", "collide_hbm_frac", "traffic/alg", "u_l2_vs_fp64_run"]
-            line["variants"] = {}
-            for k in ("dfdev", "f32dev", "f16dev", "f64_eps_table", "dfdev_eps_table"):
-                r = variants.get(k, {})
-                if "mlups" in r:
-                    alg = r["bytes_per_lup"] * cfg.n_nodes
-                    line["variants"][k] = [sig(r["mlups"]), sig(r["hbm_frac"], 3),
-                                           sig(r["traffic"] / alg, 3) if r.get("traffic") else None,
-                                           sig(r.get("velocity_l2_rel"), 2)]
-            r = variants.get("slabs4_f64", {})
-            if "mlups" in r:
-                line["variants"]["slabs4_f64"] = [sig(r["mlups"]), None, None,
-                                                  sig(r["particles_vs_whole_rel"]["force"], 2)]
-            oc = variants.get("oracle_check", {})
-            if "f64" in oc:
-                line["vs_oracle_fields"] = ["u_l2", "pos_max_lu", "mass_drift", "force_max_rel"]
-                line["vs_oracle"] = {k: [sig(oc[k][f], 2) for f in ("u_l2", "pos_max", "mass_drift", "force_max_rel")]
-                                     for k in ("f64", "dfdev", "f32dev", "f16dev") if k in oc}
-            b = variants.get("batch32_d2q9_f64", {})
-            if "mlups" in b:
-                line["batch32"] = {"mlups": sig(b["mlups"]), "vs_separate": sig(b["speedup_vs_separate"], 3),
-                                   "fp64_pipe_frac": sig(b["fp64_pipe_frac"], 3), "hbm_frac": sig(b["hbm_frac"], 3)}
-            c = variants.get("closure_d3q19", {})
-            if "held_out_rel_error" in c:
-                e = c["held_out_rel_error"]
-                line["closure"] = {"mlp_err": sig(e["mlp"], 3), "wen_yu_fit_err": sig(e["wen_yu_fit"], 3),
-                                   "stokes_err": sig(e["stokes"], 3), "train_tflops": sig(c["train_tflops"], 3),
-                                   "speedup_vs_resolved": sig(c["speedup_vs_resolved"], 3)}
-            t3 = variants.get("table3_sizes", {})
-            if "rows" in t3:
-                line["table3_gpu_over_c2050"] = [sig(r["gpu_over_paper_gpu"], 3) for r in t3["rows"]]
-            vf = variants.get("validation_fixed_sphere", {})
-            if "re_0.2" in vf:
-                line["validation_re0.2_K_err"] = {str(r["R"]): sig(r["rel_error"], 3) for r in vf["re_0.2"]}
-                line["validation_re2_K"] = {str(r["R"]): sig(r["K"], 4) for r in vf["re_2"]}
-        print(json.dumps(line, separators=(",", ":")))
+                  "fp64_probe": {"rates_gops": fp64_rates, "ms": fp64_ms, "clocks": fp64_clocks},
+                  "roofline": roofline, "roofline_hbm": roof_hbm, "e2e": e2e, "cpu_baseline": cpu}
+        # the full record on stderr; stdout holds only the result line
+        print("bench detail " + json.dumps(detail), file=sys.stderr, flush=True)
+        head = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": DTYPE[cfg.storage], "data": "synthetic",
+                "config": {"workload": wl["short"], "storage": cfg.storage,
+                           "l2": f"inputs>L2 ({2 * (19 if cfg.dim == 3 else 9) * ESZ[cfg.storage] * cfg.n_nodes / 1e9:.0f}"
+                                 " GB)"},
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(compact_line(head, roofline, roof_hbm, fp64_clocks, e2e, cpu, variants, cfg.n_nodes),
+                         separators=(",", ":")))
     if world > 1:
         dist.destroy_process_group()
 

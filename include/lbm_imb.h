@@ -116,7 +116,9 @@ typedef struct lbm_imb_config {
   const double* pos;       /* host, [n][3], copied at init */
   const double* vel;       /* host, [n][3], copied at init */
   const double* omega;     /* host, [n][3], copied at init */
-  const double* radius;    /* host, [n], copied at init; > 0 */
+  const double* radius;    /* host, [n], copied at init; > 0 and at most 8
+                            * (3D with exact fractions) or 29 (2D, and 3D
+                            * with eps_method = 1), else LBM_IMB_EUNSUPPORTED */
   const double* density;   /* host, [n], solid density in lattice units */
   double dem_skin;         /* 0: DEM contacts from a cell list rebuilt every
                             * (sub)step; > 0: from Verlet neighbour lists of the
@@ -221,8 +223,9 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
  * persistent queue form with budgets for 4, 3 and 2 CTAs per SM, 5 and 4
  * the pulled-ahead form with 3 and 2, 2 the TMA form, 6 and 7 the split
  * forms (plain nodes in one launch, then the covered nodes listed by the
- * rasteriser in a second: in FP64 for 6, in pair arithmetic for 7); 8 and
- * 9 fall back to 0.
+ * rasteriser in a second: in FP64 for 6, in pair arithmetic for 7, and for
+ * 8 in pair arithmetic by CTAs of 12 warps kept in step by barriers); 9
+ * falls back to 0.
  * Returns EINVAL outside 0..9.  Not for batch members or batches. */
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
 
@@ -485,12 +488,13 @@ int lbm_imb_probe_df(const float* h, const float* l, const double* d, double* to
 /* Test hook for the FP64 pipe's throughput, the peak the FP64 collision is
  * measured against: sink_len threads (a multiple of 256; dev_sink holds one
  * double per thread, device, caller-owned) each run 8 independent chains of
- * 32 * trips fused multiply-adds; one warm-up launch, then one launch timed
- * with CUDA events on `stream`.  *gops = FP64-pipe operations (one per FMA)
- * per second / 1e9, *ms_out (may be NULL) the timed launch's duration.
- * Synchronises the stream.  EINVAL on bad sizes or pointers. */
-int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64_t trips, double* gops, double* ms_out,
-                            void* stream);
+ * 32 * trips FP64 instructions of one kind (0 fused multiply-add, 1 add,
+ * 2 multiply); one warm-up launch, then one launch timed with CUDA events on
+ * `stream`.  *gops = instructions per second / 1e9 (over all threads),
+ * *ms_out (may be NULL) the timed launch's duration.  Synchronises the
+ * stream.  EINVAL on bad sizes, kind or pointers. */
+int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64_t trips, int kind, double* gops,
+                            double* ms_out, void* stream);
 
 /* Release the handle (its CUDA graphs and host state).  The caller's device
  * block is not touched. */

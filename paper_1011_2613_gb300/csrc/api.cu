@@ -151,13 +151,17 @@ int make_layout(const lbm_imb_config* c, Layout* L, bool check_positions = true)
   L->rmax = rmax;
   L->smem = 0;
   if (c->n_particles > 0) {
-    if ((c->dim == 3 && rmax > 8.0) || (c->dim == 2 && rmax > 29.0)) return LBM_IMB_EUNSUPPORTED;
+    // the exact 3D rasteriser keeps its corner tables in shared memory (R <= 8);
+    // the Eq. 6 table form and 2D keep per-axis tables of <= 64 entries
+    const double rlim = (c->dim == 3 && c->eps_method == 0) ? 8.0 : 29.0;
+    if (rmax > rlim) return LBM_IMB_EUNSUPPORTED;
     if (c->eps_method == 1) {  // one table: one radius, and a cell centre never at the table's r < 0
       for (int64_t p = 0; p < c->n_particles; p++)
         if (c->radius[p] != c->radius[0]) return LBM_IMB_EUNSUPPORTED;
       if (!(c->radius[0] > 1.0)) return LBM_IMB_EUNSUPPORTED;
     }
-    L->smem = lbm::eps_raster_smem_bytes(c->dim, c->storage, rmax);
+    L->smem = c->eps_method == 1 ? lbm::eps_table_raster_smem_bytes(c->dim, c->storage, rmax)
+                                 : lbm::eps_raster_smem_bytes(c->dim, c->storage, rmax);
     if (L->smem < 0) return LBM_IMB_EUNSUPPORTED;
   }
   const long long nbins = (long long)L->nb[0] * L->nb[1] * L->nb[2];

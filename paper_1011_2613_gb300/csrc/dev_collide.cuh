@@ -526,7 +526,11 @@ __device__ __forceinline__ void node_rel(const View& v, const Kin<PT>& k, const 
 // The whole warp calls it; lanes with mine = false do the arithmetic on a
 // valid node and write nothing.
 // ---------------------------------------------------------------------------
-template <class LAT, int STORE>
+// SYNC: every thread of the CTA calls this together, and CTA barriers split
+// the update into four stretches of code (solid velocity and beta; the first
+// and the second half of the direction pairs; stores and force sums), so the
+// warps of the CTA run through the long unrolled code side by side.
+template <class LAT, int STORE, bool SYNC = false>
 __device__ __forceinline__ void imb_core(const View& v, const int xx, const int y, const int z, const int n,
                                          const bool mine, typename Storage<STORE>::T (&f)[LAT::Q],
                                          const Moments<typename Storage<STORE>::T>& m) {
@@ -543,18 +547,37 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   const T tau_t = pick<STORE>(v.tau, v.tau_f, v.tau_df);
 
   // owners, sorted by id with empty slots last, so that V_S sums in particle
-  // order.  Slots fill in order, so the taken ones are a prefix; all four
-  // are read at once (one memory round trip instead of a chain).
+  // order.  Slots fill in order, so the taken ones are a prefix: slots 0 and
+  // 1 are read at once, and the rest (and the fractions past the first) only
+  // where the second slot is taken, so that the usual node with one owner
+  // touches two of the eight slot arrays.
   int own[K];
   E eo[K];
   int no = 0;
+  {
+    const int o0 = v.own[0][n], o1 = v.own[1][n];
+    const E e0 = static_cast<const E*>(v.eps[0])[n];
+    own[0] = o0 >= 0 ? o0 : 0x7fffffff;
+    eo[0] = o0 >= 0 ? e0 : E(0);
+    no = o0 >= 0 ? 1 : 0;
 #pragma unroll
-  for (int s = 0; s < K; s++) {
-    const int o = v.own[s][n];
-    const E e = static_cast<const E*>(v.eps[s])[n];
-    own[s] = o >= 0 ? o : 0x7fffffff;
-    eo[s] = o >= 0 ? e : E(0);
-    no += o >= 0 ? 1 : 0;
+    for (int s = 1; s < K; s++) {
+      own[s] = 0x7fffffff;
+      eo[s] = E(0);
+    }
+    if (o1 >= 0) {
+      own[1] = o1;
+      eo[1] = static_cast<const E*>(v.eps[1])[n];
+      no = 2;
+#pragma unroll
+      for (int s = 2; s < K; s++) {
+        const int o = v.own[s][n];
+        if (o < 0) break;
+        own[s] = o;
+        eo[s] = static_cast<const E*>(v.eps[s])[n];
+        no = s + 1;
+      }
+    }
   }
   auto cswap = [&](int a, int b) {
     if (own[a] > own[b]) {
@@ -626,6 +649,7 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   //   Omega^S_q = D + dA + dB,  Omega^S_{-q} = dA - (D + dB),
   //   f*_q = f_q + F_q + (beta - 1) omega g_q + beta Omega^S_q
   // with A = W (k + (c.u_s)^2) (+ w drho), B = sqrt(2) W c.u_s, W = w rho.
+  if constexpr (SYNC) __syncthreads();
   const T rho = m.rho;
   const T vx = T(kSqrt45) * VSx, vy = T(kSqrt45) * VSy, vz = T(kSqrt45) * VSz;
   const T dk = k_of<LAT, STORE>(vx, vy, vz) - m.k;
@@ -639,6 +663,8 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   }
 #pragma unroll
   for (int k = 0; k < NP; k++) {
+    if constexpr (SYNC)
+      if (k == NP / 2) __syncthreads();
     const int q = 2 * k + 1;
     const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
     const T wq = T(LAT::w(q));
@@ -659,6 +685,7 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
     if (cy) my += cy > 0 ? E : -E;
     if (cz) mz += cz > 0 ? E : -E;
   }
+  if constexpr (SYNC) __syncthreads();
   if (mine) {
 #pragma unroll
     for (int q = 0; q < Q; q++)

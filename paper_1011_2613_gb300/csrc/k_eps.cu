@@ -95,6 +95,13 @@ int eps_raster_smem_bytes(int dim, int storage, double rmax) {
   return (int)bytes;
 }
 
+// the Eq. 6 table form keeps only the covered-node flags (pair storage)
+int eps_table_raster_smem_bytes(int dim, int storage, double rmax) {
+  if (storage != LBM_IMB_STORE_DFDEV) return 0;
+  const long long bytes = raster_list_bytes(dim, rmax);
+  return bytes > 200 * 1024 ? -1 : (int)bytes;
+}
+
 void launch_eps_clear(const View& v, bool zero_forces, cudaStream_t s) {
   if (v.np <= 0) return;
   eps_clear_kernel<<<(v.np + 3) / 4, 128, 0, s>>>(v, zero_forces);

@@ -302,9 +302,11 @@ extern "C" int lbm_imb_probe_df(const float* h, const float* l, const double* d,
 
 namespace lbm {
 
-// FP64 pipe rate: every thread runs 8 independent chains of fused
-// multiply-adds (one FP64-pipe slot each), 32 per loop trip; the chains'
-// sums are stored so that nothing is optimised away
+// FP64 pipe rate: every thread runs 8 independent chains of one FP64
+// instruction (KIND 0 fused multiply-add, 1 add, 2 multiply; one FP64-pipe
+// operation each), 32 per loop trip; the chains' sums are stored so that
+// nothing is optimised away
+template <int KIND>
 __global__ void __launch_bounds__(256) fp64_rate_kernel(double* sink, long long trips) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double a[8];
@@ -315,7 +317,11 @@ __global__ void __launch_bounds__(256) fp64_rate_kernel(double* sink, long long 
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll
-      for (int k = 0; k < 8; k++) a[k] = fma(a[k], m, c);
+      for (int k = 0; k < 8; k++) {
+        if constexpr (KIND == 0) a[k] = fma(a[k], m, c);
+        else if constexpr (KIND == 1) a[k] = __dadd_rn(a[k], c);
+        else a[k] = __dmul_rn(a[k], m);
+      }
   }
   double s = 0.0;
 #pragma unroll
@@ -325,9 +331,10 @@ __global__ void __launch_bounds__(256) fp64_rate_kernel(double* sink, long long 
 
 }  // namespace lbm
 
-extern "C" int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64_t trips, double* gops,
+extern "C" int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64_t trips, int kind, double* gops,
                                        double* ms_out, void* stream) {
-  if (!dev_sink || sink_len < 256 || sink_len % 256 || sink_len > (1ll << 30) || trips < 1 || !gops)
+  if (!dev_sink || sink_len < 256 || sink_len % 256 || sink_len > (1ll << 30) || trips < 1 || !gops ||
+      kind < 0 || kind > 2)
     return LBM_IMB_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
@@ -337,9 +344,14 @@ extern "C" int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64
     return LBM_IMB_ECUDA;
   }
   const unsigned blocks = (unsigned)(sink_len / 256);
-  lbm::fp64_rate_kernel<<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);  // warm-up
+  auto launch = [&]() {
+    if (kind == 0) lbm::fp64_rate_kernel<0><<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);
+    else if (kind == 1) lbm::fp64_rate_kernel<1><<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);
+    else lbm::fp64_rate_kernel<2><<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);
+  };
+  launch();  // warm-up
   cudaEventRecord(e0, s);
-  lbm::fp64_rate_kernel<<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);
+  launch();
   cudaEventRecord(e1, s);
   cudaError_t e = cudaEventSynchronize(e1);
   float ms = 0.f;

@@ -13,7 +13,8 @@
 // Completion is signalled through tcgen05.commit on an mbarrier; epilogues
 // read the accumulator with tcgen05.ld (32 lanes x 16 columns per
 // instruction).  A training step is four launches: forward (keeps the
-// activations), backward (gradients of the pre-activations, bias gradients),
+// activations, zeroes the gradient sums), backward (gradients of the
+// pre-activations, bias gradients),
 // the weight-gradient products, and Adam fused with the refresh of the BF16
 // operand tiles.
 //
@@ -278,6 +279,10 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SmemFwd& S = *reinterpret_cast<SmemFwd*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
+  if (train) {  // the step's gradient and loss sums start from zero (the backward pass adds to them)
+    for (int i = blockIdx.x * blockDim.x + tid; i < kNumParams; i += gridDim.x * blockDim.x) P.g[i] = 0.f;
+    if (blockIdx.x == 0 && tid == 0) *P.loss = 0.f;
+  }
   if (tid == 0) {
     __nv_bfloat16* dst[5] = {S.w1, S.w[0], S.w[1], S.w[2], S.w5};
     __nv_bfloat16* src[5] = {P.wt[0], P.wt[1], P.wt[2], P.wt[3], P.wt[4]};
@@ -805,11 +810,9 @@ cudaError_t launch_wgrad(lbm_imb_mlp* h, int B) {
 }
 
 // one training step's products on the minibatch x [B][6], t [B][3]: the
-// gradients (flat, zeroed first) and the loss
+// gradients (flat; the forward pass zeroes them) and the loss
 cudaError_t launch_gradients(lbm_imb_mlp* h, const float* x, const float* t, int B) {
-  cudaError_t e = cudaMemsetAsync(h->P.g, 0, (size_t)kNumParams * 4, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->P.loss, 0, 4, h->stream);
-  if (e == cudaSuccess) e = launch_forward(h, x, B, 1, nullptr);
+  cudaError_t e = launch_forward(h, x, B, 1, nullptr);
   if (e == cudaSuccess) e = launch_backward(h, t, B);
   if (e == cudaSuccess) e = launch_wgrad(h, B);
   return e;

@@ -147,10 +147,11 @@ static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
 
 // collide forms of the pair storage that update plain and covered nodes in
 // two launches (the covered ones from the rasteriser's list): covered nodes
-// in FP64 (kCollideSplit) or in pair arithmetic (kCollideSplit + 1)
+// in FP64 (kCollideSplit) or in pair arithmetic (kCollideSplit + 1, and + 2
+// with each CTA's warps in step)
 constexpr int kCollideSplit = 6;
 __host__ __device__ inline bool split_form(int variant) {
-  return variant == kCollideSplit || variant == kCollideSplit + 1;
+  return variant >= kCollideSplit && variant <= kCollideSplit + 2;
 }
 
 // bytes of one stored population; whether the covered fractions (and the
@@ -169,6 +170,7 @@ void launch_init_equilibrium(const View& v, void* f, cudaStream_t s);
 void launch_eps_clear(const View& v, bool zero_forces, cudaStream_t s);
 void launch_eps_raster(const View& v, int smem_bytes, cudaStream_t s);
 int eps_raster_smem_bytes(int dim, int storage, double rmax);
+int eps_table_raster_smem_bytes(int dim, int storage, double rmax);
 long long eps_table_entries(int dim);
 void eps_table_geometry(int dim, double R, float* lo_r, float* h_r, float* h_s, float* h_t);
 cudaError_t launch_eps_table_build(int dim, double R, float* tab, cudaStream_t s);

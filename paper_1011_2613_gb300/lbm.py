@@ -130,7 +130,7 @@ def lib():
             L.lbm_imb_batch_set_barrier_test.restype = C.c_int
             L.lbm_imb_batch_set_barrier_test.argtypes = [C.c_void_p, C.c_int64, C.c_int]
             L.lbm_imb_probe_fp64_rate.restype = C.c_int
-            L.lbm_imb_probe_fp64_rate.argtypes = [C.c_void_p, C.c_int64, C.c_int64, _dp, _dp, C.c_void_p]
+            L.lbm_imb_probe_fp64_rate.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int, _dp, _dp, C.c_void_p]
             L.lbm_imb_probe_df.restype = C.c_int
             L.lbm_imb_probe_df.argtypes = [C.c_void_p] * 5 + [C.c_int64, C.c_void_p]
             L.lbm_imb_probe_atan2q1.restype = C.c_int
@@ -507,9 +507,12 @@ def probe_df(h, l, d):
     return to_double, roundtrip
 
 
-def probe_fp64_rate(trips: int = 20000, blocks_per_sm: int = 8, device=None):
-    """Measured FP64-pipe throughput of this GPU (G operations/s, one per
-    fused multiply-add) and the timed launch's ms (test hook)."""
+FP64_KINDS = {"fma": 0, "add": 1, "mul": 2}
+
+
+def probe_fp64_rate(kind: str = "fma", trips: int = 20000, blocks_per_sm: int = 8, device=None):
+    """Measured FP64 throughput of this GPU for one instruction kind ("fma",
+    "add", "mul"; G instructions/s) and the timed launch's ms (test hook)."""
     import torch
     dev = torch.device(device if device is not None else "cuda")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -517,8 +520,8 @@ def probe_fp64_rate(trips: int = 20000, blocks_per_sm: int = 8, device=None):
     sink = torch.empty(n, dtype=torch.float64, device=dev)
     g, ms = C.c_double(), C.c_double()
     s = torch.cuda.current_stream(dev)
-    _check(lib().lbm_imb_probe_fp64_rate(C.c_void_p(sink.data_ptr()), n, int(trips), C.byref(g), C.byref(ms),
-                                         C.c_void_p(s.cuda_stream)), "lbm_imb_probe_fp64_rate")
+    _check(lib().lbm_imb_probe_fp64_rate(C.c_void_p(sink.data_ptr()), n, int(trips), FP64_KINDS[kind], C.byref(g),
+                                         C.byref(ms), C.c_void_p(s.cuda_stream)), "lbm_imb_probe_fp64_rate")
     return float(g.value), float(ms.value)
 
 
