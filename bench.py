@@ -84,8 +84,8 @@ FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
 # smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum of the same
 # cases: the roofline's peak is the rate the FP64 pipe sustains on this mix,
 # each kind at its rate measured in the run (lbm_imb_probe_fp64_rate)
-FP64_MIX = {3: ({"add": None, "mul": None, "fma": None}, {"add": None, "mul": None, "fma": None}),
-            2: ({"add": None, "mul": None, "fma": None}, {"add": None, "mul": None, "fma": None})}
+FP64_MIX = {3: ({"add": 58.33, "mul": 29.00, "fma": 71.00}, {"add": 112.0, "mul": 32.3, "fma": 114.4}),
+            2: ({"add": 18.00, "mul": 18.00, "fma": 31.00}, {"add": 79.7, "mul": 29.7, "fma": 67.8})}
 
 
 def fp64_mix(dim, owned_fraction):

@@ -231,6 +231,9 @@ struct Params {
   // layer l's pre-activation output (H rows; NOUT rows for l = 4)
   __nv_bfloat16* actT[5];
   __nv_bfloat16* dactT[5];
+  // ReLU masks of H_1..H_4 (mask[l], l = 1..4): bit c of sample m's 128 bits
+  // = (BF16 H_l[m][c] > 0), uint4 [B]; read by the backward pass
+  uint4* mask[5];
   float* y;                // network output, normalised [B][NOUT]
   float* loss;             // [1]
   int* err;                // [1]
@@ -323,6 +326,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
       // epilogue: this warp's 32 rows
       const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
       const float* bias = P.b[l];
+      uint32_t mb0 = 0u, mb1 = 0u, mb2 = 0u, mb3 = 0u;  // ReLU mask words (registers, not an array)
       for (int c0 = 0; c0 < lay_N(l); c0 += 16) {
         float r[16];
         tc_ld16(lane_base + c0, r);
@@ -332,7 +336,15 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
             const float hv = fmaxf(r[i] + bias[c0 + i], 0.f);
             const __nv_bfloat16 bv = __float2bfloat16_rn(hv);
             S.a[cm_index(tid, c0 + i, H)] = bv;
-            if (train) P.actT[l + 1][tblock_index(c0 + i, row, H)] = valid ? bv : __float2bfloat16_rn(0.f);
+            if (train) {
+              P.actT[l + 1][tblock_index(c0 + i, row, H)] = valid ? bv : __float2bfloat16_rn(0.f);
+              const uint32_t bit = __bfloat162float(bv) > 0.f ? 1u << ((c0 + i) & 31) : 0u;
+              const int w = (c0 + i) >> 5;
+              mb0 |= w == 0 ? bit : 0u;
+              mb1 |= w == 1 ? bit : 0u;
+              mb2 |= w == 2 ? bit : 0u;
+              mb3 |= w == 3 ? bit : 0u;
+            }
           }
         } else if (valid) {
 #pragma unroll
@@ -343,6 +355,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(Params P, const float*
           }
         }
       }
+      if (train && l < 4) P.mask[l + 1][row] = make_uint4(mb0, mb1, mb2, mb3);
       proxy_fence();
       tc_fence_before();
       __syncthreads();
@@ -370,15 +383,24 @@ struct SmemBwd {
   uint32_t tmem;
 };
 
-// column sums of one 16-column slice over the warp's 32 samples, by lane 0
+// column sums of one 16-column slice over the warp's 32 samples: a
+// butterfly that halves the columns a lane carries at each exchange (16
+// shuffles instead of 5 per column); lane L ends with the sum of column
+// 8 b4 + 4 b3 + 2 b2 + b1 (b_k the bits of L), written by the even lanes
 __device__ __forceinline__ void warp_colsum16(const float (&g)[16], float* out) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  float a[8], b[4], c[2];
+  const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
 #pragma unroll
-  for (int i = 0; i < 16; i++) {
-    float v = g[i];
+  for (int i = 0; i < 8; i++) a[i] = (u16 ? g[8 + i] : g[i]) + __shfl_xor_sync(FULL, u16 ? g[i] : g[8 + i], 16);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) out[i] = v;
-  }
+  for (int i = 0; i < 4; i++) b[i] = (u8 ? a[4 + i] : a[i]) + __shfl_xor_sync(FULL, u8 ? a[i] : a[4 + i], 8);
+#pragma unroll
+  for (int i = 0; i < 2; i++) c[i] = (u4 ? b[2 + i] : b[i]) + __shfl_xor_sync(FULL, u4 ? b[i] : b[2 + i], 4);
+  float d = (u2 ? c[1] : c[0]) + __shfl_xor_sync(FULL, u2 ? c[0] : c[1], 2);
+  d += __shfl_xor_sync(FULL, d, 1);
+  if ((lane & 1) == 0) out[(u16 ? 8 : 0) + (u8 ? 4 : 0) + (u4 ? 2 : 0) + (u2 ? 1 : 0)] = d;
 }
 
 // the CTA's per-warp column sums [4][n] -> atomic adds into gb[n]
@@ -444,16 +466,15 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(Params P, const float
       ok = tc_gemm(S.d, Bt, H, l == 4 ? NOUT : H, tmem, &S.bar, phase, &S.wbar[4 - l]);
       if (!ok) break;
       const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      const uint4 mk = P.mask[l][row];  // H_l > 0 (rows past the batch: all clear)
       for (int c0 = 0; c0 < H; c0 += 16) {
         float r[16], gl[16];
         tc_ld16(lane_base + c0, r);
+        const uint32_t word = c0 < 64 ? (c0 < 32 ? mk.x : mk.y) : (c0 < 96 ? mk.z : mk.w);
+        const uint32_t bits = word >> (c0 & 31);
 #pragma unroll
         for (int i = 0; i < 16; i++) {
-          gl[i] = 0.f;
-          if (valid) {
-            const float hv = __bfloat162float(P.actT[l][tblock_index(c0 + i, row, H)]);
-            gl[i] = hv > 0.f ? r[i] : 0.f;
-          }
+          gl[i] = (valid && ((bits >> i) & 1u)) ? r[i] : 0.f;
           const __nv_bfloat16 bg = __float2bfloat16_rn(gl[i]);
           S.d[cm_index(tid, c0 + i, H)] = bg;
           P.dactT[l - 1][tblock_index(c0 + i, row, H)] = bg;
@@ -714,6 +735,7 @@ void mlp_sizes(int64_t B, size_t* sz, int* n) {
   sz[k++] = 32 * 4;                                                        // norm
   for (int l = 0; l < 5; l++) sz[k++] = Bp * act_rows(l) * 2;              // actT
   for (int l = 0; l < 5; l++) sz[k++] = Bp * dact_rows(l) * 2;             // dactT
+  for (int l = 0; l < 5; l++) sz[k++] = l == 0 ? 16 : Bp * 16;             // mask (l = 1..4)
   sz[k++] = Bp * NOUT * 4;                                                 // y
   sz[k++] = 16;                                                            // loss
   sz[k++] = 16;                                                            // err
@@ -752,6 +774,7 @@ void mlp_bind(lbm_imb_mlp* h, unsigned char* base, const MlpLayout& L) {
   P.norm = (float*)(base + L.off[k++]);
   for (int l = 0; l < 5; l++) P.actT[l] = (__nv_bfloat16*)(base + L.off[k++]);
   for (int l = 0; l < 5; l++) P.dactT[l] = (__nv_bfloat16*)(base + L.off[k++]);
+  for (int l = 0; l < 5; l++) P.mask[l] = (uint4*)(base + L.off[k++]);
   P.y = (float*)(base + L.off[k++]);
   P.loss = (float*)(base + L.off[k++]);
   P.err = (int*)(base + L.off[k++]);
