@@ -272,7 +272,9 @@ __device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-template <class LAT, int STORE>
+// PLAIN: the plain part of a split form (pair storage): covered nodes are
+// skipped (the covered kernel updates them), no queue
+template <class LAT, int STORE, bool PLAIN = false>
 __global__ void __launch_bounds__(128) collide_tma_kernel(View v, int ntiles) {
   using S = Storage<STORE>;
   using T = typename S::T;
@@ -413,33 +415,38 @@ __global__ void __launch_bounds__(128) collide_tma_kernel(View v, int ntiles) {
       f[q] = S::load_shared(cur + q * RW::STRIDE, off);
     }
     const int n = (z * ny + y) * pitch + xx;
-    fused_core<LAT, STORE>(v, xx, y, z, n, active, f, wq, cnt, tid & 31);
+    if constexpr (PLAIN) {
+      const bool covered = active && v.own[0][n] >= 0;
+      plain_core<LAT, STORE>(v, n, active && !covered, f);
+    } else {
+      fused_core<LAT, STORE>(v, xx, y, z, n, active, f, wq, cnt, tid & 31);
+    }
     __syncthreads();  // buffer b is free for the tile after next
     halo = halo_next;
   }
-  queue_drain<LAT, STORE>(v, wq, cnt, tid & 31);
+  if constexpr (!PLAIN) queue_drain<LAT, STORE>(v, wq, cnt, tid & 31);
 }
 
-template <class LAT, int STORE>
+template <class LAT, int STORE, bool PLAIN = false>
 static int tma_smem_bytes() {
   using RW = TmaRow<STORE>;
-  return 2 * LAT::Q * RW::STRIDE * RW::ES + 4 * queue_bytes_per_warp<LAT, STORE>();
+  return 2 * LAT::Q * RW::STRIDE * RW::ES + (PLAIN ? 0 : 4 * queue_bytes_per_warp<LAT, STORE>());
 }
 
-template <class LAT, int STORE>
+template <class LAT, int STORE, bool PLAIN = false>
 static void launch_tma(const View& v, cudaStream_t s) {
   static int grid = 0;
-  const int smem = tma_smem_bytes<LAT, STORE>();
+  const int smem = tma_smem_bytes<LAT, STORE, PLAIN>();
   if (grid == 0) {
     int per_sm = 0, dev = 0, sms = 0;
-    cudaFuncSetAttribute(collide_tma_kernel<LAT, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_tma_kernel<LAT, STORE>, 128, smem);
+    cudaFuncSetAttribute(collide_tma_kernel<LAT, STORE, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_tma_kernel<LAT, STORE, PLAIN>, 128, smem);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
   const int ntiles = ((v.nx + TX - 1) / TX) * v.ny * v.nz;
-  collide_tma_kernel<LAT, STORE><<<grid < ntiles ? grid : ntiles, 128, smem, s>>>(v, ntiles);
+  collide_tma_kernel<LAT, STORE, PLAIN><<<grid < ntiles ? grid : ntiles, 128, smem, s>>>(v, ntiles);
 }
 
 template <class LAT, int STORE, int MINB, bool PREFETCH>
@@ -476,17 +483,18 @@ static void launch_split(const View& v, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
     grid_a = (per_sm > 0 ? per_sm : 1) * sms;
     per_sm = 0;
-    if constexpr (COVERED == 1)
+    if constexpr (COVERED == 1 || COVERED == 3)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_pair_kernel<LAT>, 128, 0);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
     grid_b = (per_sm > 0 ? per_sm : 1) * sms;
   }
   const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
-  collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
+  if constexpr (COVERED == 3) launch_tma<LAT, STORE, true>(v, s);  // plain part staged by bulk copies
+  else collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
   if (v.cov_list == nullptr) return;
   if constexpr (COVERED == 2) collide_covered_pair_sync_kernel<LAT><<<sms, kCoveredSyncThreads, 0, s>>>(v);
-  else if constexpr (COVERED == 1) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+  else if constexpr (COVERED == 1 || COVERED == 3) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
   else collide_covered_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
 }
 
@@ -538,7 +546,8 @@ static void dispatch(const View& v, cudaStream_t s) {
     // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
     // split forms (plain nodes, then the rasteriser's covered-node list: 6
     // in FP64, 7 in pair arithmetic, 8 in pair arithmetic with each CTA's
-    // warps in step); the other numbers use 0
+    // warps in step, 9 as 7 with the plain part's rows staged in shared
+    // memory by bulk copies); the other numbers use 0
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;
@@ -548,6 +557,7 @@ static void dispatch(const View& v, cudaStream_t s) {
       case kCollideSplit: launch_split<LAT, STORE, 0>(v, s); break;
       case kCollideSplit + 1: launch_split<LAT, STORE, 1>(v, s); break;
       case kCollideSplit + 2: launch_split<LAT, STORE, 2>(v, s); break;
+      case kCollideSplit + 3: launch_split<LAT, STORE, 3>(v, s); break;
       default: launch_fused<LAT, STORE, 4, false>(v, s);
     }
   } else {

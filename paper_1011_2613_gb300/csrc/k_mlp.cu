@@ -720,8 +720,12 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 // samples of the per-minibatch arrays: whole 128-sample tiles
 int64_t padded_batch(int64_t B) { return (B + TILE - 1) / TILE * TILE; }
 
+// arrays of the parameter block (mlp_sizes lists them in this order):
+// p, m, v, g; wt[5]; wtt[5]; norm; actT[5]; dactT[5]; mask[5]; y, loss, err
+constexpr int kMlpArrays = 4 + 5 + 5 + 1 + 5 + 5 + 5 + 3;
+
 struct MlpLayout {
-  size_t off[32];
+  size_t off[kMlpArrays];
   size_t total;
 };
 
@@ -729,24 +733,29 @@ struct MlpLayout {
 void mlp_sizes(int64_t B, size_t* sz, int* n) {
   const size_t Bp = (size_t)padded_batch(B);
   int k = 0;
-  for (int i = 0; i < 4; i++) sz[k++] = (size_t)kNumParams * 4;  // p, m, v, g
-  for (int l = 0; l < 5; l++) sz[k++] = (size_t)lay_N(l) * lay_K(l) * 2;  // wt
-  for (int l = 0; l < 5; l++) sz[k++] = (size_t)lay_N(l) * lay_K(l) * 2;  // wtt
-  sz[k++] = 32 * 4;                                                        // norm
-  for (int l = 0; l < 5; l++) sz[k++] = Bp * act_rows(l) * 2;              // actT
-  for (int l = 0; l < 5; l++) sz[k++] = Bp * dact_rows(l) * 2;             // dactT
-  for (int l = 0; l < 5; l++) sz[k++] = l == 0 ? 16 : Bp * 16;             // mask (l = 1..4)
-  sz[k++] = Bp * NOUT * 4;                                                 // y
-  sz[k++] = 16;                                                            // loss
-  sz[k++] = 16;                                                            // err
-  *n = k;
+  auto put = [&](size_t bytes) {  // never writes past kMlpArrays entries
+    if (k < kMlpArrays) sz[k] = bytes;
+    k++;
+  };
+  for (int i = 0; i < 4; i++) put((size_t)kNumParams * 4);           // p, m, v, g
+  for (int l = 0; l < 5; l++) put((size_t)lay_N(l) * lay_K(l) * 2);  // wt
+  for (int l = 0; l < 5; l++) put((size_t)lay_N(l) * lay_K(l) * 2);  // wtt
+  put(32 * 4);                                                        // norm
+  for (int l = 0; l < 5; l++) put(Bp * act_rows(l) * 2);              // actT
+  for (int l = 0; l < 5; l++) put(Bp * dact_rows(l) * 2);             // dactT
+  for (int l = 0; l < 5; l++) put(l == 0 ? 16 : Bp * 16);             // mask (l = 1..4)
+  put(Bp * NOUT * 4);                                                 // y
+  put(16);                                                            // loss
+  put(16);                                                            // err
+  *n = k;  // == kMlpArrays
 }
 
 int mlp_layout(int64_t B, MlpLayout* L) {
   if (B < 1 || B > (1ll << 24)) return LBM_IMB_EINVAL;
-  size_t sz[32];
+  size_t sz[kMlpArrays];
   int n = 0;
   mlp_sizes(B, sz, &n);
+  if (n != kMlpArrays) return LBM_IMB_EINVAL;  // the list and kMlpArrays disagree (a build error)
   size_t o = 0;
   for (int i = 0; i < n; i++) {
     L->off[i] = o;
