@@ -526,11 +526,7 @@ __device__ __forceinline__ void node_rel(const View& v, const Kin<PT>& k, const 
 // The whole warp calls it; lanes with mine = false do the arithmetic on a
 // valid node and write nothing.
 // ---------------------------------------------------------------------------
-// SYNC: every thread of the CTA calls this together, and CTA barriers split
-// the update into four stretches of code (solid velocity and beta; the first
-// and the second half of the direction pairs; stores and force sums), so the
-// warps of the CTA run through the long unrolled code side by side.
-template <class LAT, int STORE, bool SYNC = false>
+template <class LAT, int STORE>
 __device__ __forceinline__ void imb_core(const View& v, const int xx, const int y, const int z, const int n,
                                          const bool mine, typename Storage<STORE>::T (&f)[LAT::Q],
                                          const Moments<typename Storage<STORE>::T>& m) {
@@ -649,7 +645,6 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   //   Omega^S_q = D + dA + dB,  Omega^S_{-q} = dA - (D + dB),
   //   f*_q = f_q + F_q + (beta - 1) omega g_q + beta Omega^S_q
   // with A = W (k + (c.u_s)^2) (+ w drho), B = sqrt(2) W c.u_s, W = w rho.
-  if constexpr (SYNC) __syncthreads();
   const T rho = m.rho;
   const T vx = T(kSqrt45) * VSx, vy = T(kSqrt45) * VSy, vz = T(kSqrt45) * VSz;
   const T dk = k_of<LAT, STORE>(vx, vy, vz) - m.k;
@@ -663,8 +658,6 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   }
 #pragma unroll
   for (int k = 0; k < NP; k++) {
-    if constexpr (SYNC)
-      if (k == NP / 2) __syncthreads();
     const int q = 2 * k + 1;
     const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
     const T wq = T(LAT::w(q));
@@ -685,7 +678,6 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
     if (cy) my += cy > 0 ? E : -E;
     if (cz) mz += cz > 0 ? E : -E;
   }
-  if constexpr (SYNC) __syncthreads();
   if (mine) {
 #pragma unroll
     for (int q = 0; q < Q; q++)

@@ -142,34 +142,6 @@ __global__ void __launch_bounds__(128, 3) collide_covered_pair_kernel(View v) {
   }
 }
 
-// Form 8 of the pair storage: the covered part in pair arithmetic as above,
-// by CTAs of 12 warps (one CTA per SM) that take 384 list entries at a time
-// and pass CTA barriers between the stretches of the update, so that all
-// warps of an SM run through the long unrolled update side by side and one
-// fetch of each instruction serves all of them (the update's code does not
-// fit the instruction cache).
-constexpr int kCoveredSyncThreads = 384;
-template <class LAT>
-__global__ void __launch_bounds__(kCoveredSyncThreads, 1) collide_covered_pair_sync_kernel(View v) {
-  constexpr int STORE = LBM_IMB_STORE_DFDEV;
-  constexpr int Q = LAT::Q;
-  const int count = *v.cov_count;
-  const int row = v.ny * v.pitch;
-  for (int base = blockIdx.x * kCoveredSyncThreads; base < count; base += gridDim.x * kCoveredSyncThreads) {
-    const int i = base + (int)threadIdx.x;  // the loop is uniform over the CTA
-    const bool mine = i < count;
-    const int n = v.cov_list[mine ? i : base];
-    const int z = n / row, r = n - z * row;
-    const int y = r / v.pitch, x = r - y * v.pitch;
-    DF f[Q];
-    pull<LAT, STORE>(v, x, y, z, n, true, f);
-    const Moments<DF> m = moments<LAT, STORE>(v, f);
-    __syncthreads();
-    imb_core<LAT, STORE, true>(v, x, y, z, n, mine, f, m);
-    __syncthreads();
-  }
-}
-
 // CTA-packed form: one CTA per 128-node row tile (no persistence).
 template <class LAT, int STORE, int MINB>
 __global__ void __launch_bounds__(128, MINB) collide_packed_kernel(View v) {
@@ -272,9 +244,7 @@ __device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// PLAIN: the plain part of a split form (pair storage): covered nodes are
-// skipped (the covered kernel updates them), no queue
-template <class LAT, int STORE, bool PLAIN = false>
+template <class LAT, int STORE>
 __global__ void __launch_bounds__(128) collide_tma_kernel(View v, int ntiles) {
   using S = Storage<STORE>;
   using T = typename S::T;
@@ -415,38 +385,33 @@ __global__ void __launch_bounds__(128) collide_tma_kernel(View v, int ntiles) {
       f[q] = S::load_shared(cur + q * RW::STRIDE, off);
     }
     const int n = (z * ny + y) * pitch + xx;
-    if constexpr (PLAIN) {
-      const bool covered = active && v.own[0][n] >= 0;
-      plain_core<LAT, STORE>(v, n, active && !covered, f);
-    } else {
-      fused_core<LAT, STORE>(v, xx, y, z, n, active, f, wq, cnt, tid & 31);
-    }
+    fused_core<LAT, STORE>(v, xx, y, z, n, active, f, wq, cnt, tid & 31);
     __syncthreads();  // buffer b is free for the tile after next
     halo = halo_next;
   }
-  if constexpr (!PLAIN) queue_drain<LAT, STORE>(v, wq, cnt, tid & 31);
+  queue_drain<LAT, STORE>(v, wq, cnt, tid & 31);
 }
 
-template <class LAT, int STORE, bool PLAIN = false>
+template <class LAT, int STORE>
 static int tma_smem_bytes() {
   using RW = TmaRow<STORE>;
-  return 2 * LAT::Q * RW::STRIDE * RW::ES + (PLAIN ? 0 : 4 * queue_bytes_per_warp<LAT, STORE>());
+  return 2 * LAT::Q * RW::STRIDE * RW::ES + 4 * queue_bytes_per_warp<LAT, STORE>();
 }
 
-template <class LAT, int STORE, bool PLAIN = false>
+template <class LAT, int STORE>
 static void launch_tma(const View& v, cudaStream_t s) {
   static int grid = 0;
-  const int smem = tma_smem_bytes<LAT, STORE, PLAIN>();
+  const int smem = tma_smem_bytes<LAT, STORE>();
   if (grid == 0) {
     int per_sm = 0, dev = 0, sms = 0;
-    cudaFuncSetAttribute(collide_tma_kernel<LAT, STORE, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_tma_kernel<LAT, STORE, PLAIN>, 128, smem);
+    cudaFuncSetAttribute(collide_tma_kernel<LAT, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_tma_kernel<LAT, STORE>, 128, smem);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
   const int ntiles = ((v.nx + TX - 1) / TX) * v.ny * v.nz;
-  collide_tma_kernel<LAT, STORE, PLAIN><<<grid < ntiles ? grid : ntiles, 128, smem, s>>>(v, ntiles);
+  collide_tma_kernel<LAT, STORE><<<grid < ntiles ? grid : ntiles, 128, smem, s>>>(v, ntiles);
 }
 
 template <class LAT, int STORE, int MINB, bool PREFETCH>
@@ -470,8 +435,7 @@ static void launch_fused(const View& v, cudaStream_t s) {
   else collide_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);
 }
 
-// COVERED: 0 FP64 (form 6), 1 pair arithmetic (form 7), 2 pair arithmetic
-// with the CTA's warps in step (form 8)
+// COVERED: 0 FP64 (form 6), 1 pair arithmetic (form 7)
 template <class LAT, int STORE, int COVERED>
 static void launch_split(const View& v, cudaStream_t s) {
   static int grid_a = 0, grid_b = 0, sms = 0;
@@ -483,18 +447,16 @@ static void launch_split(const View& v, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
     grid_a = (per_sm > 0 ? per_sm : 1) * sms;
     per_sm = 0;
-    if constexpr (COVERED == 1 || COVERED == 3)
+    if constexpr (COVERED == 1)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_pair_kernel<LAT>, 128, 0);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
     grid_b = (per_sm > 0 ? per_sm : 1) * sms;
   }
   const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
-  if constexpr (COVERED == 3) launch_tma<LAT, STORE, true>(v, s);  // plain part staged by bulk copies
-  else collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
+  collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
   if (v.cov_list == nullptr) return;
-  if constexpr (COVERED == 2) collide_covered_pair_sync_kernel<LAT><<<sms, kCoveredSyncThreads, 0, s>>>(v);
-  else if constexpr (COVERED == 1 || COVERED == 3) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+  if constexpr (COVERED == 1) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
   else collide_covered_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
 }
 
@@ -545,9 +507,7 @@ static void dispatch(const View& v, cudaStream_t s) {
     // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
     // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
     // split forms (plain nodes, then the rasteriser's covered-node list: 6
-    // in FP64, 7 in pair arithmetic, 8 in pair arithmetic with each CTA's
-    // warps in step, 9 as 7 with the plain part's rows staged in shared
-    // memory by bulk copies); the other numbers use 0
+    // in FP64, 7 in pair arithmetic); the other numbers use 0
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;
@@ -556,8 +516,7 @@ static void dispatch(const View& v, cudaStream_t s) {
       case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
       case kCollideSplit: launch_split<LAT, STORE, 0>(v, s); break;
       case kCollideSplit + 1: launch_split<LAT, STORE, 1>(v, s); break;
-      case kCollideSplit + 2: launch_split<LAT, STORE, 2>(v, s); break;
-      case kCollideSplit + 3: launch_split<LAT, STORE, 3>(v, s); break;
+
       default: launch_fused<LAT, STORE, 4, false>(v, s);
     }
   } else {

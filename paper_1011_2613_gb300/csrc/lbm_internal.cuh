@@ -147,12 +147,10 @@ static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
 
 // collide forms of the pair storage that update plain and covered nodes in
 // two launches (the covered ones from the rasteriser's list): covered nodes
-// in FP64 (kCollideSplit) or in pair arithmetic (kCollideSplit + 1; + 2
-// with each CTA's warps in step; + 3 with the plain part staged by bulk
-// copies)
+// in FP64 (kCollideSplit) or in pair arithmetic (kCollideSplit + 1)
 constexpr int kCollideSplit = 6;
 __host__ __device__ inline bool split_form(int variant) {
-  return variant >= kCollideSplit && variant <= kCollideSplit + 3;
+  return variant == kCollideSplit || variant == kCollideSplit + 1;
 }
 
 // bytes of one stored population; whether the covered fractions (and the
