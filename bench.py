@@ -126,6 +126,8 @@ def collide_kernel_name(storage, dim, form):
         return f"collide_plain_kernel<{lat},dfdev> + collide_covered_kernel<{lat}>"
     if storage == "dfdev" and form == 7:
         return f"collide_plain_kernel<{lat},dfdev> + collide_covered_pair_kernel<{lat}>"
+    if storage == "dfdev" and form == 8:
+        return f"collide_plain_pair_kernel<{lat}> + collide_covered_pair_kernel<{lat}>"
     if form in (4, 5):
         return f"collide_prefetch_kernel<{lat},{storage}>"
     if form in (6, 7) and storage != "dfdev":

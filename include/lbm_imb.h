@@ -223,8 +223,9 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
  * persistent queue form with budgets for 4, 3 and 2 CTAs per SM, 5 and 4
  * the pulled-ahead form with 3 and 2, 2 the TMA form, 6 and 7 the split
  * forms (plain nodes in one launch, then the covered nodes listed by the
- * rasteriser in a second: in FP64 for 6, in pair arithmetic for 7); 8 and
- * 9 fall back to 0.
+ * rasteriser in a second: in FP64 for 6, in pair arithmetic for 7, and
+ * for 8 as 7 with the plain part two adjacent nodes per thread in paired
+ * FP32 instructions); 9 falls back to 0.
  * Returns EINVAL outside 0..9.  Not for batch members or batches. */
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
 

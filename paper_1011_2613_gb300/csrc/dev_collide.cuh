@@ -115,11 +115,25 @@ struct Storage<kDfDevImb> {
   }
 };
 
+// the pair storage's plain update of two adjacent nodes at once in paired
+// FP32 instructions (DF2; internal id, not a storage of the C ABI): the
+// arithmetic type only; the two-node kernel does its own loads and stores
+constexpr int kDfDevPair = 17;
+template <>
+struct Storage<kDfDevPair> {
+  using Elem = float2;
+  using T = DF2;
+  using E = double;
+  static constexpr bool DEV = true;
+  static constexpr bool SCALED = false;
+};
+
 // a per-simulation constant in the arithmetic type of the storage
 template <int STORE>
 __device__ __forceinline__ typename Storage<STORE>::T pick(const double d, const float f, const float (&p)[2]) {
   if constexpr (STORE == LBM_IMB_STORE_F64 || STORE == kDfDevImb) return d;
   else if constexpr (STORE == LBM_IMB_STORE_DFDEV) return DF(p[0], p[1]);
+  else if constexpr (STORE == kDfDevPair) return DF2(DF(p[0], p[1]));
   else return f;
 }
 
@@ -1085,6 +1099,72 @@ __device__ __forceinline__ void pair_node(const View& v, const int x, const int 
     mm.uz = sf[(Q + 4) * CAP + s];
     mm.k = k_of<LAT, STORE, float>(mm.ux, mm.uy, mm.uz);
     imb_core<LAT, STORE>(v, sxy[s] & 0xffff, sxy[s] >> 16, sz[s], sn[s], mine, g, mm);
+  }
+  (void)NP;
+}
+
+// ---------------------------------------------------------------------------
+// Plain part of the pair storage's split form, two adjacent nodes x, x+1 (x
+// even) per thread in paired FP32 instructions (DF2): directions with
+// c_x = 0 come as one aligned 16-byte load of both nodes' pairs, the others
+// as two 8-byte loads; the moments and BGK of both nodes run side by side
+// (bitwise the single-node results); uncovered nodes are stored (aligned
+// 16 bytes when both are), covered ones are left to the covered kernel.
+// ---------------------------------------------------------------------------
+template <class LAT>
+__device__ __forceinline__ void plain_pair_node(const View& v, const int x, const int y, const int z,
+                                                const bool row_ok) {
+  constexpr int Q = LAT::Q;
+  constexpr int NP = (Q - 1) / 2;
+  constexpr int ST = kDfDevPair;
+  const int nx = v.nx, ny = v.ny, nz = v.nz, pitch = v.pitch;
+  const bool a0 = row_ok && x < nx, a1 = row_ok && x + 1 < nx;
+  const int xc = a0 ? x : ((nx - 1) & ~1);  // a valid even node for idle lanes
+  const int n = (z * ny + y) * pitch + xc;
+  const int2 o = *reinterpret_cast<const int2*>(v.own[0] + n);
+  const bool s0 = a0 && o.x < 0, s1 = a1 && o.y < 0;  // stored here (not covered)
+  if (!__any_sync(0xffffffffu, s0 || s1)) return;     // the whole warp's nodes are covered (or idle)
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+  const int ry[3] = {y * pitch, ym * pitch, yp * pitch};
+  const int rz[3] = {z * ny * pitch, zm * ny * pitch, zp * ny * pitch};
+  const int l0 = xc == 0 ? nx - 1 : xc - 1, l1 = xc;
+  const int r0 = xc + 1 < nx ? xc + 1 : 0, r1 = xc + 2 < nx ? xc + 2 : (xc + 2 == nx ? 0 : 1);
+  const bool wlo = v.wall_lo && y == v.y0, whi = v.wall_hi && y == v.y0 + v.ny_c - 1;
+  DF2 f[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
+    const int row = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)];
+    const bool bounce = (cy == 1 && wlo) || (cy == -1 && whi);
+    float4 w;
+    if (bounce) {  // halfway bounce-back: the opposite populations of the pair itself
+      w = __ldg(reinterpret_cast<const float4*>(static_cast<const float2*>(v.src_q[opp(q)]) + n));
+    } else {
+      const float2* src = static_cast<const float2*>(v.src_q[q]);
+      if (cx == 0) {
+        w = __ldg(reinterpret_cast<const float4*>(src + row + xc));
+      } else {
+        const float2 e0 = __ldg(src + row + (cx == 1 ? l0 : r0));
+        const float2 e1 = __ldg(src + row + (cx == 1 ? l1 : r1));
+        w = make_float4(e0.x, e0.y, e1.x, e1.y);
+      }
+    }
+    f[q] = DF2(make_float2(w.x, w.z), make_float2(w.y, w.w));
+  }
+  const Moments<DF2> m = moments<LAT, ST>(v, f);
+  DF2 out[Q];
+  bgk<LAT, ST>(v, m, f, out);
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const DF2 r = df_norm(out[q]);
+    float2* dst = static_cast<float2*>(v.dst_q[q]) + n;
+    if (s0 && s1) {
+      *reinterpret_cast<float4*>(dst) = make_float4(r.h.x, r.l.x, r.h.y, r.l.y);
+    } else {
+      if (s0) dst[0] = make_float2(r.h.x, r.l.x);
+      if (s1) dst[1] = make_float2(r.h.y, r.l.y);
+    }
   }
   (void)NP;
 }

@@ -198,4 +198,95 @@ __device__ __forceinline__ double df_to_bits(const DF xx) {
   return __longlong_as_double((long long)bits);
 }
 
+// Two pair values (the same node quantity of two adjacent nodes) processed
+// together by the paired FP32 instructions of this GPU (FADD2 / FMUL2 /
+// FFMA2): every step of the pair operations above, lane by lane, each
+// rounded on its own, so DF2 gives bitwise the results of two DF
+// computations.  Subtraction is a fused multiply-add by -1 (one rounding,
+// the same value as the subtraction).
+struct DF2 {
+  float2 h, l;
+  __device__ __forceinline__ DF2() {}
+  __device__ __forceinline__ DF2(float2 a, float2 b) : h(a), l(b) {}
+  __device__ __forceinline__ DF2(const DF a) : h(make_float2(a.h, a.h)), l(make_float2(a.l, a.l)) {}
+  __device__ __forceinline__ DF2(int a) : h(make_float2((float)a, (float)a)), l(make_float2(0.f, 0.f)) {}
+  __device__ __forceinline__ explicit DF2(double d) : DF2(DF(d)) {}
+  __device__ __forceinline__ DF lo() const { return DF(h.x, l.x); }
+  __device__ __forceinline__ DF hi() const { return DF(h.y, l.y); }
+  friend __device__ DF2 df2_fma(const DF2 a, const DF2 b, const DF2 c);
+  friend __device__ __forceinline__ DF2 fma(const DF2 a, const DF2 b, const DF2 c) { return df2_fma(a, b, c); }
+};
+
+__device__ __forceinline__ float2 f2_sub(const float2 a, const float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 f2_neg(const float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+
+__device__ __forceinline__ DF2 fast_two_sum2(const float2 a, const float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  return DF2(s, f2_sub(b, f2_sub(s, a)));
+}
+
+__device__ __forceinline__ DF2 df_norm(const DF2 a) {
+#if LBM_DF_LAZY
+  return fast_two_sum2(a.h, a.l);
+#else
+  return a;
+#endif
+}
+
+__device__ __forceinline__ DF2 operator+(const DF2 a, const DF2 b) {
+  const float2 s = __fadd2_rn(a.h, b.h);
+  const float2 bb = f2_sub(s, a.h);
+  float2 e = __fadd2_rn(f2_sub(a.h, f2_sub(s, bb)), f2_sub(b.h, bb));
+  e = __fadd2_rn(e, __fadd2_rn(a.l, b.l));
+#if LBM_DF_LAZY
+  return DF2(s, e);
+#else
+  return fast_two_sum2(s, e);
+#endif
+}
+__device__ __forceinline__ DF2 operator-(const DF2 a) { return DF2(f2_neg(a.h), f2_neg(a.l)); }
+__device__ __forceinline__ DF2 operator-(const DF2 a, const DF2 b) { return a + (-b); }
+
+__device__ __forceinline__ DF2 operator*(const DF2 a, const DF2 b) {
+  const float2 p = __fmul2_rn(a.h, b.h);
+  float2 e = __ffma2_rn(a.h, b.h, f2_neg(p));
+  e = __ffma2_rn(a.h, b.l, e);
+  e = __ffma2_rn(a.l, b.h, e);
+#if LBM_DF_LAZY
+  return DF2(p, e);
+#else
+  return fast_two_sum2(p, e);
+#endif
+}
+
+// a b + c with one normalisation: found by argument-dependent lookup only,
+// through the friend declaration in DF2 (does not hide ::fma for other types)
+__device__ __forceinline__ DF2 df2_fma(const DF2 a, const DF2 b, const DF2 c) {
+  const float2 p = __fmul2_rn(a.h, b.h);
+  float2 e = __ffma2_rn(a.h, b.h, f2_neg(p));
+  e = __ffma2_rn(a.h, b.l, e);
+  e = __ffma2_rn(a.l, b.h, e);
+  const float2 s = __fadd2_rn(p, c.h);
+  const float2 bb = f2_sub(s, p);
+  float2 t = __fadd2_rn(f2_sub(p, f2_sub(s, bb)), f2_sub(c.h, bb));
+  t = __fadd2_rn(t, __fadd2_rn(e, c.l));
+#if LBM_DF_LAZY
+  return DF2(s, t);
+#else
+  const float2 r = __fadd2_rn(s, t);
+  return DF2(r, f2_sub(t, f2_sub(r, s)));
+#endif
+}
+
+// 1 / a lane by lane (the hardware reciprocal has no paired form)
+__device__ __forceinline__ DF2 rcp(const DF2 x) {
+  const DF2 a = df_norm(x);
+  const float2 r = make_float2(__frcp_rn(a.h.x), __frcp_rn(a.h.y));
+  float2 t = __ffma2_rn(f2_neg(a.h), r, make_float2(1.f, 1.f));  // 1 - h r, exact
+  t = __ffma2_rn(f2_neg(a.l), r, t);
+  return fast_two_sum2(r, __fmul2_rn(r, t));
+}
+
 }  // namespace lbm

@@ -84,6 +84,20 @@ __global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntile
   }
 }
 
+// Split form of the pair storage, plain part with two nodes per thread
+// (form 8): CTA = 128 nodes (64 pairs) of two consecutive rows; grid x over
+// row pairs, grid y over 128-node x tiles.
+template <class LAT>
+__global__ void __launch_bounds__(128, 3) collide_plain_pair_kernel(View v) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = v.ny_c * v.nz;
+  const int r = blockIdx.x * 2 + (warp >> 1);
+  const bool row_ok = r < rows;
+  const int rr = row_ok ? r : rows - 1;
+  const int x = blockIdx.y * 128 + ((warp & 1) * 32 + lane) * 2;
+  plain_pair_node<LAT>(v, x, v.y0 + rr % v.ny_c, rr / v.ny_c, row_ok);
+}
+
 // Split form, covered part: each warp takes 32 entries of the covered-node
 // list (grouped by particle, so the warp's force sums mostly go to one
 // owner), pulls and takes the moments in pair arithmetic, and gives the
@@ -435,7 +449,8 @@ static void launch_fused(const View& v, cudaStream_t s) {
   else collide_kernel<LAT, STORE, MINB><<<g, 128, smem, s>>>(v, ntiles);
 }
 
-// COVERED: 0 FP64 (form 6), 1 pair arithmetic (form 7)
+// COVERED: 0 FP64 (form 6), 1 pair arithmetic (form 7), 2 pair arithmetic
+// with the plain part two nodes per thread (form 8)
 template <class LAT, int STORE, int COVERED>
 static void launch_split(const View& v, cudaStream_t s) {
   static int grid_a = 0, grid_b = 0, sms = 0;
@@ -447,16 +462,21 @@ static void launch_split(const View& v, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
     grid_a = (per_sm > 0 ? per_sm : 1) * sms;
     per_sm = 0;
-    if constexpr (COVERED == 1)
+    if constexpr (COVERED >= 1)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_pair_kernel<LAT>, 128, 0);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
     grid_b = (per_sm > 0 ? per_sm : 1) * sms;
   }
   const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
-  collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
+  if constexpr (COVERED == 2) {  // the plain part two nodes per thread
+    const dim3 grid((v.ny_c * v.nz + 1) / 2, (v.nx + 127) / 128);
+    collide_plain_pair_kernel<LAT><<<grid, 128, 0, s>>>(v);
+  } else {
+    collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
+  }
   if (v.cov_list == nullptr) return;
-  if constexpr (COVERED == 1) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+  if constexpr (COVERED >= 1) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
   else collide_covered_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
 }
 
@@ -507,7 +527,8 @@ static void dispatch(const View& v, cudaStream_t s) {
     // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
     // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
     // split forms (plain nodes, then the rasteriser's covered-node list: 6
-    // in FP64, 7 in pair arithmetic); the other numbers use 0
+    // in FP64, 7 in pair arithmetic, 8 as 7 with two plain nodes per thread
+    // in paired instructions); the other numbers use 0
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;
@@ -516,7 +537,7 @@ static void dispatch(const View& v, cudaStream_t s) {
       case 5: launch_fused<LAT, STORE, 3, true>(v, s); break;
       case kCollideSplit: launch_split<LAT, STORE, 0>(v, s); break;
       case kCollideSplit + 1: launch_split<LAT, STORE, 1>(v, s); break;
-
+      case kCollideSplit + 2: launch_split<LAT, STORE, 2>(v, s); break;
       default: launch_fused<LAT, STORE, 4, false>(v, s);
     }
   } else {

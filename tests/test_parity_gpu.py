@@ -212,7 +212,7 @@ def test_spinning_particles_torque_3d(storage):
     assert np.max(np.abs(pg["omega"] - pr["omega"])) < 1e-12
 
 
-@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6), ("dfdev", 7)])
+@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6), ("dfdev", 7), ("dfdev", 8)])
 def test_config3_shape_channel_3d(storage, form):
     """Cut-down config 3 (D3Q19, walls in y, spheres R=3.75, ratio 1000)."""
     cfg = I.config3_scaled(nx=40, ny=48, nz=36, storage=storage)
@@ -284,8 +284,9 @@ def test_reduced_storage_error(storage, tol_u, tol_f):
 def test_collide_variants_agree(dim, storage):
     """Every kernel form gives bitwise the populations of form 0 after one
     step (nx = 300 spans ragged row tiles), and the FP64 forms stay within
-    the oracle tolerance after 12 steps.  Form 7 of the pair storage updates
-    covered nodes in pair arithmetic instead of FP64: within 1e-14 there."""
+    the oracle tolerance after 12 steps.  Forms 7 and 8 of the pair storage
+    update covered nodes in pair arithmetic instead of FP64: within 1e-14
+    there."""
     if dim == 3:
         cfg = I.config3_scaled(nx=300, ny=20, nz=12).replace(storage=storage)
     else:
@@ -298,7 +299,7 @@ def test_collide_variants_agree(dim, storage):
         sim = L.Simulation(cfg)
         sim.set_collide_variant(var)
         sim.step(1)
-        if storage == "dfdev" and var == 7:
+        if storage == "dfdev" and var in (7, 8):
             assert rel_err(sim.populations(), f_base) < 1e-14, f"variant {var}"
         else:
             assert np.array_equal(sim.populations(), f_base), f"variant {var}"
@@ -309,6 +310,33 @@ def test_collide_variants_agree(dim, storage):
             assert rel_err(sim.populations(), ref.populations()) < POP_TOL, f"variant {var}"
     with pytest.raises(L.LbmImbError):
         base.set_collide_variant(10)
+
+
+@pytest.mark.parametrize("nx", [300, 131, 64])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pair_storage_two_node_plain_part_is_bitwise(dim, nx):
+    """Form 8 of the pair storage (plain part two nodes per thread in paired
+    FP32 instructions) gives bitwise the populations of form 7 (one node per
+    thread) after a step: the paired instructions round every lane on its
+    own.  Odd and even row lengths, walls in y."""
+    if dim == 3:
+        cfg = I.config3_scaled(nx=nx, ny=20, nz=12).replace(storage="dfdev")
+    else:
+        cfg = I.channel_config(nx=nx, ny=64, n_particles=6, radius=5.0, storage="dfdev")
+    L = lbm()
+    a = L.Simulation(cfg)
+    a.set_collide_variant(7)
+    b = L.Simulation(cfg)
+    b.set_collide_variant(8)
+    f0 = I.random_populations(np.random.default_rng(4), cfg)
+    a.set_populations(f0)
+    b.set_populations(f0)
+    a.step(1)
+    b.step(1)
+    assert np.array_equal(a.populations(), b.populations())
+    a.step(20)
+    b.step(20)
+    assert rel_err(b.populations(), a.populations()) < 1e-13  # later: the force atomics' order
 
 
 @pytest.mark.parametrize("storage", ["f32dev", "f16dev"])
