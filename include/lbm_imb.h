@@ -486,13 +486,15 @@ int lbm_imb_probe_df(const float* h, const float* l, const double* d, double* to
                      int64_t n, void* stream);
 
 /* Test hook for the FP64 pipe's throughput, the peak the FP64 collision is
- * measured against: sink_len threads (a multiple of 256; dev_sink holds one
- * double per thread, device, caller-owned) each run 8 independent chains of
- * 32 * trips FP64 instructions of one kind (0 fused multiply-add, 1 add,
- * 2 multiply); one warm-up launch, then one launch timed with CUDA events on
- * `stream`.  *gops = instructions per second / 1e9 (over all threads),
- * *ms_out (may be NULL) the timed launch's duration.  Synchronises the
- * stream.  EINVAL on bad sizes, kind or pointers. */
+ * measured against: one wave of resident 256-thread blocks on every SM (at
+ * most sink_len threads; sink_len a multiple of 256; dev_sink holds one
+ * double per thread, device, caller-owned), each thread running 16
+ * independent chains of 32 * trips FP64 instructions of one kind (0 fused
+ * multiply-add, 1 add, 2 multiply); one warm-up launch, then one launch
+ * timed with CUDA events on `stream`.  *gops = instructions per second /
+ * 1e9 (over all threads), *ms_out (may be NULL) the timed launch's
+ * duration.  Synchronises the stream.  EINVAL on bad sizes, kind or
+ * pointers. */
 int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64_t trips, int kind, double* gops,
                             double* ms_out, void* stream);
 

@@ -1108,8 +1108,9 @@ __device__ __forceinline__ void pair_node(const View& v, const int x, const int 
 // even) per thread in paired FP32 instructions (DF2): directions with
 // c_x = 0 come as one aligned 16-byte load of both nodes' pairs, the others
 // as two 8-byte loads; the moments and BGK of both nodes run side by side
-// (bitwise the single-node results); uncovered nodes are stored (aligned
-// 16 bytes when both are), covered ones are left to the covered kernel.
+// (bitwise the single-node results); uncovered nodes are pulled and stored
+// (aligned 16 bytes when both are), covered ones are left to the covered
+// kernel.
 // ---------------------------------------------------------------------------
 template <class LAT>
 __device__ __forceinline__ void plain_pair_node(const View& v, const int x, const int y, const int z,
@@ -1137,20 +1138,22 @@ __device__ __forceinline__ void plain_pair_node(const View& v, const int x, cons
     const int cx = LAT::c(q, 0), cy = LAT::c(q, 1), cz = LAT::c(q, 2);
     const int row = rz[cz == 0 ? 0 : (cz == 1 ? 1 : 2)] + ry[cy == 0 ? 0 : (cy == 1 ? 1 : 2)];
     const bool bounce = (cy == 1 && wlo) || (cy == -1 && whi);
-    float4 w;
-    if (bounce) {  // halfway bounce-back: the opposite populations of the pair itself
-      w = __ldg(reinterpret_cast<const float4*>(static_cast<const float2*>(v.src_q[opp(q)]) + n));
+    // only the nodes stored here are pulled (the covered kernel pulls the
+    // others); both as one aligned 16-byte load where the sources are adjacent
+    const float2* src = static_cast<const float2*>(v.src_q[bounce ? opp(q) : q]);
+    const bool adj = bounce || cx == 0;  // halfway bounce-back: the pair's own opposite populations
+    const int i0 = bounce ? n : row + (cx == 0 ? xc : (cx == 1 ? l0 : r0));
+    const int i1 = bounce ? n + 1 : row + (cx == 0 ? xc + 1 : (cx == 1 ? l1 : r1));
+    float2 e0 = make_float2(0.f, 0.f), e1 = make_float2(0.f, 0.f);
+    if (adj && s0 && s1) {
+      const float4 w = __ldg(reinterpret_cast<const float4*>(src + i0));
+      e0 = make_float2(w.x, w.y);
+      e1 = make_float2(w.z, w.w);
     } else {
-      const float2* src = static_cast<const float2*>(v.src_q[q]);
-      if (cx == 0) {
-        w = __ldg(reinterpret_cast<const float4*>(src + row + xc));
-      } else {
-        const float2 e0 = __ldg(src + row + (cx == 1 ? l0 : r0));
-        const float2 e1 = __ldg(src + row + (cx == 1 ? l1 : r1));
-        w = make_float4(e0.x, e0.y, e1.x, e1.y);
-      }
+      if (s0) e0 = __ldg(src + i0);
+      if (s1) e1 = __ldg(src + i1);
     }
-    f[q] = DF2(make_float2(w.x, w.z), make_float2(w.y, w.w));
+    f[q] = DF2(make_float2(e0.x, e1.x), make_float2(e0.y, e1.y));
   }
   const Moments<DF2> m = moments<LAT, ST>(v, f);
   DF2 out[Q];

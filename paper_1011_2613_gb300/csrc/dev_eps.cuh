@@ -460,7 +460,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ T kax[3][64];  // 3D: v (3 R^2 - v^2) / 2 of every axis value v
   __shared__ T ax_s[2][64], ax_psi[2][64];  // 2D per-axis tables
   __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
-  __shared__ int n_part, n_need, cov_base, cov_wsum[4];
+  __shared__ int n_part, n_need, n_pin, cov_base, cov_wsum[4];
   // nodes whose first owner slot this particle claims (split collision):
   // one flag per cell of the box, compacted in box order (x fastest, then
   // y, then z) at the end, so that the list holds each particle's nodes in
@@ -478,6 +478,7 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     }
     n_part = 0;
     n_need = 0;
+    n_pin = 0;
   }
   if (!rows_meet_slab(v, lo[1], ne[1])) return;  // another slab's particle (block-uniform)
   for (int t = threadIdx.x; t < 3 * 64; t += blockDim.x) {
@@ -607,31 +608,62 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
       ax_psi[d][i] = atan2_q1(su, u);
     }
   } else {
+    // entries whose edge line meets the ball are listed first (the list
+    // shares the corner list's space, built later) and then evaluated by
+    // consecutive threads, so that no lane idles through the square root
+    // and arctangents of its neighbours; the others are the limit z -> 0
+    // of the angles, zero
     const int axes[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     const int n01 = tx * ty, n02 = tx * tz, n12 = ty * tz;
     const FastDiv dx(tx), dy(ty);
-    for (int t = threadIdx.x; t < n01 + n02 + n12; t += blockDim.x) {
-      const int g = t < n01 ? 0 : (t < n01 + n02 ? 1 : 2);
-      const int r = t - (g == 0 ? 0 : (g == 1 ? n01 : n01 + n02));
+    auto pair_entry = [&](const int t, int& g, int& r, T& u, T& w) -> T {
+      g = t < n01 ? 0 : (t < n01 + n02 ? 1 : 2);
+      r = t - (g == 0 ? 0 : (g == 1 ? n01 : n01 + n02));
       const FastDiv& dv = g == 2 ? dy : dx;
       const int j = dv.div(r), i = r - j * (int)dv.d;
-      const T u = val[axes[g][0]][i], w = val[axes[g][1]][j];
-      const T z2 = (R * R - u * u) - w * w;
-      T* e = pr + 4 * (g * cap.pair_cap + r);
-      if (z2 > T(0)) {
-        const T z = sqrt(z2);
-        e[0] = (u * w) * z;
-        e[1] = atan2_q1(R * z, u * w);
-        e[2] = atan2_q1(z, u);
-        e[3] = atan2_q1(z, w);
-      } else {  // edge line outside the ball: the limit z -> 0 of the angles
+      u = val[axes[g][0]][i];
+      w = val[axes[g][1]][j];
+      return (R * R - u * u) - w * w;
+    };
+    for (int t = threadIdx.x; t < n01 + n02 + n12; t += blockDim.x) {
+      int g, r;
+      T u, w;
+      if (pair_entry(t, g, r, u, w) > T(0)) {
+        clist[atomicAdd(&n_pin, 1)] = t;
+      } else {
+        T* e = pr + 4 * (g * cap.pair_cap + r);
         e[0] = e[1] = e[2] = e[3] = T(0);
       }
     }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n_pin; q += blockDim.x) {
+      int g, r;
+      T u, w;
+      const T z = sqrt(pair_entry(clist[q], g, r, u, w));
+      T* e = pr + 4 * (g * cap.pair_cap + r);
+      e[0] = (u * w) * z;
+      e[1] = atan2_q1(R * z, u * w);
+      e[2] = atan2_q1(z, u);
+      e[3] = atan2_q1(z, w);
+    }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < tsize; t += blockDim.x)
-    if (need[t]) clist[atomicAdd(&n_need, 1)] = t;
+  // needed corners inside the ball are listed (the others are zero), so
+  // that the closed forms below run on consecutive threads
+  const FastDiv3 tdiv(tx, ty);
+  auto corner_inside = [&](const int t) -> bool {
+    int i, j, k;
+    tdiv.split(t, i, j, k);
+    const T a = val[0][i], b = val[1][j];
+    if (DIM == 2) return a * a + b * b < R * R;
+    const T cc = val[2][k];
+    return (a * a + b * b) + cc * cc < R * R;
+  };
+  for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
+    if (!need[t]) continue;
+    if (corner_inside(t)) clist[atomicAdd(&n_need, 1)] = t;
+    else tab[t] = T(0);
+  }
   __syncthreads();
 
   // pass 2: the needed corner values.  3D: with the face angles
@@ -642,7 +674,6 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   // a A_a - b A_b - c A_c collects to
   //   3P = R^3 (sum(alpha) - pi) - sum_d k_d th_d + sum_pairs u v z_uv - 3abc,
   // k_d = v_d (3R^2 - v_d^2) / 2 per axis value, u v z_uv per pair entry.
-  const FastDiv3 tdiv(tx, ty);
   const T R3 = R * R * R;
   const T piR3 = T(3.14159265358979323846) * R3;
   for (int q = threadIdx.x; q < n_need; q += blockDim.x) {
@@ -650,27 +681,24 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     int i, j, k;
     tdiv.split(t, i, j, k);
     const T a = val[0][i], b = val[1][j];
-    T out = T(0);
+    T out;
     if (DIM == 2) {
-      if (a * a + b * b < R * R)
-        out = T(0.5) * R * R * (ax_psi[0][i] + ax_psi[1][j] - hpi) -
-              T(0.5) * (a * ax_s[0][i] + b * ax_s[1][j]) + a * b;
+      out = T(0.5) * R * R * (ax_psi[0][i] + ax_psi[1][j] - hpi) -
+            T(0.5) * (a * ax_s[0][i] + b * ax_s[1][j]) + a * b;
     } else {
       const T cc = val[2][k];
-      if ((a * a + b * b) + cc * cc < R * R) {
-        const T* ab = pr + 4 * (0 * cap.pair_cap + j * tx + i);
-        const T* ac = pr + 4 * (1 * cap.pair_cap + k * tx + i);
-        const T* bc = pr + 4 * (2 * cap.pair_cap + k * ty + j);
-        const T ka = kax[0][i], kb = kax[1][j], kc = kax[2][k];
-        T t3 = fma(R3, (ab[1] + ac[1]) + bc[1], -piR3);
-        t3 = fma(-ka, ab[3] + ac[3], t3);
-        t3 = fma(-kb, ab[2] + bc[3], t3);
-        t3 = fma(-kc, ac[2] + bc[2], t3);
-        t3 = fma(hpi, (ka + kb) + kc, t3);
-        t3 += (ab[0] + ac[0]) + bc[0];
-        t3 = fma(T(-3) * (a * b), cc, t3);
-        out = t3 * T(1.0 / 3.0);
-      }
+      const T* ab = pr + 4 * (0 * cap.pair_cap + j * tx + i);
+      const T* ac = pr + 4 * (1 * cap.pair_cap + k * tx + i);
+      const T* bc = pr + 4 * (2 * cap.pair_cap + k * ty + j);
+      const T ka = kax[0][i], kb = kax[1][j], kc = kax[2][k];
+      T t3 = fma(R3, (ab[1] + ac[1]) + bc[1], -piR3);
+      t3 = fma(-ka, ab[3] + ac[3], t3);
+      t3 = fma(-kb, ab[2] + bc[3], t3);
+      t3 = fma(-kc, ac[2] + bc[2], t3);
+      t3 = fma(hpi, (ka + kb) + kc, t3);
+      t3 += (ab[0] + ac[0]) + bc[0];
+      t3 = fma(T(-3) * (a * b), cc, t3);
+      out = t3 * T(1.0 / 3.0);
     }
     tab[t] = out;
   }

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntile
     const bool covered = v.own[0][n] >= 0;
     if (__all_sync(0xffffffffu, covered || !active)) continue;  // the whole segment is covered
     T f[LAT::Q];
-    pull<LAT, STORE>(v, xx, y, w.z, n, active, f);
+    pull<LAT, STORE>(v, xx, y, w.z, n, active && !covered, f);  // covered nodes: the covered kernel pulls them
     plain_core<LAT, STORE>(v, n, active && !covered, f);
   }
 }

@@ -302,22 +302,23 @@ extern "C" int lbm_imb_probe_df(const float* h, const float* l, const double* d,
 
 namespace lbm {
 
-// FP64 pipe rate: every thread runs 8 independent chains of one FP64
+// FP64 pipe rate: every thread runs 16 independent chains of one FP64
 // instruction (KIND 0 fused multiply-add, 1 add, 2 multiply; one FP64-pipe
-// operation each), 32 per loop trip; the chains' sums are stored so that
-// nothing is optimised away
+// operation each), 32 per chain and loop trip; the chains' sums are stored
+// so that nothing is optimised away
+constexpr int kFp64Chains = 16;
 template <int KIND>
 __global__ void __launch_bounds__(256) fp64_rate_kernel(double* sink, long long trips) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double a[8];
+  double a[kFp64Chains];
 #pragma unroll
-  for (int k = 0; k < 8; k++) a[k] = 1.0 + 1e-9 * (double)(i + k);
+  for (int k = 0; k < kFp64Chains; k++) a[k] = 1.0 + 1e-9 * (double)(i + k);
   const double m = 0.9999999999, c = 1e-13;
   for (long long t = 0; t < trips; t++) {
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+    for (int r = 0; r < 32; r++)
 #pragma unroll
-      for (int k = 0; k < 8; k++) {
+      for (int k = 0; k < kFp64Chains; k++) {
         if constexpr (KIND == 0) a[k] = fma(a[k], m, c);
         else if constexpr (KIND == 1) a[k] = __dadd_rn(a[k], c);
         else a[k] = __dmul_rn(a[k], m);
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(256) fp64_rate_kernel(double* sink, long long 
   }
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < 8; k++) s += a[k];
+  for (int k = 0; k < kFp64Chains; k++) s += a[k];
   sink[i] = s;
 }
 
@@ -343,7 +344,16 @@ extern "C" int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64
     cudaEventDestroy(e0);
     return LBM_IMB_ECUDA;
   }
-  const unsigned blocks = (unsigned)(sink_len / 256);
+  // exactly the resident blocks (one wave, no tail): at most sink_len threads
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::fp64_rate_kernel<0>, 256, 0);
+  else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::fp64_rate_kernel<1>, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::fp64_rate_kernel<2>, 256, 0);
+  long long nb = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  if (nb > sink_len / 256) nb = sink_len / 256;
+  const unsigned blocks = (unsigned)nb;
   auto launch = [&]() {
     if (kind == 0) lbm::fp64_rate_kernel<0><<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);
     else if (kind == 1) lbm::fp64_rate_kernel<1><<<blocks, 256, 0, s>>>(dev_sink, (long long)trips);
@@ -360,7 +370,7 @@ extern "C" int lbm_imb_probe_fp64_rate(double* dev_sink, int64_t sink_len, int64
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess || !(ms > 0.f)) return LBM_IMB_ECUDA;
-  *gops = (double)sink_len * (double)trips * 32.0 / (ms * 1e-3) / 1e9;
+  *gops = (double)blocks * 256.0 * (double)trips * 32.0 * lbm::kFp64Chains / (ms * 1e-3) / 1e9;
   if (ms_out) *ms_out = ms;
   return LBM_IMB_OK;
 }
