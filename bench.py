@@ -64,6 +64,10 @@ WORKLOADS = {
                   name="D3Q19 192x384x192 channel (walls y), config-3 solid fraction, spheres R=3.75, "
                        "density ratio 1000 (profiling case)",
                   short="D3Q19 192x384x192 walls y, config-3 physics"),
+    "cfg3w": dict(make=lambda seed: I.config3_scaled(nx=256, ny=384, nz=192, seed=seed),
+                  name="D3Q19 256x384x192 channel (walls y), config-3 solid fraction, spheres R=3.75, "
+                       "density ratio 1000 (profiling case, rows of whole 128-node tiles)",
+                  short="D3Q19 256x384x192 walls y, config-3 physics"),
     "cfg1": dict(make=lambda seed: I.config1(seed=seed),
                  name="D2Q9 128x256 channel, 20 disks R=6, density ratio 10, g=1e-6, tau=0.6",
                  short="D2Q9 128x256 channel, 20 disks R=6"),
@@ -73,18 +77,18 @@ WORKLOADS = {
 }
 
 
-# FP64 operations (DADD, DMUL, DFMA: one FP64-pipe slot each) the collision
-# executes per node, by lattice dimension: (every node: pull, moments, BGK;
-# extra per covered node: the immersed-boundary update).  Counted with ncu
-# (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}) on the profiling
-# cases of `bench.py --profile-case` with and without particles:
-# D3Q19 192x384x192 (covered fraction 0.218), D2Q9 2048x4096 (0.067).
-FP64_OPS = {3: (158.3, 259.0), 2: (67.0, 175.0)}
-# the same counts split by instruction (DADD, DMUL, DFMA), from
-# smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum of the same
-# cases: the roofline's peak is the rate the FP64 pipe sustains on this mix,
-# each kind at its rate measured in the run (lbm_imb_probe_fp64_rate)
-FP64_MIX = {3: ({"add": 58.33, "mul": 29.00, "fma": 71.00}, {"add": 112.0, "mul": 32.3, "fma": 114.4}),
+# FP64 operations (DADD, DMUL, DFMA) the collision executes per node, by
+# lattice dimension: (every node: pull, moments, BGK; extra per covered node:
+# the immersed-boundary update).  Counted with ncu
+# (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum) on the
+# profiling cases of `bench.py --profile-case` with and without particles,
+# whose rows are whole 128-node tiles (no idle lanes): D3Q19 256x384x192
+# (covered fraction 0.2181), D2Q9 2048x4096 (0.067).
+FP64_OPS = {3: (131.0, 257.0), 2: (67.0, 175.0)}
+# the same counts split by instruction: the roofline's peak is the rate the
+# FP64 pipe sustains on this mix, each kind at its rate measured in the run
+# (lbm_imb_probe_fp64_rate: DFMA 2 per SM and clock, DADD and DMUL 16/19 of that)
+FP64_MIX = {3: ({"add": 45.0, "mul": 24.0, "fma": 62.0}, {"add": 111.75, "mul": 31.26, "fma": 113.98}),
             2: ({"add": 18.00, "mul": 18.00, "fma": 31.00}, {"add": 79.7, "mul": 29.7, "fma": 67.8})}
 
 

@@ -489,8 +489,10 @@ int lbm_imb_probe_df(const float* h, const float* l, const double* d, double* to
  * measured against: one wave of resident 256-thread blocks on every SM (at
  * most sink_len threads; sink_len a multiple of 256; dev_sink holds one
  * double per thread, device, caller-owned), each thread running 16
- * independent chains of 32 * trips FP64 instructions of one kind (0 fused
- * multiply-add, 1 add, 2 multiply); one warm-up launch, then one launch
+ * independent chains of 16 * trips FP64 instructions of one kind (0 fused
+ * multiply-add, 1 add, 2 multiply; the constant operands in the constant
+ * bank, so that register-file bandwidth does not cap the rate); one
+ * warm-up launch, then one launch
  * timed with CUDA events on `stream`.  *gops = instructions per second /
  * 1e9 (over all threads), *ms_out (may be NULL) the timed launch's
  * duration.  Synchronises the stream.  EINVAL on bad sizes, kind or

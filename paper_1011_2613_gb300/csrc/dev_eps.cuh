@@ -84,6 +84,9 @@ __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, c
     i = wrap_idx(i, v.nx);
     k = wrap_idx(k, v.nz);
     const long long n = ((long long)k * v.ny + j) * v.pitch + i;
+    // a flagged group holds a node whose first slot a particle claimed, and
+    // that node lies in the particle's box: clear the flag with the slots
+    if (v.grp != nullptr && v.own[0][n] >= 0) v.grp[n >> 2] = 0;
     // taken slots form a prefix: stop at the first free one (concurrent
     // clears of overlapping boxes only ever write -1, so the order of their
     // reads and writes does not matter)
@@ -196,7 +199,10 @@ __device__ __forceinline__ int classify_cell(const T (*bnd)[64], const float (*b
 }
 
 // per-axis decomposition of cell i into (lower, upper) value indices of boxes
-// on the non-negative half-axis; returns the number of boxes (1 or 2)
+// on the non-negative half-axis; returns the number of boxes (1 or 2).  Only
+// signs are tested, so the FP32 copies of the offsets serve every element
+// type (the conversion keeps the sign and zero; offsets are multiples of the
+// centre's ulp, far above FP32's smallest number)
 template <typename T>
 __device__ __forceinline__ int split_axis(const T* b, int i, int zero, int (&lo_i)[2], int (&hi_i)[2]) {
   const T bl = b[i], bh = b[i + 1];
@@ -462,9 +468,10 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
   __shared__ int n_part, n_need, n_pin, cov_base, cov_wsum[4];
   // nodes whose first owner slot this particle claims (split collision):
-  // one flag per cell of the box, compacted in box order (x fastest, then
-  // y, then z) at the end, so that the list holds each particle's nodes in
-  // row order and consecutive entries are mostly adjacent in memory
+  // one flag per cell of the box; at the end their four-node groups are
+  // claimed (one flag word per group, the first claimant lists it) and
+  // listed in box order (x fastest, then y, then z), so that the list holds
+  // each particle's groups in row order, mostly adjacent in memory
   const bool want_list = v.cov_list != nullptr && split_form(v.collide_variant);
   unsigned char* s_flag = smem + (TABLE ? 0 : raster_list_offset(cap, (int)sizeof(T)));
   const double R2 = R64 * R64;
@@ -527,15 +534,33 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     }
     atomicOr(v.err, ERR_OWNERS);
   };
-  // the flagged cells in box order: a block scan of per-thread counts over
-  // contiguous cell ranges, one reservation per particle in the global list
+  // the groups of the flagged cells in box order: each thread walks a
+  // contiguous cell range, claims the group of every flagged cell (a run of
+  // cells in one group tries once) and marks the cells whose group it won
+  // (flag 2); a block scan of the per-thread counts gives one reservation
+  // per particle in the global list
   auto flush_list = [&]() {
     if (!want_list) return;
     __syncthreads();
     const int per = (ncell + (int)blockDim.x - 1) / (int)blockDim.x;
     const int t0 = min((int)threadIdx.x * per, ncell), t1 = min(t0 + per, ncell);
     int c = 0;
-    for (int t = t0; t < t1; t++) c += s_flag[t];
+    long long last = -1;
+    for (int t = t0; t < t1; t++) {
+      if (!s_flag[t]) continue;
+      const int ci = t % ne[0], cj = (t / ne[0]) % ne[1], ck = t / (ne[0] * ne[1]);
+      long long n = 0;
+      node_of(ci, cj, ck, n);
+      const long long g = n >> 2;
+      if (g == last) {
+        s_flag[t] = 1;
+        continue;
+      }
+      last = g;
+      const bool won = atomicExch(&v.grp[g], 1) == 0;
+      s_flag[t] = won ? 2 : 1;
+      c += won ? 1 : 0;
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int incl = c;
 #pragma unroll
@@ -554,11 +579,11 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     __syncthreads();
     int o = cov_base + wbase + incl - c;
     for (int t = t0; t < t1; t++) {
-      if (!s_flag[t]) continue;
+      if (s_flag[t] != 2) continue;
       const int ci = t % ne[0], cj = (t / ne[0]) % ne[1], ck = t / (ne[0] * ne[1]);
       long long n = 0;
       node_of(ci, cj, ck, n);
-      v.cov_list[o++] = (int)n;
+      v.cov_list[o++] = (int)(n >> 2);
     }
   };
   const FastDiv3 cdiv(ne[0], ne[1]);
@@ -582,9 +607,9 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     }
     cells[atomicAdd(&n_part, 1)] = idx[0] | (idx[1] << 8) | (idx[2] << 16);  // ne <= 62
     int al[2], ah[2], bl[2], bh[2], cl[2] = {0, 0}, ch[2] = {0, 0};
-    const int na = split_axis<T>(bnd[0], idx[0], ne[0] + 1, al, ah);
-    const int nb = split_axis<T>(bnd[1], idx[1], ne[1] + 1, bl, bh);
-    const int nc = DIM == 3 ? split_axis<T>(bnd[2], idx[2], ne[2] + 1, cl, ch) : 1;
+    const int na = split_axis<float>(bndf[0], idx[0], ne[0] + 1, al, ah);
+    const int nb = split_axis<float>(bndf[1], idx[1], ne[1] + 1, bl, bh);
+    const int nc = DIM == 3 ? split_axis<float>(bndf[2], idx[2], ne[2] + 1, cl, ch) : 1;
     for (int ia = 0; ia < na; ia++)
       for (int ib = 0; ib < nb; ib++)
         for (int ic = 0; ic < nc; ic++) {
@@ -709,9 +734,9 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     const int t = cells[q];
     const int idx[3] = {t & 0xff, (t >> 8) & 0xff, t >> 16};
     int al[2], ah[2], bl[2], bh[2], cl[2] = {0, 0}, ch[2] = {0, 0};
-    const int na = split_axis<T>(bnd[0], idx[0], ne[0] + 1, al, ah);
-    const int nb = split_axis<T>(bnd[1], idx[1], ne[1] + 1, bl, bh);
-    const int nc = DIM == 3 ? split_axis<T>(bnd[2], idx[2], ne[2] + 1, cl, ch) : 1;
+    const int na = split_axis<float>(bndf[0], idx[0], ne[0] + 1, al, ah);
+    const int nb = split_axis<float>(bndf[1], idx[1], ne[1] + 1, bl, bh);
+    const int nc = DIM == 3 ? split_axis<float>(bndf[2], idx[2], ne[2] + 1, cl, ch) : 1;
     T sum = T(0);
     for (int ia = 0; ia < na; ia++)
       for (int ib = 0; ib < nb; ib++)

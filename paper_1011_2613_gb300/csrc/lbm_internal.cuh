@@ -114,11 +114,17 @@ struct View {
   double* vl_ref;
   int* vl_flag;
   long long* vl_builds;
-  // covered-node list of the split collision (pair storage, form
-  // kCollideSplit): the rasteriser appends every node whose first owner slot
-  // it claims; null otherwise
+  // covered-group list of the split collision (pair storage, forms
+  // kCollideSplit..+2): groups of four consecutive nodes of a row (one
+  // 32-byte sector of a population array) holding a node whose first owner
+  // slot a particle claims.  grp[n >> 2] flags the group of node n (set by
+  // the rasteriser, which lists each flagged group once; cleared with the
+  // owner slots); the covered kernel updates every node of a listed group,
+  // the plain kernel the others, so that neither writes part of a sector.
+  // Null otherwise
   int* cov_list;
   int* cov_count;
+  int* grp;
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i

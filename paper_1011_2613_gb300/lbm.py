@@ -510,7 +510,7 @@ def probe_df(h, l, d):
 FP64_KINDS = {"fma": 0, "add": 1, "mul": 2}
 
 
-def probe_fp64_rate(kind: str = "fma", trips: int = 1200, blocks_per_sm: int = 8, device=None):
+def probe_fp64_rate(kind: str = "fma", trips: int = 2400, blocks_per_sm: int = 8, device=None):
     """Measured FP64 throughput of this GPU for one instruction kind ("fma",
     "add", "mul"; G instructions/s) and the timed launch's ms (test hook)."""
     import torch
