@@ -108,18 +108,17 @@ def fp64_peak_for(mix, rates):
     n = sum(mix.values())
     return n / sum(c / rates[k] for k, c in mix.items())
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node of
-# one collide launch, from ncu captures of the 192x384x192 D3Q19 profiling
-# case at the config-3 solid fraction (forms 5 / 9 / 8); a config-3 launch
-# moves this many bytes per node times its node count (same solid fraction).
-TRAFFIC_B_PER_NODE = {("f64", 3): 385.5, ("f32dev", 3): 189.6, ("f16dev", 3): 116.3}
-# forms whose DRAM traffic differs from the storage's entry (FP64: the
-# pulled-ahead forms 4 and 5 read 375 B per node, the others 386 B; the pair
-# storage only for its split forms, both kernels together)
-TRAFFIC_BY_FORM = {("f64", 3, 4): 374.9, ("f64", 3, 5): 374.9, ("dfdev", 3, 6): 586.2, ("dfdev", 3, 7): 625.3}
+# one collide launch (the split forms: both kernels), from ncu captures of
+# the D3Q19 256x384x192 profiling case at the config-3 solid fraction, by
+# storage and form; a config-3 launch moves this many bytes per node times
+# its node count (same solid fraction).  Forms not captured on the current
+# kernels report no traffic.
+TRAFFIC_BY_FORM = {("f64", 3, 5): 363.5, ("f32dev", 3, 6): 171.2, ("f32dev", 3, 9): 170.3,
+                   ("f16dev", 3, 8): 97.7, ("dfdev", 3, 7): 452.7, ("dfdev", 3, 8): 458.4}
 
 
 def traffic_per_node(storage, dim, form):
-    return TRAFFIC_BY_FORM.get((storage, dim, form), TRAFFIC_B_PER_NODE.get((storage, dim)))
+    return TRAFFIC_BY_FORM.get((storage, dim, form))
 
 
 def collide_kernel_name(storage, dim, form):
@@ -127,11 +126,11 @@ def collide_kernel_name(storage, dim, form):
     launch form 0's kernel)."""
     lat = "D3Q19" if dim == 3 else "D2Q9"
     if storage == "dfdev" and form == 6:
-        return f"collide_plain_kernel<{lat},dfdev> + collide_covered_kernel<{lat}>"
+        return f"collide_plain_kernel<{lat},dfdev> + collide_covered_group_kernel<{lat},FP64>"
     if storage == "dfdev" and form == 7:
-        return f"collide_plain_kernel<{lat},dfdev> + collide_covered_pair_kernel<{lat}>"
+        return f"collide_plain_kernel<{lat},dfdev> + collide_covered_group_kernel<{lat},pairs>"
     if storage == "dfdev" and form == 8:
-        return f"collide_plain_pair_kernel<{lat}> + collide_covered_pair_kernel<{lat}>"
+        return f"collide_plain_pair_kernel<{lat}> + collide_covered_group_kernel<{lat},pairs>"
     if form in (4, 5):
         return f"collide_prefetch_kernel<{lat},{storage}>"
     if form in (6, 7) and storage != "dfdev":

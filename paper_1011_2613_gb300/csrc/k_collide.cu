@@ -520,9 +520,10 @@ static void dispatch(const View& v, cudaStream_t s) {
     // the persistent fused forms, with the register budgets the pair
     // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
     // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
-    // split forms (plain nodes, then the rasteriser's covered-node list: 6
-    // in FP64, 7 in pair arithmetic, 8 as 7 with two plain nodes per thread
-    // in paired instructions); the other numbers use 0
+    // split forms (the nodes outside the listed groups, then the
+    // rasteriser's covered-group list: covered nodes in FP64 for 6, in pair
+    // arithmetic for 7, 8 as 7 with two plain nodes per thread in paired
+    // instructions); the other numbers use 0
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;

@@ -152,9 +152,9 @@ struct View {
 static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
 
 // collide forms of the pair storage that update plain and covered nodes in
-// two launches (the covered ones from the rasteriser's list): covered nodes
-// in FP64 (kCollideSplit) or in pair arithmetic (kCollideSplit + 1, and + 2
-// with the plain part two nodes per thread)
+// two launches (the groups holding covered nodes from the rasteriser's
+// list): covered nodes in FP64 (kCollideSplit) or in pair arithmetic
+// (kCollideSplit + 1, and + 2 with the plain part two nodes per thread)
 constexpr int kCollideSplit = 6;
 __host__ __device__ inline bool split_form(int variant) {
   return variant >= kCollideSplit && variant <= kCollideSplit + 2;

@@ -56,5 +56,8 @@ def test_collide_kernel_names_and_traffic():
     assert bench.collide_kernel_name("f64", 3, 9).startswith("collide_kernel")
     assert bench.collide_kernel_name("f32dev", 3, 9).startswith("collide_pair_kernel")
     assert "covered" in bench.collide_kernel_name("dfdev", 3, 6)
-    assert bench.traffic_per_node("f64", 3, 5) < bench.traffic_per_node("f64", 3, 0)
+    # measured forms only: the FP64 pulled-ahead form above its algorithmic
+    # 309.7 B per node, an uncaptured form without a figure
+    assert 309.7 < bench.traffic_per_node("f64", 3, 5) < 400.0
+    assert bench.traffic_per_node("f64", 3, 0) is None
     assert bench.traffic_per_node("f64", 2, 0) is None
