@@ -221,12 +221,11 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
  *   9 the same with 4 CTAs per SM.
  * The pair storage (LBM_IMB_STORE_DFDEV) has its own set: 0, 3 and 1 the
  * persistent queue form with budgets for 4, 3 and 2 CTAs per SM, 5 and 4
- * the pulled-ahead form with 3 and 2, 2 the TMA form, 6 to 8 the split
- * forms (the nodes outside the four-node groups that hold a covered node
- * in one launch, then the groups the rasteriser listed in a second, their
- * covered nodes in FP64 for 6, in pair arithmetic for 7; 8 as 7 with the
- * first launch two adjacent nodes per thread in paired FP32
- * instructions); 9 falls back to 0.
+ * the pulled-ahead form with 3 and 2, 2 the TMA form, 6 and 7 the split
+ * forms (plain nodes in one launch, then the covered nodes listed by the
+ * rasteriser in a second: in FP64 for 6, in pair arithmetic for 7, and
+ * for 8 as 7 with the plain part two adjacent nodes per thread in paired
+ * FP32 instructions); 9 falls back to 0.
  * Returns EINVAL outside 0..9.  Not for batch members or batches. */
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
 

@@ -44,7 +44,7 @@ struct Layout {
   size_t off_lo, off_kin, off_binof, off_bincount, off_binslot, off_err, off_red, off_stage;
   size_t off_tab;  // Eq. 6 table (eps_method 1), 0 bytes otherwise
   size_t off_vl_nbr, off_vl_count, off_vl_ref, off_vl_flag;  // Verlet lists (dem_skin > 0)
-  size_t off_cov_list, off_cov_count, off_grp;  // covered-group list and flags (pair storage with particles)
+  size_t off_cov_list, off_cov_count;  // covered-node list (pair storage with particles)
   size_t stage_bytes;
   size_t total;
 };
@@ -198,9 +198,8 @@ int make_layout(const lbm_imb_config* c, Layout* L, bool check_positions = true)
   L->off_vl_ref = take(vl ? np * 24 : 0);
   L->off_vl_flag = take(16);
   const bool cov = c->storage == LBM_IMB_STORE_DFDEV && c->n_particles > 0;
-  L->off_cov_list = take(cov ? (size_t)L->plane : 0);  // one int per four-node group
+  L->off_cov_list = take(cov ? (size_t)L->plane * 4 : 0);
   L->off_cov_count = take(16);
-  L->off_grp = take(cov ? (size_t)L->plane : 0);
   const size_t dense_row = (size_t)c->nx * 8 * (L->Q > 5 ? L->Q : 5);
   const size_t full = dense_row * (size_t)c->ny * nz;
   L->stage_bytes = full < kStageMax ? full : kStageMax;
@@ -477,7 +476,6 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   const bool cov = c->storage == LBM_IMB_STORE_DFDEV && np > 0;
   v.cov_list = cov ? reinterpret_cast<int*>(base + L.off_cov_list) : nullptr;
   v.cov_count = cov ? reinterpret_cast<int*>(base + L.off_cov_count) : nullptr;
-  v.grp = cov ? reinterpret_cast<int*>(base + L.off_grp) : nullptr;
   v.tab_lo_r = v.tab_h_r = v.tab_h_s = v.tab_h_t = 0.f;
   if (v.eps_method == 1)
     lbm::eps_table_geometry(c->dim, c->radius[0], &v.tab_lo_r, &v.tab_h_r, &v.tab_h_s, &v.tab_h_t);
@@ -541,7 +539,6 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   if (!st) {
     cudaError_t e = cudaMemsetAsync(v.err, 0, 16, h->stream);
     if (e == cudaSuccess && v.cov_count) e = cudaMemsetAsync(v.cov_count, 0, 16, h->stream);
-    if (e == cudaSuccess && v.grp) e = cudaMemsetAsync(v.grp, 0, (size_t)L.plane, h->stream);
     for (int s = 0; s < lbm::kMaxOwners && e == cudaSuccess; s++)
       e = cudaMemsetAsync(v.own[s], 0xff, (size_t)L.plane * 4, h->stream);
     if (e == cudaSuccess && v.eps_method == 1)

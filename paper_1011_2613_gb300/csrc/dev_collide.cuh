@@ -1108,9 +1108,9 @@ __device__ __forceinline__ void pair_node(const View& v, const int x, const int 
 // even) per thread in paired FP32 instructions (DF2): directions with
 // c_x = 0 come as one aligned 16-byte load of both nodes' pairs, the others
 // as two 8-byte loads; the moments and BGK of both nodes run side by side
-// (bitwise the single-node results); nodes outside the covered groups are
-// pulled and stored (aligned 16 bytes when both are), the listed groups are
-// left to the covered kernel.
+// (bitwise the single-node results); uncovered nodes are pulled and stored
+// (aligned 16 bytes when both are), covered ones are left to the covered
+// kernel.
 // ---------------------------------------------------------------------------
 template <class LAT>
 __device__ __forceinline__ void plain_pair_node(const View& v, const int x, const int y, const int z,
@@ -1122,9 +1122,9 @@ __device__ __forceinline__ void plain_pair_node(const View& v, const int x, cons
   const bool a0 = row_ok && x < nx, a1 = row_ok && x + 1 < nx;
   const int xc = a0 ? x : ((nx - 1) & ~1);  // a valid even node for idle lanes
   const int n = (z * ny + y) * pitch + xc;
-  const bool listed = v.grp != nullptr && v.grp[n >> 2] != 0;  // the pair's group is the covered kernel's
-  const bool s0 = a0 && !listed, s1 = a1 && !listed;  // stored here
-  if (!__any_sync(0xffffffffu, s0 || s1)) return;     // the whole warp's nodes are listed (or idle)
+  const int2 o = *reinterpret_cast<const int2*>(v.own[0] + n);
+  const bool s0 = a0 && o.x < 0, s1 = a1 && o.y < 0;  // stored here (not covered)
+  if (!__any_sync(0xffffffffu, s0 || s1)) return;     // the whole warp's nodes are covered (or idle)
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
   const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
   const int ry[3] = {y * pitch, ym * pitch, yp * pitch};

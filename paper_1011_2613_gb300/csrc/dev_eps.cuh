@@ -84,9 +84,6 @@ __device__ __forceinline__ void eps_clear_particle(const View& v, const int p, c
     i = wrap_idx(i, v.nx);
     k = wrap_idx(k, v.nz);
     const long long n = ((long long)k * v.ny + j) * v.pitch + i;
-    // a flagged group holds a node whose first slot a particle claimed, and
-    // that node lies in the particle's box: clear the flag with the slots
-    if (v.grp != nullptr && v.own[0][n] >= 0) v.grp[n >> 2] = 0;
     // taken slots form a prefix: stop at the first free one (concurrent
     // clears of overlapping boxes only ever write -1, so the order of their
     // reads and writes does not matter)
@@ -468,10 +465,9 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
   __shared__ float offc[TABLE ? 3 : 1][64];  // table: cell-centre offsets (FP64 difference, FP32)
   __shared__ int n_part, n_need, n_pin, cov_base, cov_wsum[4];
   // nodes whose first owner slot this particle claims (split collision):
-  // one flag per cell of the box; at the end their four-node groups are
-  // claimed (one flag word per group, the first claimant lists it) and
-  // listed in box order (x fastest, then y, then z), so that the list holds
-  // each particle's groups in row order, mostly adjacent in memory
+  // one flag per cell of the box, compacted in box order (x fastest, then
+  // y, then z) at the end, so that the list holds each particle's nodes in
+  // row order and consecutive entries are mostly adjacent in memory
   const bool want_list = v.cov_list != nullptr && split_form(v.collide_variant);
   unsigned char* s_flag = smem + (TABLE ? 0 : raster_list_offset(cap, (int)sizeof(T)));
   const double R2 = R64 * R64;
@@ -534,33 +530,15 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     }
     atomicOr(v.err, ERR_OWNERS);
   };
-  // the groups of the flagged cells in box order: each thread walks a
-  // contiguous cell range, claims the group of every flagged cell (a run of
-  // cells in one group tries once) and marks the cells whose group it won
-  // (flag 2); a block scan of the per-thread counts gives one reservation
-  // per particle in the global list
+  // the flagged cells in box order: a block scan of per-thread counts over
+  // contiguous cell ranges, one reservation per particle in the global list
   auto flush_list = [&]() {
     if (!want_list) return;
     __syncthreads();
     const int per = (ncell + (int)blockDim.x - 1) / (int)blockDim.x;
     const int t0 = min((int)threadIdx.x * per, ncell), t1 = min(t0 + per, ncell);
     int c = 0;
-    long long last = -1;
-    for (int t = t0; t < t1; t++) {
-      if (!s_flag[t]) continue;
-      const int ci = t % ne[0], cj = (t / ne[0]) % ne[1], ck = t / (ne[0] * ne[1]);
-      long long n = 0;
-      node_of(ci, cj, ck, n);
-      const long long g = n >> 2;
-      if (g == last) {
-        s_flag[t] = 1;
-        continue;
-      }
-      last = g;
-      const bool won = atomicExch(&v.grp[g], 1) == 0;
-      s_flag[t] = won ? 2 : 1;
-      c += won ? 1 : 0;
-    }
+    for (int t = t0; t < t1; t++) c += s_flag[t];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int incl = c;
 #pragma unroll
@@ -579,11 +557,11 @@ __device__ __forceinline__ void eps_raster_particle(const View& v, const int p, 
     __syncthreads();
     int o = cov_base + wbase + incl - c;
     for (int t = t0; t < t1; t++) {
-      if (s_flag[t] != 2) continue;
+      if (!s_flag[t]) continue;
       const int ci = t % ne[0], cj = (t / ne[0]) % ne[1], ck = t / (ne[0] * ne[1]);
       long long n = 0;
       node_of(ci, cj, ck, n);
-      v.cov_list[o++] = (int)(n >> 2);
+      v.cov_list[o++] = (int)n;
     }
   };
   const FastDiv3 cdiv(ne[0], ne[1]);

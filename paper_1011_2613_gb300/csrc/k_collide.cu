@@ -65,8 +65,7 @@ __global__ void __launch_bounds__(128, MINB) collide_kernel(View v, int ntiles) 
 }
 
 // Split form of the pair storage, plain part: persistent row tiles as in
-// form 0; the four-node groups the rasteriser listed (those holding a
-// covered node) are skipped: the covered kernel updates them.
+// form 0; covered nodes are skipped (the rasteriser listed them).
 template <class LAT, int STORE>
 __global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntiles) {
   using T = typename Storage<STORE>::T;
@@ -77,11 +76,11 @@ __global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntile
     const bool active = x < nx;
     const int xx = active ? x : nx - 1, y = v.y0 + w.y;
     const int n = (w.z * v.ny + y) * v.pitch + xx;
-    const bool listed = v.grp != nullptr && v.grp[n >> 2] != 0;  // the group is the covered kernel's
-    if (__all_sync(0xffffffffu, listed || !active)) continue;  // the whole segment is listed
+    const bool covered = v.own[0][n] >= 0;
+    if (__all_sync(0xffffffffu, covered || !active)) continue;  // the whole segment is covered
     T f[LAT::Q];
-    pull<LAT, STORE>(v, xx, y, w.z, n, active && !listed, f);
-    plain_core<LAT, STORE>(v, n, active && !listed, f);
+    pull<LAT, STORE>(v, xx, y, w.z, n, active && !covered, f);  // covered nodes: the covered kernel pulls them
+    plain_core<LAT, STORE>(v, n, active && !covered, f);
   }
 }
 
@@ -99,58 +98,61 @@ __global__ void __launch_bounds__(128, 3) collide_plain_pair_kernel(View v) {
   plain_pair_node<LAT>(v, x, v.y0 + rr % v.ny_c, rr / v.ny_c, row_ok);
 }
 
-// Split form, covered part: each warp takes 8 entries of the covered-group
+// Split form, covered part: each warp takes 32 entries of the covered-node
 // list (grouped by particle, so the warp's force sums mostly go to one
-// owner), a lane per node of the four-node groups, and pulls and takes the
-// moments in pair arithmetic.  The group's uncovered nodes get the plain
-// update (so that every population sector is written whole); the covered
-// ones the immersed-boundary update, in FP64 (form 6) or in pair arithmetic
-// (forms 7, 8).
-__device__ __forceinline__ int group_node(const View& v, const int count, const int base, const int lane,
-                                          bool& active, int& x, int& y, int& z) {
-  const int e = base + (lane >> 2);
-  const int g = v.cov_list[e < count ? e : base];
-  const int n = 4 * g + (lane & 3);
-  const int row = v.ny * v.pitch;
-  z = n / row;
-  const int r = n - z * row;
-  y = r / v.pitch;
-  x = r - y * v.pitch;
-  active = e < count && x < v.nx;  // the row's padding past nx is no node
-  return n;
-}
-
-template <class LAT, bool FP64_IMB>
-__global__ void __launch_bounds__(128, 3) collide_covered_group_kernel(View v) {
+// owner), pulls and takes the moments in pair arithmetic, and gives the
+// immersed-boundary update in FP64.
+template <class LAT>
+__global__ void __launch_bounds__(128, 3) collide_covered_kernel(View v) {
   constexpr int STORE = LBM_IMB_STORE_DFDEV;
   constexpr int Q = LAT::Q;
   const int count = *v.cov_count;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int base = warp * 8; base < count; base += nwarps * 8) {
-    bool active;
-    int x, y, z;
-    const int n = group_node(v, count, base, lane, active, x, y, z);
-    const bool cov = active && v.own[0][n] >= 0;
+  const int row = v.ny * v.pitch;
+  for (int base = warp * 32; base < count; base += nwarps * 32) {
+    const int i = base + lane;
+    const bool mine = i < count;
+    const int n = v.cov_list[mine ? i : base];
+    const int z = n / row, r = n - z * row;
+    const int y = r / v.pitch, x = r - y * v.pitch;
     DF f[Q];
-    pull<LAT, STORE>(v, x < v.nx ? x : v.nx - 1, y, z, n, active, f);
-    const Moments<DF> md = plain_core<LAT, STORE>(v, n, active && !cov, f);
-    if (!__any_sync(0xffffffffu, cov)) continue;
-    if constexpr (FP64_IMB) {
-      double g[Q];
+    pull<LAT, STORE>(v, x, y, z, n, true, f);
+    const Moments<DF> md = moments<LAT, STORE>(v, f);
+    double g[Q];
 #pragma unroll
-      for (int q = 0; q < Q; q++) g[q] = df_to_bits(f[q]);
-      Moments<double> m;
-      m.rho = df_to_bits(md.rho);
-      m.drho = df_to_bits(md.drho);
-      m.ux = df_to_bits(md.ux);
-      m.uy = df_to_bits(md.uy);
-      m.uz = df_to_bits(md.uz);
-      m.k = k_of<LAT, kDfDevImb>(m.ux, m.uy, m.uz);
-      imb_core<LAT, kDfDevImb>(v, x, y, z, n, cov, g, m);
-    } else {
-      imb_core<LAT, STORE>(v, x, y, z, n, cov, f, md);
-    }
+    for (int q = 0; q < Q; q++) g[q] = df_to_bits(f[q]);
+    Moments<double> m;
+    m.rho = df_to_bits(md.rho);
+    m.drho = df_to_bits(md.drho);
+    m.ux = df_to_bits(md.ux);
+    m.uy = df_to_bits(md.uy);
+    m.uz = df_to_bits(md.uz);
+    m.k = k_of<LAT, kDfDevImb>(m.ux, m.uy, m.uz);
+    imb_core<LAT, kDfDevImb>(v, x, y, z, n, mine, g, m);
+  }
+}
+
+// The same covered part in pair arithmetic throughout (form 7): the
+// update's FP32-pipe instructions instead of the FP64 pipe.
+template <class LAT>
+__global__ void __launch_bounds__(128, 3) collide_covered_pair_kernel(View v) {
+  constexpr int STORE = LBM_IMB_STORE_DFDEV;
+  constexpr int Q = LAT::Q;
+  const int count = *v.cov_count;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int row = v.ny * v.pitch;
+  for (int base = warp * 32; base < count; base += nwarps * 32) {
+    const int i = base + lane;
+    const bool mine = i < count;
+    const int n = v.cov_list[mine ? i : base];
+    const int z = n / row, r = n - z * row;
+    const int y = r / v.pitch, x = r - y * v.pitch;
+    DF f[Q];
+    pull<LAT, STORE>(v, x, y, z, n, true, f);
+    const Moments<DF> m = moments<LAT, STORE>(v, f);
+    imb_core<LAT, STORE>(v, x, y, z, n, mine, f, m);
   }
 }
 
@@ -460,7 +462,10 @@ static void launch_split(const View& v, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
     grid_a = (per_sm > 0 ? per_sm : 1) * sms;
     per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_group_kernel<LAT, COVERED == 0>, 128, 0);
+    if constexpr (COVERED >= 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_pair_kernel<LAT>, 128, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
     grid_b = (per_sm > 0 ? per_sm : 1) * sms;
   }
   const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
@@ -471,7 +476,8 @@ static void launch_split(const View& v, cudaStream_t s) {
     collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
   }
   if (v.cov_list == nullptr) return;
-  collide_covered_group_kernel<LAT, COVERED == 0><<<grid_b, 128, 0, s>>>(v);
+  if constexpr (COVERED >= 1) collide_covered_pair_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+  else collide_covered_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
 }
 
 template <class LAT, int STORE, int MINB>
@@ -520,10 +526,9 @@ static void dispatch(const View& v, cudaStream_t s) {
     // the persistent fused forms, with the register budgets the pair
     // arithmetic needs (1 and 3: 2 and 3 CTAs per SM; 4 and 5: the
     // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
-    // split forms (the nodes outside the listed groups, then the
-    // rasteriser's covered-group list: covered nodes in FP64 for 6, in pair
-    // arithmetic for 7, 8 as 7 with two plain nodes per thread in paired
-    // instructions); the other numbers use 0
+    // split forms (plain nodes, then the rasteriser's covered-node list: 6
+    // in FP64, 7 in pair arithmetic, 8 as 7 with two plain nodes per thread
+    // in paired instructions); the other numbers use 0
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;

@@ -114,17 +114,11 @@ struct View {
   double* vl_ref;
   int* vl_flag;
   long long* vl_builds;
-  // covered-group list of the split collision (pair storage, forms
-  // kCollideSplit..+2): groups of four consecutive nodes of a row (one
-  // 32-byte sector of a population array) holding a node whose first owner
-  // slot a particle claims.  grp[n >> 2] flags the group of node n (set by
-  // the rasteriser, which lists each flagged group once; cleared with the
-  // owner slots); the covered kernel updates every node of a listed group,
-  // the plain kernel the others, so that neither writes part of a sector.
-  // Null otherwise
+  // covered-node list of the split collision (pair storage, form
+  // kCollideSplit): the rasteriser appends every node whose first owner slot
+  // it claims; null otherwise
   int* cov_list;
   int* cov_count;
-  int* grp;
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i
@@ -152,9 +146,9 @@ struct View {
 static_assert(sizeof(View) % sizeof(int) == 0, "View is copied as ints");
 
 // collide forms of the pair storage that update plain and covered nodes in
-// two launches (the groups holding covered nodes from the rasteriser's
-// list): covered nodes in FP64 (kCollideSplit) or in pair arithmetic
-// (kCollideSplit + 1, and + 2 with the plain part two nodes per thread)
+// two launches (the covered ones from the rasteriser's list): covered nodes
+// in FP64 (kCollideSplit) or in pair arithmetic (kCollideSplit + 1, and + 2
+// with the plain part two nodes per thread)
 constexpr int kCollideSplit = 6;
 __host__ __device__ inline bool split_form(int variant) {
   return variant >= kCollideSplit && variant <= kCollideSplit + 2;
