@@ -114,7 +114,7 @@ def fp64_peak_for(mix, rates):
 # its node count (same solid fraction).  Forms not captured on the current
 # kernels report no traffic.
 TRAFFIC_BY_FORM = {("f64", 3, 5): 363.5, ("f32dev", 3, 6): 171.2, ("f32dev", 3, 9): 170.3,
-                   ("f16dev", 3, 8): 97.7}
+                   ("f16dev", 3, 8): 97.7, ("dfdev", 3, 7): 533.5, ("dfdev", 3, 8): 539.5}
 
 
 def traffic_per_node(storage, dim, form):
@@ -193,7 +193,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
@@ -204,13 +204,17 @@ class ClockSampler:
                 mx.append(float(parts[1]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[2]))
+            except ValueError:
+                pass
             for nm, val in zip(names, parts[3:7]):
                 if val.lower() == "active":
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w": statistics.median(pw) if pw else None}
 
 
 # ---------------------------------------------------------------------------
@@ -362,8 +366,9 @@ def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=N
     tune, done = pick_collide(sim, args)
     sim.step(args.warmup)
     sim.sync()
-    ms = time_graph_steps(sim, torch, args.steps)
-    kms, tot = sim.step_profiled(args.steps)
+    with ClockSampler() as clk:  # clocks and power while this form is timed
+        ms = time_graph_steps(sim, torch, args.steps)
+        kms, tot = sim.step_profiled(args.steps)
     fo = owned_fraction(sim, torch)
     bpl = algorithmic_bytes_per_lup(cfg, fo)
     t_coll = kms["collide"] / args.steps
@@ -374,7 +379,7 @@ def measure_variant(cfg, args, torch, peaks, label, ref_sim=None, steps_target=N
            "traffic": (traffic_per_node(cfg.storage, cfg.dim, tune["variant"]) * cfg.n_nodes
                        if traffic_per_node(cfg.storage, cfg.dim, tune["variant"]) is not None else None),
            "kernel": collide_kernel_name(cfg.storage, cfg.dim, tune["variant"]),
-           "collide_variant": tune["variant"], "collide_tuning": tune.get("table")}
+           "collide_variant": tune["variant"], "collide_tuning": tune.get("table"), "clocks": clk.summary()}
     if ref_sim is not None:
         done += args.warmup + 2 * args.steps
         if steps_target > done:
