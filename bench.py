@@ -114,7 +114,8 @@ def fp64_peak_for(mix, rates):
 # its node count (same solid fraction).  Forms not captured on the current
 # kernels report no traffic.
 TRAFFIC_BY_FORM = {("f64", 3, 5): 363.5, ("f32dev", 3, 6): 171.2, ("f32dev", 3, 9): 170.3,
-                   ("f16dev", 3, 8): 97.7, ("dfdev", 3, 7): 533.5, ("dfdev", 3, 8): 539.5}
+                   ("f16dev", 3, 8): 97.7, ("dfdev", 3, 7): 533.5, ("dfdev", 3, 8): 539.5,
+                   ("dfdev", 3, 9): 497.8}
 
 
 def traffic_per_node(storage, dim, form):
@@ -131,6 +132,8 @@ def collide_kernel_name(storage, dim, form):
         return f"collide_plain_kernel<{lat},dfdev> + collide_covered_pair_kernel<{lat}>"
     if storage == "dfdev" and form == 8:
         return f"collide_plain_pair_kernel<{lat}> + collide_covered_pair_kernel<{lat}>"
+    if storage == "dfdev" and form == 9:
+        return f"collide_plain_buf_kernel<{lat}> + collide_covered_buf_kernel<{lat}>"
     if form in (4, 5):
         return f"collide_prefetch_kernel<{lat},{storage}>"
     if form in (6, 7) and storage != "dfdev":

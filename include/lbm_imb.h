@@ -225,7 +225,9 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
  * forms (plain nodes in one launch, then the covered nodes listed by the
  * rasteriser in a second: in FP64 for 6, in pair arithmetic for 7, and
  * for 8 as 7 with the plain part two adjacent nodes per thread in paired
- * FP32 instructions); 9 falls back to 0.
+ * FP32 instructions; 9 as 7 with the covered nodes' pulled populations and
+ * moments handed from the plain launch to the covered one through a
+ * compact buffer instead of the rasteriser's list).
  * Returns EINVAL outside 0..9.  Not for batch members or batches. */
 int lbm_imb_set_collide_variant(lbm_imb_t* h, int variant);
 

@@ -102,7 +102,7 @@ def tuned_batch(cfgs, device=None, path: str | None = None, steps: int = 3):
 COLLIDE_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9)
 # the pair storage has the persistent fused forms, the TMA form and the
 # split forms (6: covered nodes in FP64, 7: in pair arithmetic)
-COLLIDE_VARIANTS_BY_STORAGE = {"dfdev": (0, 1, 2, 3, 4, 5, 6, 7, 8)}
+COLLIDE_VARIANTS_BY_STORAGE = {"dfdev": (0, 1, 2, 3, 4, 5, 6, 7, 8, 9)}
 
 
 def collide_variants(storage) -> tuple:

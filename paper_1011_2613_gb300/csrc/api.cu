@@ -45,6 +45,8 @@ struct Layout {
   size_t off_tab;  // Eq. 6 table (eps_method 1), 0 bytes otherwise
   size_t off_vl_nbr, off_vl_count, off_vl_ref, off_vl_flag;  // Verlet lists (dem_skin > 0)
   size_t off_cov_list, off_cov_count;  // covered-node list (pair storage with particles)
+  size_t off_cbuf;                      // covered-node buffer of split form 9 (same)
+  long long cbuf_cap;
   size_t stage_bytes;
   size_t total;
 };
@@ -200,6 +202,11 @@ int make_layout(const lbm_imb_config* c, Layout* L, bool check_positions = true)
   const bool cov = c->storage == LBM_IMB_STORE_DFDEV && c->n_particles > 0;
   L->off_cov_list = take(cov ? (size_t)L->plane * 4 : 0);
   L->off_cov_count = take(16);
+  // covered nodes lie in particle boxes of at most (2 rmax + 2)^dim cells
+  long long cells = 1;
+  for (int d = 0; d < c->dim; d++) cells *= (long long)floor(2.0 * rmax) + 2;
+  L->cbuf_cap = cov ? (c->n_particles < L->plane / cells ? c->n_particles * cells : L->plane) : 0;
+  L->off_cbuf = take(cov ? (size_t)L->cbuf_cap * ((size_t)(L->Q + 5) * 8 + 4) : 0);
   const size_t dense_row = (size_t)c->nx * 8 * (L->Q > 5 ? L->Q : 5);
   const size_t full = dense_row * (size_t)c->ny * nz;
   L->stage_bytes = full < kStageMax ? full : kStageMax;
@@ -476,6 +483,8 @@ static int setup_handle(lbm_imb* h, const lbm_imb_config* c, void* dev_buf, cons
   const bool cov = c->storage == LBM_IMB_STORE_DFDEV && np > 0;
   v.cov_list = cov ? reinterpret_cast<int*>(base + L.off_cov_list) : nullptr;
   v.cov_count = cov ? reinterpret_cast<int*>(base + L.off_cov_count) : nullptr;
+  v.cbuf = cov ? reinterpret_cast<float2*>(base + L.off_cbuf) : nullptr;
+  v.cbuf_cap = cov ? L.cbuf_cap : 0;
   v.tab_lo_r = v.tab_h_r = v.tab_h_s = v.tab_h_t = 0.f;
   if (v.eps_method == 1)
     lbm::eps_table_geometry(c->dim, c->radius[0], &v.tab_lo_r, &v.tab_h_r, &v.tab_h_s, &v.tab_h_t);

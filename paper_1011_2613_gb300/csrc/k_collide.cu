@@ -84,6 +84,94 @@ __global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntile
   }
 }
 
+// Split form 9 of the pair storage, plain part: as collide_plain_kernel,
+// but the covered nodes are pulled here too, and their populations and
+// moments go to a compact buffer (one atomic per warp reserves the
+// entries), which the covered kernel reads contiguously instead of pulling
+// 19 strided populations again.
+template <class LAT>
+__global__ void __launch_bounds__(128, 4) collide_plain_buf_kernel(View v, int ntiles) {
+  constexpr int STORE = LBM_IMB_STORE_DFDEV;
+  constexpr int Q = LAT::Q;
+  const unsigned FULL = 0xffffffffu;
+  const int nx = v.nx, nz = v.nz, lane = threadIdx.x & 31;
+  const long long cap = v.cbuf_cap;
+  (void)ntiles;
+  for (TileWalk w(blockIdx.x, gridDim.x, (nx + 127) / 128, v.ny_c); w.z < nz; w.next()) {
+    const int x = w.xt * 128 + (int)threadIdx.x;
+    const bool active = x < nx;
+    const int xx = active ? x : nx - 1, y = v.y0 + w.y;
+    const int n = (w.z * v.ny + y) * v.pitch + xx;
+    const bool covered = active && v.own[0][n] >= 0;
+    DF f[Q];
+    pull<LAT, STORE>(v, xx, y, w.z, n, active, f);
+    const Moments<DF> m = plain_core<LAT, STORE>(v, n, active && !covered, f);
+    const unsigned b = __ballot_sync(FULL, covered);
+    if (b == 0u) continue;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(v.cov_count, __popc(b));
+    base = __shfl_sync(FULL, base, 0);
+    if (!covered) continue;
+    const long long i = (long long)base + __popc(b & ((1u << lane) - 1u));
+    if (i >= cap) {  // more covered nodes than the particles' boxes hold: reported, not stored
+      atomicOr(v.err, ERR_OWNERS);
+      continue;
+    }
+    float2* e = v.cbuf;
+#pragma unroll
+    for (int q = 0; q < Q; q++) e[q * cap + i] = make_float2(f[q].h, f[q].l);
+    e[(Q + 0) * cap + i] = make_float2(m.rho.h, m.rho.l);
+    e[(Q + 1) * cap + i] = make_float2(m.drho.h, m.drho.l);
+    e[(Q + 2) * cap + i] = make_float2(m.ux.h, m.ux.l);
+    e[(Q + 3) * cap + i] = make_float2(m.uy.h, m.uy.l);
+    e[(Q + 4) * cap + i] = make_float2(m.uz.h, m.uz.l);
+    reinterpret_cast<int*>(e + (Q + 5) * cap)[i] = n;
+  }
+}
+
+// Split form 9, covered part: the buffer's entries 32 per warp, the
+// immersed-boundary update in pair arithmetic.
+template <class LAT>
+__global__ void __launch_bounds__(128, 3) collide_covered_buf_kernel(View v) {
+  constexpr int STORE = LBM_IMB_STORE_DFDEV;
+  constexpr int Q = LAT::Q;
+  const long long cap = v.cbuf_cap;
+  const int cnt = *v.cov_count;
+  const int count = cnt < cap ? cnt : (int)cap;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int row = v.ny * v.pitch;
+  const float2* e = v.cbuf;
+  const int* en = reinterpret_cast<const int*>(e + (Q + 5) * cap);
+  for (int base = warp * 32; base < count; base += nwarps * 32) {
+    const int i = base + lane;
+    const bool mine = i < count;
+    const long long k = mine ? i : base;
+    DF f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const float2 a = e[q * cap + k];
+      f[q] = DF(a.x, a.y);
+    }
+    Moments<DF> m;
+    float2 a = e[(Q + 0) * cap + k];
+    m.rho = DF(a.x, a.y);
+    a = e[(Q + 1) * cap + k];
+    m.drho = DF(a.x, a.y);
+    a = e[(Q + 2) * cap + k];
+    m.ux = DF(a.x, a.y);
+    a = e[(Q + 3) * cap + k];
+    m.uy = DF(a.x, a.y);
+    a = e[(Q + 4) * cap + k];
+    m.uz = DF(a.x, a.y);
+    m.k = k_of<LAT, STORE>(m.ux, m.uy, m.uz);
+    const int n = en[k];
+    const int z = n / row, r = n - z * row;
+    const int y = r / v.pitch, x = r - y * v.pitch;
+    imb_core<LAT, STORE>(v, x, y, z, n, mine, f, m);
+  }
+}
+
 // Split form of the pair storage, plain part with two nodes per thread
 // (form 8): CTA = 128 nodes (64 pairs) of two consecutive rows; grid x over
 // row pairs, grid y over 128-node x tiles.
@@ -459,17 +547,26 @@ static void launch_split(const View& v, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms < 1) sms = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
+    if constexpr (COVERED == 3)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_buf_kernel<LAT>, 128, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_plain_kernel<LAT, STORE>, 128, 0);
     grid_a = (per_sm > 0 ? per_sm : 1) * sms;
     per_sm = 0;
-    if constexpr (COVERED >= 1)
+    if constexpr (COVERED == 3)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_buf_kernel<LAT>, 128, 0);
+    else if constexpr (COVERED >= 1)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_pair_kernel<LAT>, 128, 0);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, collide_covered_kernel<LAT>, 128, 0);
     grid_b = (per_sm > 0 ? per_sm : 1) * sms;
   }
   const int ntiles = ((v.nx + 127) / 128) * v.ny_c * v.nz;
-  if constexpr (COVERED == 2) {  // the plain part two nodes per thread
+  if constexpr (COVERED == 3) {  // covered nodes through the compact buffer
+    collide_plain_buf_kernel<LAT><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
+    if (v.cbuf != nullptr) collide_covered_buf_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
+    return;
+  } else if constexpr (COVERED == 2) {  // the plain part two nodes per thread
     const dim3 grid((v.ny_c * v.nz + 1) / 2, (v.nx + 127) / 128);
     collide_plain_pair_kernel<LAT><<<grid, 128, 0, s>>>(v);
   } else {
@@ -528,7 +625,8 @@ static void dispatch(const View& v, cudaStream_t s) {
     // prefetching form at 2 and 3), the TMA-pipelined form (2) and the
     // split forms (plain nodes, then the rasteriser's covered-node list: 6
     // in FP64, 7 in pair arithmetic, 8 as 7 with two plain nodes per thread
-    // in paired instructions); the other numbers use 0
+    // in paired instructions; 9: the covered nodes' pulled populations and
+    // moments passed through a compact buffer instead of the list)
     switch (v.collide_variant) {
       case 1: launch_fused<LAT, STORE, 2, false>(v, s); break;
       case 2: launch_tma<LAT, STORE>(v, s); break;
@@ -538,6 +636,7 @@ static void dispatch(const View& v, cudaStream_t s) {
       case kCollideSplit: launch_split<LAT, STORE, 0>(v, s); break;
       case kCollideSplit + 1: launch_split<LAT, STORE, 1>(v, s); break;
       case kCollideSplit + 2: launch_split<LAT, STORE, 2>(v, s); break;
+      case kCollideSplit + 3: launch_split<LAT, STORE, 3>(v, s); break;
       default: launch_fused<LAT, STORE, 4, false>(v, s);
     }
   } else {

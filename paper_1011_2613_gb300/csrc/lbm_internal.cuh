@@ -119,6 +119,12 @@ struct View {
   // it claims; null otherwise
   int* cov_list;
   int* cov_count;
+  // compact buffer of the split form kCollideSplit + 3 (pair storage): the
+  // plain kernel appends each covered node's pulled populations and moments
+  // (pairs as float2, SoA [Q + 5][cbuf_cap]) and node offset
+  // ([cbuf_cap] ints after them), counted in cov_count; null otherwise
+  float2* cbuf;
+  long long cbuf_cap;
   // physics
   double tau, omega, gf[3], gs[3], rho0, kn, ln_e, dem_den;
   double fq[19];  // 3 w_q (c_q . g_f): body force per unit density, Eq. (1) F_i

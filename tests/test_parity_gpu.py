@@ -212,7 +212,8 @@ def test_spinning_particles_torque_3d(storage):
     assert np.max(np.abs(pg["omega"] - pr["omega"])) < 1e-12
 
 
-@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6), ("dfdev", 7), ("dfdev", 8)])
+@pytest.mark.parametrize("storage,form", [("f64", 0), ("dfdev", 0), ("dfdev", 6), ("dfdev", 7), ("dfdev", 8),
+                                          ("dfdev", 9)])
 def test_config3_shape_channel_3d(storage, form):
     """Cut-down config 3 (D3Q19, walls in y, spheres R=3.75, ratio 1000)."""
     cfg = I.config3_scaled(nx=40, ny=48, nz=36, storage=storage)
@@ -284,9 +285,9 @@ def test_reduced_storage_error(storage, tol_u, tol_f):
 def test_collide_variants_agree(dim, storage):
     """Every kernel form gives bitwise the populations of form 0 after one
     step (nx = 300 spans ragged row tiles), and the FP64 forms stay within
-    the oracle tolerance after 12 steps.  Forms 7 and 8 of the pair storage
-    update covered nodes in pair arithmetic instead of FP64: within 1e-14
-    there."""
+    the oracle tolerance after 12 steps.  Forms 7, 8 and 9 of the pair
+    storage update covered nodes in pair arithmetic instead of FP64: within
+    1e-14 there."""
     if dim == 3:
         cfg = I.config3_scaled(nx=300, ny=20, nz=12).replace(storage=storage)
     else:
@@ -299,7 +300,7 @@ def test_collide_variants_agree(dim, storage):
         sim = L.Simulation(cfg)
         sim.set_collide_variant(var)
         sim.step(1)
-        if storage == "dfdev" and var in (7, 8):
+        if storage == "dfdev" and var in (7, 8, 9):
             assert rel_err(sim.populations(), f_base) < 1e-14, f"variant {var}"
         else:
             assert np.array_equal(sim.populations(), f_base), f"variant {var}"
