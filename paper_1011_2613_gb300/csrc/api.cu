@@ -206,7 +206,7 @@ int make_layout(const lbm_imb_config* c, Layout* L, bool check_positions = true)
   long long cells = 1;
   for (int d = 0; d < c->dim; d++) cells *= (long long)floor(2.0 * rmax) + 2;
   L->cbuf_cap = cov ? (c->n_particles < L->plane / cells ? c->n_particles * cells : L->plane) : 0;
-  L->off_cbuf = take(cov ? (size_t)L->cbuf_cap * ((size_t)(L->Q + 5) * 8 + 4) : 0);
+  L->off_cbuf = take(cov ? (size_t)L->cbuf_cap * ((size_t)(L->Q + 5) * 8 + 20) : 0);
   const size_t dense_row = (size_t)c->nx * 8 * (L->Q > 5 ? L->Q : 5);
   const size_t full = dense_row * (size_t)c->ny * nz;
   L->stage_bytes = full < kStageMax ? full : kStageMax;

@@ -540,10 +540,19 @@ __device__ __forceinline__ void node_rel(const View& v, const Kin<PT>& k, const 
 // The whole warp calls it; lanes with mine = false do the arithmetic on a
 // valid node and write nothing.
 // ---------------------------------------------------------------------------
-template <class LAT, int STORE>
+// the first two owner slots and first covered fraction of a node, when a
+// caller has them already (HEAD = true)
+template <typename E>
+struct SlotHead {
+  int o0, o1;
+  E e0;
+};
+
+template <class LAT, int STORE, bool HEAD = false>
 __device__ __forceinline__ void imb_core(const View& v, const int xx, const int y, const int z, const int n,
                                          const bool mine, typename Storage<STORE>::T (&f)[LAT::Q],
-                                         const Moments<typename Storage<STORE>::T>& m) {
+                                         const Moments<typename Storage<STORE>::T>& m,
+                                         const SlotHead<typename Storage<STORE>::E> head = {}) {
   using S = Storage<STORE>;
   using T = typename S::T;
   using E = typename S::E;
@@ -565,8 +574,8 @@ __device__ __forceinline__ void imb_core(const View& v, const int xx, const int 
   E eo[K];
   int no = 0;
   {
-    const int o0 = v.own[0][n], o1 = v.own[1][n];
-    const E e0 = static_cast<const E*>(v.eps[0])[n];
+    const int o0 = HEAD ? head.o0 : v.own[0][n], o1 = HEAD ? head.o1 : v.own[1][n];
+    const E e0 = HEAD ? head.e0 : static_cast<const E*>(v.eps[0])[n];
     own[0] = o0 >= 0 ? o0 : 0x7fffffff;
     eo[0] = o0 >= 0 ? e0 : E(0);
     no = o0 >= 0 ? 1 : 0;

@@ -85,10 +85,12 @@ __global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntile
 }
 
 // Split form 9 of the pair storage, plain part: as collide_plain_kernel,
-// but the covered nodes are pulled here too, and their populations and
-// moments go to a compact buffer (one atomic per warp reserves the
-// entries), which the covered kernel reads contiguously instead of pulling
-// 19 strided populations again.
+// but the covered nodes are pulled here too, and their populations,
+// moments, node offset and first owner slots go to a compact buffer (one
+// atomic per warp reserves the entries; layout: float2 [Q + 5][cap], then
+// double fraction [cap], int node [cap], int owner 0 [cap], int owner 1
+// [cap]), which the covered kernel reads contiguously instead of pulling 19
+// strided populations and the slots again.
 template <class LAT>
 __global__ void __launch_bounds__(128, 4) collide_plain_buf_kernel(View v, int ntiles) {
   constexpr int STORE = LBM_IMB_STORE_DFDEV;
@@ -102,7 +104,14 @@ __global__ void __launch_bounds__(128, 4) collide_plain_buf_kernel(View v, int n
     const bool active = x < nx;
     const int xx = active ? x : nx - 1, y = v.y0 + w.y;
     const int n = (w.z * v.ny + y) * v.pitch + xx;
-    const bool covered = active && v.own[0][n] >= 0;
+    const int o0 = active ? v.own[0][n] : -1;
+    const bool covered = o0 >= 0;
+    int o1 = -1;
+    double e0 = 0.0;
+    if (covered) {  // requested with the pull, consumed only by the covered kernel
+      o1 = v.own[1][n];
+      e0 = static_cast<const double*>(v.eps[0])[n];
+    }
     DF f[Q];
     pull<LAT, STORE>(v, xx, y, w.z, n, active, f);
     const Moments<DF> m = plain_core<LAT, STORE>(v, n, active && !covered, f);
@@ -125,14 +134,18 @@ __global__ void __launch_bounds__(128, 4) collide_plain_buf_kernel(View v, int n
     e[(Q + 2) * cap + i] = make_float2(m.ux.h, m.ux.l);
     e[(Q + 3) * cap + i] = make_float2(m.uy.h, m.uy.l);
     e[(Q + 4) * cap + i] = make_float2(m.uz.h, m.uz.l);
-    reinterpret_cast<int*>(e + (Q + 5) * cap)[i] = n;
+    reinterpret_cast<double*>(e + (Q + 5) * cap)[i] = e0;
+    int* ei = reinterpret_cast<int*>(reinterpret_cast<double*>(e + (Q + 5) * cap) + cap);
+    ei[i] = n;
+    ei[cap + i] = o0;
+    ei[2 * cap + i] = o1;
   }
 }
 
 // Split form 9, covered part: the buffer's entries 32 per warp, the
 // immersed-boundary update in pair arithmetic.
 template <class LAT>
-__global__ void __launch_bounds__(128, 3) collide_covered_buf_kernel(View v) {
+__global__ void __launch_bounds__(128, 4) collide_covered_buf_kernel(View v) {
   constexpr int STORE = LBM_IMB_STORE_DFDEV;
   constexpr int Q = LAT::Q;
   const long long cap = v.cbuf_cap;
@@ -142,7 +155,8 @@ __global__ void __launch_bounds__(128, 3) collide_covered_buf_kernel(View v) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   const int row = v.ny * v.pitch;
   const float2* e = v.cbuf;
-  const int* en = reinterpret_cast<const int*>(e + (Q + 5) * cap);
+  const double* ee = reinterpret_cast<const double*>(e + (Q + 5) * cap);
+  const int* en = reinterpret_cast<const int*>(ee + cap);
   for (int base = warp * 32; base < count; base += nwarps * 32) {
     const int i = base + lane;
     const bool mine = i < count;
@@ -168,7 +182,7 @@ __global__ void __launch_bounds__(128, 3) collide_covered_buf_kernel(View v) {
     const int n = en[k];
     const int z = n / row, r = n - z * row;
     const int y = r / v.pitch, x = r - y * v.pitch;
-    imb_core<LAT, STORE>(v, x, y, z, n, mine, f, m);
+    imb_core<LAT, STORE, true>(v, x, y, z, n, mine, f, m, SlotHead<double>{en[cap + k], en[2 * cap + k], ee[k]});
   }
 }
 

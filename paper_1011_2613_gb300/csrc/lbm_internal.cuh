@@ -121,8 +121,9 @@ struct View {
   int* cov_count;
   // compact buffer of the split form kCollideSplit + 3 (pair storage): the
   // plain kernel appends each covered node's pulled populations and moments
-  // (pairs as float2, SoA [Q + 5][cbuf_cap]) and node offset
-  // ([cbuf_cap] ints after them), counted in cov_count; null otherwise
+  // (pairs as float2, SoA [Q + 5][cbuf_cap]), first covered fraction
+  // (double [cbuf_cap]), node offset and first two owner slots (int
+  // [3][cbuf_cap]), counted in cov_count; null otherwise
   float2* cbuf;
   long long cbuf_cap;
   // physics
