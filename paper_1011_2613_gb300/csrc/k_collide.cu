@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(128, 4) collide_plain_buf_kernel(View v, int n
     }
     DF f[Q];
     pull<LAT, STORE>(v, xx, y, w.z, n, active, f);
-    const Moments<DF> m = plain_core<LAT, STORE>(v, n, active && !covered, f);
+    // every node of the row gets the plain update stored (the covered
+    // kernel overwrites the covered ones later): whole sectors, so the L2
+    // writes them back without reading the rest of a sector from DRAM
+    const Moments<DF> m = plain_core<LAT, STORE>(v, n, active, f);
     const unsigned b = __ballot_sync(FULL, covered);
     if (b == 0u) continue;
     int base = 0;
