@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128, 4) collide_plain_kernel(View v, int ntile
 // [cap]), which the covered kernel reads contiguously instead of pulling 19
 // strided populations and the slots again.
 template <class LAT>
-__global__ void __launch_bounds__(128, 4) collide_plain_buf_kernel(View v, int ntiles) {
+__global__ void __launch_bounds__(128, 5) collide_plain_buf_kernel(View v, int ntiles) {
   constexpr int STORE = LBM_IMB_STORE_DFDEV;
   constexpr int Q = LAT::Q;
   const unsigned FULL = 0xffffffffu;
