@@ -115,7 +115,7 @@ def fp64_peak_for(mix, rates):
 # kernels report no traffic.
 TRAFFIC_BY_FORM = {("f64", 3, 5): 363.5, ("f32dev", 3, 6): 171.2, ("f32dev", 3, 9): 170.3,
                    ("f16dev", 3, 8): 97.7, ("dfdev", 3, 7): 533.5, ("dfdev", 3, 8): 539.5,
-                   ("dfdev", 3, 9): 503.6}
+                   ("dfdev", 3, 9): 493.2}
 
 
 def traffic_per_node(storage, dim, form):
