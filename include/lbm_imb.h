@@ -218,7 +218,7 @@ int lbm_imb_launches_per_step(lbm_imb_t* h, int* launches);
  *   7 the same with a budget for 5 CTAs per SM, 8 two adjacent nodes per
  *   thread with paired FP32 arithmetic and aligned pair loads/stores
  *   (reduced-precision storages only; FP64 falls back to 0; 6 CTAs per SM),
- *   9 the same with 4 CTAs per SM.
+ *   9 the same with 5 CTAs per SM.
  * The pair storage (LBM_IMB_STORE_DFDEV) has its own set: 0, 3 and 1 the
  * persistent queue form with budgets for 4, 3 and 2 CTAs per SM, 5 and 4
  * the pulled-ahead form with 3 and 2, 2 the TMA form, 6 and 7 the split

@@ -633,7 +633,7 @@ static void launch_pair(const View& v, cudaStream_t s) {
 //   7  the same, 5 CTAs per SM
 //   8  two-node form (paired FP32 arithmetic), 6 CTAs per SM (reduced-
 //      precision storages; FP64 uses 0)
-//   9  the same, 4 CTAs per SM
+//   9  the same, 5 CTAs per SM
 template <class LAT, int STORE>
 static void dispatch(const View& v, cudaStream_t s) {
   if constexpr (STORE == LBM_IMB_STORE_DFDEV) {
@@ -669,7 +669,7 @@ static void dispatch(const View& v, cudaStream_t s) {
       case 6: launch_packed<LAT, STORE, 8>(v, s); break;
       case 7: launch_packed<LAT, STORE, 5>(v, s); break;
       case 8: launch_pair<LAT, STORE, 6>(v, s); break;
-      case 9: launch_pair<LAT, STORE, 4>(v, s); break;
+      case 9: launch_pair<LAT, STORE, 5>(v, s); break;
       default: launch_fused<LAT, STORE, 4, false>(v, s);
     }
   }
