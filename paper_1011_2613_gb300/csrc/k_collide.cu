@@ -190,16 +190,17 @@ __global__ void __launch_bounds__(128, 4) collide_covered_buf_kernel(View v) {
 }
 
 // Split form of the pair storage, plain part with two nodes per thread
-// (form 8): CTA = 128 nodes (64 pairs) of two consecutive rows; grid x over
-// row pairs, grid y over 128-node x tiles.
+// (form 8): CTA = 128 nodes (64 pairs) of two consecutive rows; one grid
+// dimension over (row pair, 128-node x tile), x tiles fastest.
 template <class LAT>
 __global__ void __launch_bounds__(128, 3) collide_plain_pair_kernel(View v) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rows = v.ny_c * v.nz;
-  const int r = blockIdx.x * 2 + (warp >> 1);
+  const int nxt = (v.nx + 127) / 128;  // x tiles fastest (see collide_pair_kernel)
+  const int r = (int)(blockIdx.x / nxt) * 2 + (warp >> 1);
   const bool row_ok = r < rows;
   const int rr = row_ok ? r : rows - 1;
-  const int x = blockIdx.y * 128 + ((warp & 1) * 32 + lane) * 2;
+  const int x = (int)(blockIdx.x % nxt) * 128 + ((warp & 1) * 32 + lane) * 2;
   plain_pair_node<LAT>(v, x, v.y0 + rr % v.ny_c, rr / v.ny_c, row_ok);
 }
 
@@ -270,17 +271,21 @@ __global__ void __launch_bounds__(128, MINB) collide_packed_kernel(View v) {
   packed_node<LAT, STORE>(v, active ? x : v.nx - 1, blockIdx.y, blockIdx.z, active, smem_p);
 }
 
-// Two-node form: CTA = 128 nodes (64 pairs) of two consecutive rows; grid x
-// over row pairs, grid y over 128-node x tiles (reduced-precision storages).
+// Two-node form: CTA = 128 nodes (64 pairs) of two consecutive rows; one
+// grid dimension over (row pair, 128-node x tile), x tiles fastest
+// (reduced-precision storages).
 template <class LAT, int STORE, int MINB>
 __global__ void __launch_bounds__(128, MINB) collide_pair_kernel(View v) {
   extern __shared__ __align__(16) unsigned char smem_pp[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rows = v.ny * v.nz;
-  const int r = blockIdx.x * 2 + (warp >> 1);
+  // x tiles fastest, so that the CTAs of a row pair run side by side and the
+  // sector a shifted pull shares with the next tile is still in L2
+  const int nxt = (v.nx + 127) / 128;
+  const int r = (int)(blockIdx.x / nxt) * 2 + (warp >> 1);
   const bool row_ok = r < rows;
   const int rr = row_ok ? r : rows - 1;
-  const int x = blockIdx.y * 128 + ((warp & 1) * 32 + lane) * 2;
+  const int x = (int)(blockIdx.x % nxt) * 128 + ((warp & 1) * 32 + lane) * 2;
   pair_node<LAT, STORE>(v, x, rr % v.ny, rr / v.ny, row_ok, smem_pp);
 }
 
@@ -584,7 +589,7 @@ static void launch_split(const View& v, cudaStream_t s) {
     if (v.cbuf != nullptr) collide_covered_buf_kernel<LAT><<<grid_b, 128, 0, s>>>(v);
     return;
   } else if constexpr (COVERED == 2) {  // the plain part two nodes per thread
-    const dim3 grid((v.ny_c * v.nz + 1) / 2, (v.nx + 127) / 128);
+    const unsigned grid = (unsigned)(((v.ny_c * v.nz + 1) / 2) * ((v.nx + 127) / 128));
     collide_plain_pair_kernel<LAT><<<grid, 128, 0, s>>>(v);
   } else {
     collide_plain_kernel<LAT, STORE><<<grid_a < ntiles ? grid_a : ntiles, 128, 0, s>>>(v, ntiles);
@@ -617,7 +622,7 @@ static void launch_pair(const View& v, cudaStream_t s) {
                            smem);
       attr = true;
     }
-    const dim3 grid((v.ny * v.nz + 1) / 2, (v.nx + 127) / 128);
+    const unsigned grid = (unsigned)(((v.ny * v.nz + 1) / 2) * ((v.nx + 127) / 128));
     collide_pair_kernel<LAT, STORE, MINB><<<grid, 128, smem, s>>>(v);
   }
 }
