@@ -113,7 +113,7 @@ def fp64_peak_for(mix, rates):
 # storage and form; a config-3 launch moves this many bytes per node times
 # its node count (same solid fraction).  Forms not captured on the current
 # kernels report no traffic.
-TRAFFIC_BY_FORM = {("f64", 3, 5): 363.5, ("f32dev", 3, 6): 171.2,
+TRAFFIC_BY_FORM = {("f64", 3, 5): 363.5, ("f32dev", 3, 6): 171.2, ("f32dev", 3, 9): 161.0,
                    ("f16dev", 3, 8): 88.5, ("dfdev", 3, 7): 533.5, ("dfdev", 3, 8): 539.5,
                    ("dfdev", 3, 9): 493.2}
 
