@@ -78,6 +78,14 @@ def test_required_bytes_and_validation(built):
     n32 = lbm.required_bytes(cfg.replace(storage="f32dev"))
     n16 = lbm.required_bytes(cfg.replace(storage="f16dev"))
     assert n16 < n32 < n
+    # the pair storage (same 8-byte elements as FP64) adds its covered-node
+    # list (one int per node) and the split form's covered-node buffer: an
+    # entry of (Q + 5) float pairs, a double and three ints for every cell
+    # of every particle's box, (2 R + 2)^d cells
+    cells = int(2 * cfg.radius.max() + 2) ** 2
+    buf = min(cfg.n_particles * cells, 128 * 256) * ((9 + 5) * 8 + 20)
+    ndf = lbm.required_bytes(cfg.replace(storage="dfdev"))
+    assert ndf >= n + 128 * 256 * 4 + buf
     assert built.lbm_imb_strerror(-7).decode().startswith("a lattice cell")
 
 
