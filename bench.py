@@ -643,7 +643,7 @@ def compact_line(head, roofline, roof_hbm, fp64_clocks, e2e, cpu, variants, node
     line["clocks"] = {k: line["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
     line["roofline"] = {"bound": roofline["bound"], "achieved": sig(roofline["achieved"]),
                         "peak": sig(roofline["peak"]), "unit": roofline["unit"], "frac": sig(roofline["frac"], 3),
-                        "traffic": sig(roofline["traffic"], 3), "peak_src": roofline.get("peak_short", "measured")}
+                        "traffic": sig(roofline["traffic"], 3)}  # the peak's source: in the detail line
     line["roofline_hbm"] = {k: sig(roof_hbm[k], 3) for k in ("achieved", "peak", "frac", "bytes_per_lup")}
     line["e2e"] = ({k: (sig(v) if isinstance(v, float) else v) for k, v in e2e.items() if k != "path"}
                    if e2e else None)
@@ -682,6 +682,22 @@ def compact_line(head, roofline, roof_hbm, fp64_clocks, e2e, cpu, variants, node
         line["valid"] = {"d/l": [int(r["R"] * 2) for r in vf["re_0.2"]],
                          "Kerr_re0.2": [sig(r["rel_error"], 2) for r in vf["re_0.2"]],
                          "K_re2": [sig(r["K"], 4) for r in vf["re_2"]]}
+    return line
+
+
+# summaries dropped, in this order, while the result line is longer than the
+# record keeps (the detail line before it holds them all)
+OPTIONAL_KEYS = ("valid", "closure", "batch32", "vs_oracle_ul2_pos_mass_force", "forms_mlups_hbm_traffic")
+
+
+def fit_line(line, limit=1490):
+    """The result line without the optional summaries it cannot hold within
+    `limit` characters; the contract's keys always stay."""
+    line = dict(line)
+    for k in OPTIONAL_KEYS:
+        if len(json.dumps(line, separators=(",", ":"))) <= limit:
+            break
+        line.pop(k, None)
     return line
 
 
@@ -835,8 +851,8 @@ def run_ours(args):
                            "l2": f"inputs>L2 ({2 * (19 if cfg.dim == 3 else 9) * ESZ[cfg.storage] * cfg.n_nodes / 1e9:.0f}"
                                  " GB)"},
                 "gpu_launches": launches, "clocks": clk.summary()}
-        print(json.dumps(compact_line(head, roofline, roof_hbm, fp64_clocks, e2e, cpu, variants, cfg.n_nodes),
-                         separators=(",", ":")))
+        print(json.dumps(fit_line(compact_line(head, roofline, roof_hbm, fp64_clocks, e2e, cpu, variants,
+                                               cfg.n_nodes)), separators=(",", ":")))
     if world > 1:
         dist.destroy_process_group()
 

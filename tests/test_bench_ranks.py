@@ -61,3 +61,18 @@ def test_collide_kernel_names_and_traffic():
     assert 309.7 < bench.traffic_per_node("f64", 3, 5) < 400.0
     assert bench.traffic_per_node("f64", 3, 0) is None
     assert bench.traffic_per_node("f64", 2, 0) is None
+
+
+def test_result_line_fits_the_record():
+    """The printed result line stays within the characters the record keeps:
+    optional summaries go first, the contract's keys stay."""
+    import json
+    import bench
+
+    line = {"metric": "m", "value": 1.0, "unit": "MLUPS", "roofline": {"frac": 0.9}, "e2e": {"value": 1.0},
+            "valid": {"x": "y" * 600}, "closure": {"x": "y" * 600}, "batch32": [1, 2, 3]}
+    out = bench.fit_line(line, limit=400)
+    assert len(json.dumps(out, separators=(",", ":"))) <= 400
+    assert {"metric", "value", "unit", "roofline", "e2e"} <= set(out)
+    assert "valid" not in out and "closure" not in out and out["batch32"] == [1, 2, 3]
+    assert bench.fit_line({"metric": "m"}, limit=400) == {"metric": "m"}
